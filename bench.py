@@ -1,0 +1,410 @@
+#!/usr/bin/env python
+"""Benchmark of the MF-WQ hot path on one GB300 (or N replicas under torchrun).
+
+Workload (the default, "ring-p4-nel128"): the thick quarter ring with the
+exact polar map, K = I, degree p = 4 (C^3), 128 elements per direction, so
+N = 130^3 = 2,197,000 DoFs and N_q = 263^3 WQ points; right-hand side from the
+forcing 3 pi^2 sin(pi x) sin(pi y) sin(pi z); FP64 operator and FP64 FD.
+
+A step is one complete FD-preconditioned BiCGStab solve from u = 0 to a
+relative residual of 1e-10 (every iteration: two MF-WQ applies, two FD
+applies, the Krylov vector updates and dot products), with the inputs
+resident in HBM.  The coefficient alone (873 MB) is larger than L2, so no L2
+flush is needed between steps.
+
+value = MF-WQ apply throughput delivered inside the solve: N x (operator
+applies per solve) / (time per solve), in DoF/s.  The line also carries the
+solve time and iteration count, the isolated apply and FD times, the apply
+DoF/s for p = 2..6 at 128 elements, and the mixed-precision versus FP64 solve
+to 1e-8 on the p = 6, 192-element ring.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MF-WQ apply DoF/s & FD-precond solve time, p=2-6; mixed vs FP64 at 1e-8"
+WORKLOAD = dict(name="ring-p4-nel128", p=4, nel=128, geometry="ring", forcing="sines", rtol=1e-10)
+SWEEP_P = (2, 3, 4, 5, 6)
+MIXED = dict(name="ring-p6-nel192", p=6, nel=192, rtol=1e-8)
+NUM_SMS = 152
+SM_MAX_MHZ_NOMINAL = 2070.0
+FP64_FLOP_PER_CLK_SM = 4  # 2 FP64 FMA per clock per SM: 1.25 TFLOP/s nominal / (152 SMs x 2.07 GHz)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the p sweep, mixed solve and CPU baseline")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- helpers
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while running."""
+
+    Q = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        try:
+            for line in open(self.f.name):
+                v = [x.strip() for x in line.split(",")]
+                if len(v) < 9:
+                    continue
+                if self.uuid and v[0] != self.uuid:
+                    continue
+                rows.append(v)
+        finally:
+            os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def band_lens(dense_rows):
+    """Band length (first to last nonzero) of each row of a dense table."""
+    out = []
+    for row in dense_rows:
+        nz = np.nonzero(row)[0]
+        out.append(0 if len(nz) == 0 else int(nz[-1] - nz[0] + 1))
+    return np.array(out)
+
+
+def stage_flops(mf, p, knots):
+    """Algorithmic FP64 flops of one launch of each stage (an FMA counts 2),
+    from the library's own band tables (zero padding excluded)."""
+    t = [mf.tables_1d(p, k) for k in knots]
+    n = [x["W"].shape[1] for x in t]
+    nq = [x["W"].shape[2] for x in t]
+    Lb = [band_lens(np.abs(x["B0"]) + np.abs(x["B1"])).sum() for x in t]
+    Lw = [band_lens(np.abs(x["W"]).sum(axis=0)).sum() for x in t]
+    N = n[0] * n[1] * n[2]
+    return {
+        "trial_z": 4.0 * Lb[2] * n[1] * n[0],
+        "trial_y": 6.0 * Lb[1] * nq[2] * n[0],
+        "xstage": float(nq[2] * nq[1]) * (6.0 * Lb[0] + 9.0 * nq[0] + 18.0 * Lw[0]),
+        "test_y": 18.0 * Lw[1] * nq[2] * n[0],
+        "test_z": 8.0 * Lw[2] * n[1] * n[0],
+        "fd_dim1": 2.0 * n[0] * N,
+        "fd_dim23": 2.0 * 0.5 * (n[1] + n[2]) * N,
+    }, n, nq
+
+
+def fp64_peak_tflops(sm_mhz=None):
+    mhz = SM_MAX_MHZ_NOMINAL if sm_mhz is None else sm_mhz
+    return NUM_SMS * mhz * 1e6 * FP64_FLOP_PER_CLK_SM / 1e12
+
+
+# --------------------------------------------------------------------------- oracle (CPU) baseline
+def oracle_iteration_sample(reps=1):
+    """Time the oracle's Algorithm-2 apply and FD apply at the full workload
+    size on the host cores; one BiCGStab iteration costs two of each."""
+    import oracle as O
+    from paper_1712_08565_gb300 import inputs
+    p, nel = WORKLOAD["p"], WORKLOAD["nel"]
+    tabs = O.uniform_tables(p, nel)
+    C6 = O.coefficient_grid(tabs, WORKLOAD["geometry"])
+    Cf = O.full_coeff(C6)
+    fd = O.fd_setup(tabs)
+    V = inputs.uniform_vector((tabs[2].n, tabs[1].n, tabs[0].n), 1)
+    ta, tf = [], []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        O.apply_alg2(tabs, Cf, V)
+        t1 = time.perf_counter()
+        O.fd_apply(fd, V)
+        t2 = time.perf_counter()
+        ta.append(t1 - t0)
+        tf.append(t2 - t1)
+    N = tabs[0].n * tabs[1].n * tabs[2].n
+    t_iter = 2 * (min(ta) + min(tf))
+    return {"value": 2 * N / t_iter, "unit": "DoF/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"oracle Algorithm-2 apply ({min(ta):.2f} s) and FD apply ({min(tf):.2f} s) at the full "
+                       f"{WORKLOAD['name']} size (numpy/BLAS on all host cores); one BiCGStab iteration = 2 of each, "
+                       f"value = 2N / iteration time"),
+            "apply_s": min(ta), "fd_s": min(tf)}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; setup is outside the timed region
+    t0 = time.perf_counter()
+    samples = [oracle_iteration_sample(1) for _ in range(max(1, args.steps))]
+    t1 = time.perf_counter()
+    best = max(samples, key=lambda s: s["value"])
+    line = {"impl": "reference", "metric": METRIC, "value": best["value"], "unit": "DoF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * (t1 - t0) / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "p": WORKLOAD["p"], "nel": WORKLOAD["nel"]},
+            "cpu_baseline": {k: best[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": best["value"], "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+def event_time(stream, fn, reps):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def make_op(mf, p, nel, mixed=False, fd="tf32", device=None, geometry="ring"):
+    from paper_1712_08565_gb300 import inputs
+    knots = [inputs.open_uniform_knots(p, nel)] * 3
+    op = mf.Operator(p, knots, mixed=mixed, fd_precision=fd, device=device)
+    C = op.eval_coeff(geometry)
+    op.set_coeff(C)
+    del C
+    return op, knots
+
+
+def p_sweep(mf, device):
+    import torch
+    from paper_1712_08565_gb300 import inputs
+    out = {}
+    for p in SWEEP_P:
+        op, knots = make_op(mf, p, WORKLOAD["nel"], device=device)
+        x = torch.from_numpy(inputs.uniform_vector(op.shape, 1)).to(device)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            op.apply(x, y)
+        ms = event_time(op.stream, lambda: op.apply(x, y), 10)
+        fl, _, _ = stage_flops(mf, p, knots)
+        apply_flops = sum(fl[k] for k in ("trial_z", "trial_y", "xstage", "test_y", "test_z"))
+        out[f"p{p}"] = {"N": op.N, "apply_ms": ms, "dof_per_s": op.N / (ms * 1e-3),
+                        "fp64_tflops": apply_flops / (ms * 1e-3) / 1e12}
+        op.close()
+        del x, y
+        torch.cuda.empty_cache()
+    return out
+
+
+def mixed_vs_fp64(mf, device):
+    import torch
+    res = {"workload": MIXED["name"], "rtol": MIXED["rtol"]}
+    op, _ = make_op(mf, MIXED["p"], MIXED["nel"], mixed=True, fd="tf32", device=device)
+    f = op.load_vector("ring", "sines")
+    res["N"] = op.N
+    for name, kw in (("fp64", dict(force_fp64=True)), ("mixed_tf32", dict(inner_rtol=1e-4))):
+        op.solve(f, rtol=MIXED["rtol"], maxit=2000, **kw)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        u, info = op.solve(f, rtol=MIXED["rtol"], maxit=2000, **kw)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        res[name] = {"time_s": dt, "iterations": info.iterations, "outer": info.outer_iterations,
+                     "rel_residual": info.rel_residual, "converged": info.converged}
+        if name == "fp64":
+            u64 = u.clone()
+        else:
+            res[name]["rel_err_vs_fp64"] = float(torch.linalg.vector_norm(u - u64) / torch.linalg.vector_norm(u64))
+    res["speedup"] = res["fp64"]["time_s"] / res["mixed_tf32"]["time_s"]
+    op.close()
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    from paper_1712_08565_gb300 import build
+    build.build()
+    from paper_1712_08565_gb300 import mfwq as mf
+    from paper_1712_08565_gb300 import inputs
+
+    p, nel = WORKLOAD["p"], WORKLOAD["nel"]
+    op, knots = make_op(mf, p, nel, device=device)
+    f = op.load_vector(WORKLOAD["geometry"], WORKLOAD["forcing"])
+    u = torch.empty_like(f)
+    rtol = WORKLOAD["rtol"]
+
+    def step():
+        return op.solve(f, u=None, rtol=rtol, maxit=1000)
+
+    for _ in range(max(args.warmup, 3)):
+        _, info = step()
+    # timed region
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(device).uuid)
+    except Exception:
+        uuid = None
+    op.profile(True)
+    op.profile_read(reset=True)
+    iters = []
+    with ClockSampler(uuid) as clk:
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        launches0 = mf.kernel_launches()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(op.stream)
+        for _ in range(args.steps):
+            _, info = step()
+            iters.append(info.iterations)
+        e1.record(op.stream)
+        e1.synchronize()
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        launches = mf.kernel_launches() - launches0
+        ms_total = e0.elapsed_time(e1)
+    clocks = clk.summary()
+    stages = op.profile_read(reset=True)
+    op.profile(False)
+    ms_step = ms_total / args.steps
+    if ws > 1:
+        t = torch.tensor([ms_step], device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    applies_per_solve = 2 * statistics.mean(iters)
+    value_rank = op.N * applies_per_solve / (ms_step * 1e-3)
+    value = value_rank * ws
+
+    # roofline of the dominant kernel (largest share of the timed region)
+    flops, n, nq = stage_flops(mf, p, knots)
+    dom = max((k for k in stages if k in flops), key=lambda k: stages[k][0])
+    dom_ms = stages[dom][0] / stages[dom][1]
+    achieved = flops[dom] / (dom_ms * 1e-3) / 1e12
+    peak = fp64_peak_tflops()
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "FP64 pipe: 152 SMs x 2070 MHz x 4 flop/clk (1.25 TFLOP/s nominal); not in MEASURED_PEAKS.json",
+                "algorithmic_flops_per_launch": flops[dom], "ms_per_launch": dom_ms}
+
+    # isolated apply and FD (same launch configuration)
+    x = torch.from_numpy(inputs.uniform_vector(op.shape, 1)).to(device)
+    y = torch.empty_like(x)
+    apply_ms = event_time(op.stream, lambda: op.apply(x, y), 10)
+    fd_ms = event_time(op.stream, lambda: op.fd_precond(x, y), 10)
+
+    # end to end through the C ABI with host buffers
+    f_host = torch.empty(op.shape, dtype=torch.float64, pin_memory=True)
+    f_host.copy_(f.cpu())
+    u_host = torch.empty(op.shape, dtype=torch.float64, pin_memory=True)
+    fh, uh = f_host.numpy(), u_host.numpy()
+    op.solve_host(fh, uh, rtol=rtol, maxit=1000)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_iters = []
+    for _ in range(args.steps):
+        _, inf = op.solve_host(fh, uh, rtol=rtol, maxit=1000)
+        e2e_iters.append(inf.iterations)
+    t1 = time.perf_counter()
+    e2e_s = (t1 - t0) / args.steps
+    e2e = {"value": ws * op.N * 2 * statistics.mean(e2e_iters) / e2e_s, "unit": "DoF/s",
+           "h2d_bytes_per_step": 8 * op.N, "d2h_bytes_per_step": 8 * op.N}
+
+    N, Nq = op.N, op.Nq
+    op.close()
+    del x, y, f, u
+    torch.cuda.empty_cache()
+
+    extras = {}
+    if not args.no_extras:
+        extras["p_sweep_nel128"] = p_sweep(mf, device)
+        extras["mixed_vs_fp64"] = mixed_vs_fp64(mf, device)
+    line = {
+        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD["name"], "p": p, "nel": nel, "N": N, "Nq": Nq, "rtol": rtol,
+                   "step": "one FD-preconditioned BiCGStab solve from u=0", "l2": "inputs larger than L2 (C alone 873 MB)",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "solve": {"time_s": ms_step / 1e3, "iterations": statistics.mean(iters), "rel_residual": info.rel_residual},
+        "apply_only": {"ms": apply_ms, "dof_per_s": N / (apply_ms * 1e-3)},
+        "fd_precond_ms": fd_ms,
+        "stages_ms_per_launch": {k: v[0] / v[1] for k, v in stages.items()},
+        "stages_share": {k: v[0] / sum(s[0] for s in stages.values()) for k, v in stages.items()},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    line.update(extras)
+    if rank == 0 and not args.no_extras:
+        line["cpu_baseline"] = {k: v for k, v in oracle_iteration_sample(1).items() if k in ("value", "unit", "cores", "kind", "sample")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,231 @@
+/*
+ * mfwq.h -- C ABI of the GB300 (sm_103a) matrix-free weighted-quadrature
+ * (MF-WQ) isogeometric k-method library.
+ *
+ * The operator is the weighted-quadrature stiffness of Sangalli & Tani,
+ * "Matrix-free weighted quadrature for a computationally efficient
+ * isogeometric k-method", applied matrix-free through the factorisation
+ *     K~ = sum_{alpha,beta=1..3} W^(alpha,beta) D^(alpha,beta) B^(beta)
+ * of Section 3.2 (Algorithm 2), preconditioned by the Fast Diagonalization
+ * (FD) method and solved with BiCGStab (Section 4).
+ *
+ * Conventions shared by every call
+ *  - Tensors of degrees of freedom (DoFs) have n1*n2*n3 entries stored as a
+ *    C array [i3][i2][i1] (direction 1 fastest, Eq. (ordering) and the scalar
+ *    index of Section 2.1).  Quadrature-point tensors have nq1*nq2*nq3 entries
+ *    stored [q3][q2][q1].  n_l = (number of B-splines in direction l) - 2
+ *    (homogeneous Dirichlet, Section 2.1); nq_l = 2*nel_l + 2*p_l - 1 (the WQ
+ *    point rule of Section 2.2: every interior knot, every interior-span
+ *    midpoint, p+1 equispaced points inside the first and the last span).
+ *  - The symmetric coefficient C = |det J| J^-1 K J^-T (Eq. (C), J_ij =
+ *    dF_i/dxi_j) is stored as 6 fields [6][nq3][nq2][nq1] in the order
+ *    C11, C22, C33, C12, C13, C23 (Section 3.2: d(d+1)/2 fields suffice).
+ *  - Pointers named *_dev are device pointers owned by the caller, at least
+ *    16-byte aligned; input and output buffers of one call must not overlap.
+ *    Pointers named *_host are host pointers.
+ *  - Work is enqueued on the stream given at setup.  Calls documented as
+ *    "asynchronous" return after enqueueing; launch errors are reported at
+ *    once, and nothing else can fail on the device.  Calls documented as
+ *    "synchronous" wait for the stream.
+ *  - Every call returns an MFWQ_* status; nothing aborts, traps or throws.
+ *  - A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef MFWQ_H
+#define MFWQ_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define MFWQ_OK          0
+#define MFWQ_EINVAL     -1  /* bad argument: size, degree, knot vector, NULL, alignment */
+#define MFWQ_ENOMEM     -2  /* a device or host allocation failed */
+#define MFWQ_ECUDA      -3  /* a CUDA runtime call or kernel launch failed */
+#define MFWQ_ESETUP     -4  /* a weight system was inconsistent or an eigensolve failed */
+#define MFWQ_EBREAKDOWN -5  /* BiCGStab breakdown: rho, r^.v or omega vanished */
+#define MFWQ_ENOCONV    -6  /* the solve did not reach rtol within maxit */
+#define MFWQ_ETIMEOUT   -7  /* a bounded device-side wait gave up */
+#define MFWQ_ENAN       -8  /* a NaN or Inf appeared in a Krylov scalar */
+#define MFWQ_EINTERNAL  -9
+
+/* ---- enumerations -------------------------------------------------------- */
+#define MFWQ_FD_FP64 0  /* FD mode products in FP64 (FP64 pipe) */
+#define MFWQ_FD_TF32 1  /* FD mode products on tensor cores, TF32 inputs, FP32 accumulate */
+#define MFWQ_FD_BF16 2  /* FD mode products on tensor cores, BF16 inputs, FP32 accumulate */
+
+#define MFWQ_GEOM_CUBE 0  /* F = identity on [0,1]^3 */
+#define MFWQ_GEOM_RING 1  /* thick quarter ring of Section 4, exact polar map
+                             F(xi) = ((1+xi1) cos(pi xi2/2), (1+xi1) sin(pi xi2/2), xi3) */
+
+#define MFWQ_FORCING_SINES      0  /* f = 3 pi^2 sin(pi x1) sin(pi x2) sin(pi x3) */
+#define MFWQ_FORCING_RING_EXACT 1  /* f = -Laplace u for Eq. (exact-solution) */
+
+typedef struct mfwq_handle_s* mfwq_handle;
+
+/* ---- setup --------------------------------------------------------------- */
+typedef struct {
+    int degree[3];            /* p_l >= 2, <= 12 (C^{p-1} splines, Section 2.1) */
+    int nknots[3];            /* length of knots[l] = nel_l + 2 p_l + 1 */
+    const double* knots[3];   /* host; open knot vector on [0,1]: p+1 zeros, strictly
+                                 increasing interior knots (multiplicity 1), p+1 ones */
+    int mixed;                /* 0: FP64 operator and FP64 FD only.
+                                 1: also build the FP32 operator and the tensor-core FD
+                                 used by the mixed-precision refinement of mfwq_solve. */
+    int fd_precision;         /* FD precision of the mixed inner solve: MFWQ_FD_TF32 or
+                                 MFWQ_FD_BF16 (ignored when mixed = 0) */
+    void* stream;             /* cudaStream_t all work is enqueued on (NULL = legacy) */
+} mfwq_setup_desc;
+
+/* Builds the 1D tables of Algorithm 2's setup on the host (B-spline values and
+ * derivatives at the WQ points, Eq. (Bl); the four weight families per
+ * direction, Eq. (exactness1d)/(exactness_K)/(weights-support) solved in the
+ * minimum-2-norm sense; the FD factors U_l, lambda_l of the generalized
+ * eigenproblem K_l U = M_l U Lambda), uploads them and allocates the handle's
+ * device workspace.  The coefficient must then be given with mfwq_set_coeff.
+ * Returns MFWQ_EINVAL for a bad descriptor, MFWQ_ESETUP if a weight system is
+ * inconsistent, MFWQ_ENOMEM / MFWQ_ECUDA on device failures.  Synchronous. */
+int mfwq_setup(const mfwq_setup_desc* desc, mfwq_handle* out);
+
+/* Frees everything the handle owns.  NULL is allowed. */
+void mfwq_destroy(mfwq_handle h);
+
+/* Static text for a status code. */
+const char* mfwq_status_string(int status);
+
+/* Message describing the last failure of a call made from this thread (empty
+ * if none).  The pointer stays valid until the next failing call. */
+const char* mfwq_last_error(void);
+
+/* n[l] = DoFs and nq[l] = WQ points in direction l (either may be NULL). */
+int mfwq_sizes(mfwq_handle h, int n[3], int nq[3]);
+
+/* WQ points of direction dir (0, 1, 2) into xq_host[nq[dir]]. */
+int mfwq_quad_points(mfwq_handle h, int dir, double* xq_host);
+
+/* Host-only (no CUDA call): the 1D tables for one direction, dense, for
+ * inspection and tests.  Pass NULL for any output not wanted; *n and *nq are
+ * always written.  xq[nq]; B0, B1 [nq][n] (row q, column j); W [4][n][nq]
+ * with family index 2a+b of the pair (a, b) (a: derivative order of the test
+ * function, b: of the trial function); U [n][n] (column k = k-th eigenvector,
+ * U^T M U = I) and lam[n] of the FD factorisation. */
+int mfwq_tables_1d(int degree, int nknots, const double* knots, int* n, int* nq,
+                   double* xq, double* B0, double* B1, double* W, double* U, double* lam);
+
+/* ---- coefficient and right-hand side (setup helpers, not the hot path) ---- */
+/* C_dev[6][nq3][nq2][nq1] = C at the WQ points for the given geometry and
+ * K(x) = exp(kscale * g(x)) I, g(x) = sum_m a_m cos(2 pi k_m . x + phi_m) in
+ * physical coordinates.  modes_host holds nmodes rows (a, k1, k2, k3, phi)
+ * (nmodes <= 32; nmodes = 0 gives K = I).  Asynchronous. */
+int mfwq_eval_coeff(mfwq_handle h, int geometry, const double* modes_host, int nmodes,
+                    double kscale, double* C_dev);
+
+/* Copies C_dev[6][Nq] into the handle (and an FP32 copy when mixed).  The
+ * caller's buffer may be reused afterwards.  Asynchronous. */
+int mfwq_set_coeff(mfwq_handle h, const double* C_dev);
+
+/* Load vector f_i = int |det J| b_i (f o F) dxi (Eq. (linearsystem)) by
+ * tensor Gauss quadrature with p+1 points per span.  Asynchronous. */
+int mfwq_load_vector(mfwq_handle h, int geometry, int forcing, double* f_dev);
+
+/* ---- hot path ------------------------------------------------------------ */
+/* y = K~ x, FP64 (Algorithm 2, sum-factorised).  x_dev, y_dev: [n3][n2][n1].
+ * Uses the handle's workspace, so calls on one handle must not overlap on the
+ * device.  Asynchronous. */
+int mfwq_apply(mfwq_handle h, const double* x_dev, double* y_dev);
+
+/* y = K~^T x = sum B^(beta)^T D^(alpha,beta) W^(alpha,beta)^T x, FP64 (the WQ
+ * matrix is not symmetric, Section 4).  Asynchronous. */
+int mfwq_apply_T(mfwq_handle h, const double* x_dev, double* y_dev);
+
+/* y = K~ x in FP32 (FP32 tables and coefficient; needs mixed = 1). */
+int mfwq_apply_f32(mfwq_handle h, const float* x_dev, float* y_dev);
+
+/* z = P^-1 r, FD preconditioner in FP64: P = M3(x)M2(x)K1 + M3(x)K2(x)M1 +
+ * K3(x)M2(x)M1, P^-1 = (U3(x)U2(x)U1) diag(1/(l1_i+l2_j+l3_k)) (U3(x)U2(x)U1)^T.
+ * Asynchronous. */
+int fd_precond(mfwq_handle h, const double* r_dev, double* z_dev);
+
+/* z = P^-1 r in the handle's low precision (TF32 or BF16 tensor-core mode
+ * products, FP32 accumulate, FP32 in and out; needs mixed = 1). */
+int fd_precond_f32(mfwq_handle h, const float* r_dev, float* z_dev);
+
+typedef struct {
+    double rtol;           /* stop when ||f - K~ u||_2 <= rtol ||f||_2 */
+    int maxit;             /* BiCGStab iterations (outer refinement steps when mixed) */
+    double inner_rtol;     /* mixed: relative tolerance of each inner FP32 solve (0: 1e-4) */
+    int inner_maxit;       /* mixed: iteration cap of each inner solve (0: 200) */
+    int use_initial_guess; /* 0: start from u = 0; 1: u_dev holds the initial guess */
+    int force_fp64;        /* 1: plain FP64 solve even on a mixed handle */
+    double* res_hist;      /* host, may be NULL: relative residual after each iteration
+                              (maxit + 1 entries) */
+} mfwq_solve_opts;
+
+typedef struct {
+    int status;            /* MFWQ_OK, MFWQ_ENOCONV, MFWQ_EBREAKDOWN, MFWQ_ENAN */
+    int iterations;        /* BiCGStab iterations (summed over inner solves when mixed) */
+    int outer_iterations;  /* refinement steps (mixed), else 0 */
+    double rel_residual;   /* last ||f - K~ u|| / ||f|| (FP64 residual) */
+} mfwq_solve_info;
+
+/* Solves K~ u = f with right-FD-preconditioned BiCGStab (Section 4): FP64
+ * throughout, or -- on a mixed handle -- FP64 iterative refinement around
+ * inner FP32 BiCGStab solves (FP32 operator, tensor-core FD, FP64 dot
+ * products).  f_dev, u_dev: [n3][n2][n1].  Synchronous; returns info->status. */
+int mfwq_solve(mfwq_handle h, const double* f_dev, double* u_dev,
+               const mfwq_solve_opts* opts, mfwq_solve_info* info);
+
+/* Solves the adjoint system K~^T lambda = g (FD is symmetric, so the same
+ * preconditioner serves).  FP64.  Synchronous. */
+int mfwq_solve_T(mfwq_handle h, const double* g_dev, double* lambda_dev,
+                 const mfwq_solve_opts* opts, mfwq_solve_info* info);
+
+/* mfwq_solve with host buffers: copies f_host to the device, solves, copies
+ * u back into u_host (both [n3][n2][n1]).  Synchronous. */
+int mfwq_solve_host(mfwq_handle h, const double* f_host, double* u_host,
+                    const mfwq_solve_opts* opts, mfwq_solve_info* info);
+
+/* Gradient of J with respect to the stored coefficient fields, given the
+ * state u (K~ u = f) and the adjoint lambda (K~^T lambda = dJ/du).  Because
+ * K~ is linear in every C_ab(x_q) (Section 3.2),
+ *   dJ/dC_ab(q) = -(W^(ab)^T lambda)_q (B^(b) u)_q,
+ * and the symmetric slot of an off-diagonal pair receives the sum of both
+ * orderings.  gC_dev: [6][nq3][nq2][nq1].  The quadrature-point gradients
+ * B^(b) u are recomputed, not stored.  Asynchronous. */
+int mfwq_grad_coeff(mfwq_handle h, const double* lambda_dev, const double* u_dev, double* gC_dev);
+
+/* Waits for the handle's stream and reports any failure seen since the last call. */
+int mfwq_sync(mfwq_handle h);
+
+/* ---- instrumentation (no counterpart in the paper) -------------------------
+ * Kernel stages, in the index order of mfwq_profile_stats: trial_z, trial_y,
+ * xstage, test_y, test_z (the five stages of the apply), test_zT, test_yT,
+ * xstage_T, trial_yT, trial_zT (the transpose), xstage_grad, fd_dim1,
+ * fd_dim23, fd_tc (FD mode products), krylov (BiCGStab vector and scalar
+ * kernels), setup. */
+#define MFWQ_NSTAGES 16
+typedef struct {
+    double ms[MFWQ_NSTAGES];           /* summed device time per stage (CUDA events) */
+    long long launches[MFWQ_NSTAGES];  /* kernel launches per stage */
+} mfwq_profile_stats;
+
+/* With on = 1, every kernel the handle launches afterwards is bracketed by
+ * CUDA events on the handle's stream (a few microseconds per launch). */
+int mfwq_profile_enable(mfwq_handle h, int on);
+
+/* Waits for the recorded events and sums them per stage; reset = 1 clears the
+ * totals afterwards.  Synchronous. */
+int mfwq_profile_read(mfwq_handle h, mfwq_profile_stats* out, int reset);
+
+/* Name of a stage index ("" if out of range). */
+const char* mfwq_stage_name(int stage);
+
+/* Kernels launched by the library in this process so far (all handles). */
+long long mfwq_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MFWQ_H */

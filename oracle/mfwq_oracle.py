@@ -42,6 +42,7 @@ from __future__ import annotations
 
 import math
 from dataclasses import dataclass, field
+from decimal import Decimal, localcontext
 
 import numpy as np
 import scipy.linalg
@@ -161,19 +162,204 @@ def wq_points(knots, p: int) -> np.ndarray:
     return np.array(pts)
 
 
-def wq_weights(knots, p: int, xq, a: int, b: int) -> np.ndarray:
-    """Weights W (n x n_q) of the 1D family (a, b).
+# The weight systems are ill-conditioned for larger p (condition numbers near
+# 1e9 at p = 6 and 1e11 at p = 8 with the points of reading R1), so float64
+# solves of them agree only to about kappa * 1e-16.  The oracle therefore
+# computes the minimum-norm solution in 80-digit decimal arithmetic from the
+# exact binary values of the knots, and rounds the result to float64 once.
+_DPREC = 80
+
+
+def _dec(x):
+    return Decimal(float(x))
+
+
+def _dec_points(tD, p):
+    """Reading R1 in decimal arithmetic (same points as wq_points)."""
+    u = sorted(set(tD))
+    nel = len(u) - 1
+    pts = [u[0] + (u[1] - u[0]) * k / (p + 2) for k in range(1, p + 2)]
+    for s in range(1, nel - 1):
+        pts.append(u[s])
+        pts.append((u[s] + u[s + 1]) / 2)
+    if nel >= 2:
+        pts.append(u[nel - 1])
+        pts.extend(u[nel - 1] + (u[nel] - u[nel - 1]) * k / (p + 2) for k in range(1, p + 2))
+    return pts
+
+
+def _dec_basis(tD, p, x):
+    """All B-splines of degree p and their derivatives at one decimal point x,
+    by the Cox-de Boor definition; returns dicts index -> value."""
+    nb = len(tD) - 1
+    nonempty = [i for i in range(nb) if tD[i] < tD[i + 1]]
+    N = {}
+    for i in nonempty:
+        if tD[i] <= x < tD[i + 1] or (i == nonempty[-1] and x == tD[i + 1]):
+            N[i] = Decimal(1)
+    low = N
+    for k in range(1, p + 1):
+        M = {}
+        for i in range(len(tD) - k - 1):
+            v = Decimal(0)
+            d1 = tD[i + k] - tD[i]
+            d2 = tD[i + k + 1] - tD[i + 1]
+            if d1 > 0 and i in N:
+                v += (x - tD[i]) / d1 * N[i]
+            if d2 > 0 and (i + 1) in N:
+                v += (tD[i + k + 1] - x) / d2 * N[i + 1]
+            if v != 0:
+                M[i] = v
+        if k == p:
+            low = N
+        N = M
+    D = {}
+    for i in range(len(tD) - p - 1):
+        v = Decimal(0)
+        d1 = tD[i + p] - tD[i]
+        d2 = tD[i + p + 1] - tD[i + 1]
+        if d1 > 0 and i in low:
+            v += p * low[i] / d1
+        if d2 > 0 and (i + 1) in low:
+            v -= p * low[i + 1] / d2
+        if v != 0:
+            D[i] = v
+    return N, D
+
+
+def _dec_gauss(k):
+    """Gauss-Legendre nodes/weights on [-1, 1], Newton's method in decimal."""
+    g0, _ = np.polynomial.legendre.leggauss(k)
+    nodes, weights = [], []
+    for z0 in g0:
+        z = Decimal(float(z0))
+        for _ in range(8):
+            p0, p1 = Decimal(1), z
+            for j in range(2, k + 1):
+                p0, p1 = p1, ((2 * j - 1) * z * p1 - (j - 1) * p0) / j
+            dp = k * (z * p1 - p0) / (z * z - 1)
+            z = z - p1 / dp
+        p0, p1 = Decimal(1), z
+        for j in range(2, k + 1):
+            p0, p1 = p1, ((2 * j - 1) * z * p1 - (j - 1) * p0) / j
+        dp = k * (z * p1 - p0) / (z * z - 1)
+        nodes.append(z)
+        weights.append(2 / ((1 - z * z) * dp * dp))
+    return nodes, weights
+
+
+def _dec_independent_rows(A):
+    """Indices of rows of A that are not combinations of earlier kept rows
+    (Gaussian elimination with column pivoting; a remaining row whose largest
+    entry falls below 1e-40 of the largest entry of A is dependent)."""
+    big = max(abs(v) for row in A for v in row)
+    basis = []  # (pivot column, reduced row)
+    keep = []
+    for i, row in enumerate(A):
+        r = list(row)
+        for col, b in basis:
+            f = r[col] / b[col]
+            if f != 0:
+                r = [x - f * y for x, y in zip(r, b)]
+        col = max(range(len(r)), key=lambda k: abs(r[k]))
+        if abs(r[col]) > big * Decimal("1e-40"):
+            basis.append((col, r))
+            keep.append(i)
+    return keep
+
+
+def _dec_min_norm(A, g):
+    """Minimum-2-norm solution of the consistent system A w = g (A: list of
+    rows): w = A_r^T (A_r A_r^T)^-1 g_r over the independent rows A_r (the
+    dependent equations hold for every solution of the others)."""
+    keep = _dec_independent_rows(A)
+    Ar = [A[i] for i in keep]
+    gr = [g[i] for i in keep]
+    r = len(Ar)
+    c = len(Ar[0])
+    G = [[sum(Ar[i][k] * Ar[j][k] for k in range(c)) for j in range(r)] for i in range(r)]
+    # Cholesky G = L L^T, then L L^T z = g_r
+    L = [[Decimal(0)] * r for _ in range(r)]
+    for j in range(r):
+        d = G[j][j] - sum(L[j][k] * L[j][k] for k in range(j))
+        L[j][j] = d.sqrt()
+        for i in range(j + 1, r):
+            L[i][j] = (G[i][j] - sum(L[i][k] * L[j][k] for k in range(j))) / L[j][j]
+    y = [Decimal(0)] * r
+    for i in range(r):
+        y[i] = (gr[i] - sum(L[i][k] * y[k] for k in range(i))) / L[i][i]
+    z = [Decimal(0)] * r
+    for i in reversed(range(r)):
+        z[i] = (y[i] - sum(L[k][i] * z[k] for k in range(i + 1, r))) / L[i][i]
+    return [sum(Ar[i][k] * z[i] for i in range(r)) for k in range(c)]
+
+
+def wq_weights_all(knots, p: int):
+    """The four 1D weight families {(a, b): W (n x n_q)}.
 
     Row i solves Eq. (exactness1d) / the 1D form of Eq. (exactness_K),
     int b_i^(a) b_j^(b) = sum_q w_iq b_j^(b)(x_q) for every interior j, with
     w_iq = 0 unless x_q lies in the open support of b_i (Eq. (weights-support),
     reading R3).  Equations for |j - i| > p hold trivially (both sides vanish),
-    the rest are solved in the minimum-2-norm sense (reading R2).
+    the rest are solved in the minimum-2-norm sense (reading R2); the
+    integrals use Gauss-Legendre with p+1 points per span (exact).
     """
+    with localcontext() as ctx:
+        ctx.prec = _DPREC
+        tD = [_dec(v) for v in knots]
+        m = len(tD) - p - 1
+        n = m - 2
+        xq = _dec_points(tD, p)
+        nq = len(xq)
+        at_q = [_dec_basis(tD, p, x) for x in xq]
+        u = sorted(set(tD))
+        gn, gw = _dec_gauss(p + 1)
+        gauss = []  # (weight, (N, D)) over all spans
+        for s in range(len(u) - 1):
+            a0, b0 = u[s], u[s + 1]
+            for z, w in zip(gn, gw):
+                x = (a0 + b0) / 2 + (b0 - a0) / 2 * z
+                gauss.append(((b0 - a0) / 2 * w, _dec_basis(tD, p, x)))
+
+        def integral(i, a, j, b):
+            tot = Decimal(0)
+            for w, (N, D) in gauss:
+                fa = (D if a else N).get(i)
+                fb = (D if b else N).get(j)
+                if fa is not None and fb is not None:
+                    tot += w * fa * fb
+            return tot
+
+        out = {(a, b): np.zeros((n, nq)) for a in (0, 1) for b in (0, 1)}
+        for i in range(n):
+            gi = i + 1
+            S = [q for q in range(nq) if tD[gi] < xq[q] < tD[gi + p + 1]]
+            T = [j for j in range(n) if abs(j - i) <= p]
+            for b in (0, 1):
+                A = [[(at_q[q][1] if b else at_q[q][0]).get(j + 1, Decimal(0)) for q in S] for j in T]
+                for a in (0, 1):
+                    rhs = [integral(gi, a, j + 1, b) for j in T]
+                    w = _dec_min_norm(A, rhs)
+                    res = max(abs(sum(A[r][k] * w[k] for k in range(len(S))) - rhs[r]) for r in range(len(T)))
+                    if res > Decimal("1e-40") * max(abs(v) for v in rhs):
+                        raise ValueError(f"WQ system of row {i} is inconsistent")
+                    out[(a, b)][i, S] = [float(v) for v in w]
+    return out
+
+
+def wq_weights(knots, p: int, xq, a: int, b: int) -> np.ndarray:
+    """One weight family (a, b) (see wq_weights_all); xq must be wq_points(knots, p)."""
+    W = wq_weights_all(knots, p)[(a, b)]
+    assert W.shape[1] == len(xq)
+    return W
+
+
+def wq_weights_float64(knots, p: int, xq, a: int, b: int) -> np.ndarray:
+    """Same systems solved in float64 by numpy's lstsq (a cross-check that is
+    accurate only while the systems are well conditioned, p <= 4)."""
     t = np.asarray(knots, dtype=np.float64)
     xq = np.asarray(xq, dtype=np.float64)
-    m = num_functions(t, p)
-    n = m - 2
+    n = num_functions(t, p) - 2
     val, der = bspline_basis(t, p, xq)
     Fb = der if b else val
     G = galerkin_1d(t, p, a, b)
@@ -182,16 +368,7 @@ def wq_weights(knots, p: int, xq, a: int, b: int) -> np.ndarray:
         gi = i + 1
         S = np.nonzero((xq > t[gi]) & (xq < t[gi + p + 1]))[0]
         T = np.array([j for j in range(n) if abs(j - i) <= p])
-        A = Fb[np.ix_(S, T + 1)].T
-        rhs = G[i, T]
-        # For b = 1 the rows are dependent in the interior (the interior
-        # B-splines sum to one on supp b_i, so their derivatives sum to zero);
-        # the system stays consistent and lstsq returns its minimum-norm solution.
-        w = np.linalg.lstsq(A, rhs, rcond=None)[0]
-        res = np.linalg.norm(A @ w - rhs)
-        if res > 1e-11 * max(np.linalg.norm(rhs), 1e-300):
-            raise ValueError(f"WQ system of row {i} is inconsistent (residual {res:.3e})")
-        W[i, S] = w
+        W[i, S] = np.linalg.lstsq(Fb[np.ix_(S, T + 1)].T, G[i, T], rcond=None)[0]
     return W
 
 
@@ -222,10 +399,14 @@ def tables_1d(knots, p: int) -> Tables1D:
     val, der = bspline_basis(t, p, xq)
     m = val.shape[1]
     tab = Tables1D(p=p, knots=t, xq=xq, B0=val[:, 1:m - 1].copy(), B1=der[:, 1:m - 1].copy())
-    for a in (0, 1):
-        for b in (0, 1):
-            tab.W[(a, b)] = wq_weights(t, p, xq, a, b)
+    key = (p, t.tobytes())
+    if key not in _WEIGHT_CACHE:
+        _WEIGHT_CACHE[key] = wq_weights_all(t, p)
+    tab.W = {k: v.copy() for k, v in _WEIGHT_CACHE[key].items()}
     return tab
+
+
+_WEIGHT_CACHE = {}
 
 
 def uniform_tables(p, nel):

@@ -1,0 +1,557 @@
+// C ABI of the MF-WQ library (include/mfwq.h): handle, device memory, and the
+// drivers that chain the kernels of Algorithm 2, the FD preconditioner and
+// BiCGStab (Section 4).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "krylov.h"
+#include "prof.h"
+
+using namespace mfwq;
+
+namespace {
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& why) {
+    g_last_error = why;
+    return code;
+}
+
+#define CU(x)                                                                                    \
+    do {                                                                                         \
+        cudaError_t _e = (x);                                                                    \
+        if (_e != cudaSuccess) return fail(MFWQ_ECUDA, std::string(#x) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+#define ST(x)                          \
+    do {                               \
+        int _st = (x);                 \
+        if (_st != MFWQ_OK) return _st; \
+    } while (0)
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Host staging of all device tables in one allocation.
+struct Arena {
+    std::vector<unsigned char> bytes;
+    size_t add(const void* src, size_t n) {
+        size_t off = (bytes.size() + 255) & ~(size_t)255;
+        bytes.resize(off + (n ? n : 1));
+        if (n) std::memcpy(bytes.data() + off, src, n);
+        return off;
+    }
+    template <typename T>
+    size_t add_vec(const std::vector<T>& v) {
+        return add(v.data(), v.size() * sizeof(T));
+    }
+};
+
+template <typename T>
+std::vector<T> convert(const std::vector<double>& v) {
+    return std::vector<T>(v.begin(), v.end());
+}
+
+struct BandOff {
+    size_t start, len, v64, v32;
+    int rows, width;
+};
+
+BandOff stage_band(Arena& a, const Band1D& b) {
+    BandOff o;
+    o.start = a.add_vec(b.start);
+    o.len = a.add_vec(b.len);
+    o.v64 = a.add_vec(b.val);
+    o.v32 = a.add_vec(convert<float>(b.val));
+    o.rows = b.rows;
+    o.width = b.width;
+    return o;
+}
+
+template <typename T>
+BandD<T> band_at(unsigned char* base, const BandOff& o) {
+    BandD<T> b;
+    b.start = reinterpret_cast<const int*>(base + o.start);
+    b.len = reinterpret_cast<const int*>(base + o.len);
+    b.val = reinterpret_cast<const T*>(base + (sizeof(T) == 8 ? o.v64 : o.v32));
+    b.rows = o.rows;
+    b.width = o.width;
+    return b;
+}
+
+}  // namespace
+
+struct mfwq_handle_s {
+    cudaStream_t stream = nullptr;
+    int mixed = 0, fd_prec = MFWQ_FD_FP64;
+    Dir1D dir[3];
+    int n[3], nq[3], ng[3];
+    size_t N = 0, Nq = 0;
+    unsigned char* d_tables = nullptr;
+    DirD<double> d64[3];
+    DirD<float> d32[3];
+    double* C64 = nullptr;
+    float* C32 = nullptr;
+    void* scratch = nullptr;
+    double* fd_tmp64 = nullptr;
+    float* fd_tmp32 = nullptr;
+    double* kv64 = nullptr;  // 8 N
+    float* kv32 = nullptr;   // 10 N (8 Krylov + rhs + correction)
+    double* part = nullptr;  // 2 kRedBlocks
+    double* dnorm = nullptr; // 2 doubles
+    KScal* dsc = nullptr;
+    KScal* hsc = nullptr;    // pinned
+    Profiler prof;
+    double* hnorm = nullptr; // pinned, 2 doubles
+    double* host_io = nullptr;  // device f/u buffers of mfwq_solve_host (2 N), lazily
+};
+
+namespace {
+
+OpCtx<double> ctx64(mfwq_handle h) {
+    OpCtx<double> c;
+    for (int l = 0; l < 3; ++l) c.d[l] = h->d64[l];
+    c.C = h->C64;
+    c.Nq = h->Nq;
+    c.scratch = static_cast<double*>(h->scratch);
+    c.stream = h->stream;
+    return c;
+}
+
+OpCtx<float> ctx32(mfwq_handle h) {
+    OpCtx<float> c;
+    for (int l = 0; l < 3; ++l) c.d[l] = h->d32[l];
+    c.C = h->C32;
+    c.Nq = h->Nq;
+    c.scratch = static_cast<float*>(h->scratch);
+    c.stream = h->stream;
+    return c;
+}
+
+void free_handle(mfwq_handle h) {
+    if (!h) return;
+    cudaFree(h->d_tables);
+    cudaFree(h->C64);
+    cudaFree(h->C32);
+    cudaFree(h->scratch);
+    cudaFree(h->fd_tmp64);
+    cudaFree(h->fd_tmp32);
+    cudaFree(h->kv64);
+    cudaFree(h->kv32);
+    cudaFree(h->part);
+    cudaFree(h->dnorm);
+    cudaFree(h->dsc);
+    cudaFree(h->host_io);
+    if (h->hsc) cudaFreeHost(h->hsc);
+    if (h->hnorm) cudaFreeHost(h->hnorm);
+    delete h;
+}
+
+int dmalloc(void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MFWQ_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    return MFWQ_OK;
+}
+
+int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
+    h->stream = static_cast<cudaStream_t>(desc->stream);
+    h->mixed = desc->mixed ? 1 : 0;
+    h->fd_prec = h->mixed ? desc->fd_precision : MFWQ_FD_FP64;
+    if (h->mixed && h->fd_prec != MFWQ_FD_TF32 && h->fd_prec != MFWQ_FD_BF16)
+        return fail(MFWQ_EINVAL, "fd_precision must be MFWQ_FD_TF32 or MFWQ_FD_BF16 when mixed = 1");
+    for (int l = 0; l < 3; ++l) {
+        std::string why;
+        int st = build_dir(desc->degree[l], desc->nknots[l], desc->knots[l], h->dir[l], why);
+        if (st != MFWQ_OK) return fail(st, "direction " + std::to_string(l + 1) + ": " + why);
+        h->n[l] = h->dir[l].n;
+        h->nq[l] = h->dir[l].nq;
+        h->ng[l] = h->dir[l].ng;
+    }
+    h->N = (size_t)h->n[0] * h->n[1] * h->n[2];
+    h->Nq = (size_t)h->nq[0] * h->nq[1] * h->nq[2];
+    if (h->Nq * 9 >= ((size_t)1 << 40)) return fail(MFWQ_EINVAL, "problem too large");
+
+    // ---- tables
+    Arena a;
+    BandOff bo[3][5];
+    size_t U64[3], UT64[3], L64[3], U32[3], UT32[3], L32[3], XQ[3], XG[3];
+    for (int l = 0; l < 3; ++l) {
+        const Dir1D& d = h->dir[l];
+        bo[l][0] = stage_band(a, d.B);
+        bo[l][1] = stage_band(a, d.BT);
+        bo[l][2] = stage_band(a, d.W);
+        bo[l][3] = stage_band(a, d.WT);
+        bo[l][4] = stage_band(a, d.GT);
+        U64[l] = a.add_vec(d.U);
+        UT64[l] = a.add_vec(d.UT);
+        L64[l] = a.add_vec(d.lam);
+        U32[l] = a.add_vec(convert<float>(d.U));
+        UT32[l] = a.add_vec(convert<float>(d.UT));
+        L32[l] = a.add_vec(convert<float>(d.lam));
+        XQ[l] = a.add_vec(d.xq);
+        XG[l] = a.add_vec(d.xg);
+    }
+    ST(dmalloc((void**)&h->d_tables, a.bytes.size()));
+    CU(cudaMemcpy(h->d_tables, a.bytes.data(), a.bytes.size(), cudaMemcpyHostToDevice));
+    unsigned char* base = h->d_tables;
+    for (int l = 0; l < 3; ++l) {
+        DirD<double>& x = h->d64[l];
+        DirD<float>& y = h->d32[l];
+        x.n = y.n = h->n[l];
+        x.nq = y.nq = h->nq[l];
+        x.ng = y.ng = h->ng[l];
+        x.B = band_at<double>(base, bo[l][0]);
+        x.BT = band_at<double>(base, bo[l][1]);
+        x.W = band_at<double>(base, bo[l][2]);
+        x.WT = band_at<double>(base, bo[l][3]);
+        x.GT = band_at<double>(base, bo[l][4]);
+        y.B = band_at<float>(base, bo[l][0]);
+        y.BT = band_at<float>(base, bo[l][1]);
+        y.W = band_at<float>(base, bo[l][2]);
+        y.WT = band_at<float>(base, bo[l][3]);
+        y.GT = band_at<float>(base, bo[l][4]);
+        x.U = reinterpret_cast<const double*>(base + U64[l]);
+        x.UT = reinterpret_cast<const double*>(base + UT64[l]);
+        x.lam = reinterpret_cast<const double*>(base + L64[l]);
+        y.U = reinterpret_cast<const float*>(base + U32[l]);
+        y.UT = reinterpret_cast<const float*>(base + UT32[l]);
+        y.lam = reinterpret_cast<const float*>(base + L32[l]);
+        x.xq = y.xq = reinterpret_cast<const double*>(base + XQ[l]);
+        x.xg = y.xg = reinterpret_cast<const double*>(base + XG[l]);
+    }
+
+    // ---- coefficient, workspace
+    ST(dmalloc((void**)&h->C64, sizeof(double) * 6 * h->Nq));
+    CU(cudaMemset(h->C64, 0, sizeof(double) * 6 * h->Nq));
+    if (h->mixed) {
+        ST(dmalloc((void**)&h->C32, sizeof(float) * 6 * h->Nq));
+        CU(cudaMemset(h->C32, 0, sizeof(float) * 6 * h->Nq));
+    }
+    size_t sc = apply_scratch_elems(h->n, h->nq);
+    size_t sr = rhs_scratch_elems(h->n, h->ng);
+    ST(dmalloc(&h->scratch, sizeof(double) * (sc > sr ? sc : sr)));
+    ST(dmalloc((void**)&h->fd_tmp64, sizeof(double) * h->N));
+    ST(dmalloc((void**)&h->kv64, sizeof(double) * 8 * h->N));
+    if (h->mixed) {
+        ST(dmalloc((void**)&h->fd_tmp32, sizeof(float) * h->N));
+        ST(dmalloc((void**)&h->kv32, sizeof(float) * 10 * h->N));
+    }
+    ST(dmalloc((void**)&h->part, sizeof(double) * 2 * kRedBlocks));
+    ST(dmalloc((void**)&h->dnorm, sizeof(double) * 2));
+    ST(dmalloc((void**)&h->dsc, sizeof(KScal)));
+    CU(cudaMallocHost((void**)&h->hsc, sizeof(KScal)));
+    CU(cudaMallocHost((void**)&h->hnorm, sizeof(double) * 2));
+
+    int smem = xstage_smem_bytes(8, h->n[0], h->nq[0]);
+    if (smem > 227 * 1024) return fail(MFWQ_EINVAL, "direction-1 size too large for the x-stage tile");
+    ST(configure_xstage_smem(smem));
+    CU(cudaDeviceSynchronize());
+    return MFWQ_OK;
+}
+
+KrylovBufs<double> bufs64(mfwq_handle h) {
+    double* v = h->kv64;
+    size_t N = h->N;
+    return KrylovBufs<double>{v, v + N, v + 2 * N, v + 3 * N, v + 4 * N, v + 5 * N, v + 6 * N, v + 7 * N};
+}
+
+KrylovBufs<float> bufs32(mfwq_handle h) {
+    float* v = h->kv32;
+    size_t N = h->N;
+    return KrylovBufs<float>{v, v + N, v + 2 * N, v + 3 * N, v + 4 * N, v + 5 * N, v + 6 * N, v + 7 * N};
+}
+
+mfwq_solve_opts default_opts() {
+    mfwq_solve_opts o;
+    std::memset(&o, 0, sizeof o);
+    o.rtol = 1e-10;
+    o.maxit = 500;
+    return o;
+}
+
+int solve64(mfwq_handle h, const double* f, double* u, const mfwq_solve_opts& o, mfwq_solve_info* info, bool transpose) {
+    OpCtx<double> c = ctx64(h);
+    LinOp<double> A = [c, transpose](const double* in, double* out, const int* skip) {
+        return transpose ? run_apply_T<double>(c, in, out, skip) : run_apply<double>(c, in, out, skip);
+    };
+    DirD<double> d[3] = {h->d64[0], h->d64[1], h->d64[2]};
+    double* tmp = h->fd_tmp64;
+    cudaStream_t s = h->stream;
+    LinOp<double> P = [d, tmp, s](const double* in, double* out, const int* skip) { return run_fd64(d, in, out, tmp, skip, s); };
+    int iters = 0, status = MFWQ_OK;
+    double rel = 0.0;
+    ST(bicgstab<double>(A, P, f, u, o.use_initial_guess != 0, o.rtol, o.maxit, bufs64(h), h->dsc, h->hsc, h->part, h->N, s,
+                        o.res_hist ? 1 : 4, o.res_hist, &iters, &rel, &status));
+    if (info) {
+        info->status = status;
+        info->iterations = iters;
+        info->outer_iterations = 0;
+        info->rel_residual = rel;
+    }
+    return status;
+}
+
+// FP64 iterative refinement around inner FP32 BiCGStab solves.
+int solve_mixed(mfwq_handle h, const double* f, double* u, const mfwq_solve_opts& o, mfwq_solve_info* info) {
+    const size_t N = h->N;
+    cudaStream_t s = h->stream;
+    OpCtx<double> c64 = ctx64(h);
+    OpCtx<float> c32 = ctx32(h);
+    double* w64 = h->kv64;       // K~ u
+    double* r64 = h->kv64 + N;   // f - K~ u
+    float* r32 = h->kv32 + 8 * N;
+    float* d32 = h->kv32 + 9 * N;
+    DirD<float> d[3] = {h->d32[0], h->d32[1], h->d32[2]};
+    float* tmp = h->fd_tmp32;
+    LinOp<float> A = [c32](const float* in, float* out, const int* skip) { return run_apply<float>(c32, in, out, skip); };
+    LinOp<float> P = [d, tmp, s](const float* in, float* out, const int* skip) { return run_fd32_simt(d, in, out, tmp, skip, s); };
+    const double inner_rtol = o.inner_rtol > 0 ? o.inner_rtol : 1e-4;
+    const int inner_maxit = o.inner_maxit > 0 ? o.inner_maxit : 200;
+    if (!o.use_initial_guess) CU(cudaMemsetAsync(u, 0, sizeof(double) * N, s));
+    ST(norm2_into(f, N, h->part, h->dnorm + 1, s));
+    int outer = 0, inner_total = 0, status = MFWQ_ENOCONV;
+    double rel = 1.0;
+    for (;;) {
+        ST(run_apply<double>(c64, u, w64, nullptr));
+        ST(axpby_into<double>(f, w64, r64, N, s));
+        ST(norm2_into(r64, N, h->part, h->dnorm, s));
+        CU(cudaMemcpyAsync(h->hnorm, h->dnorm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        const double r2 = h->hnorm[0], f2 = h->hnorm[1];
+        if (!std::isfinite(r2)) { status = MFWQ_ENAN; break; }
+        rel = f2 > 0 ? std::sqrt(r2 / f2) : 0.0;
+        if (o.res_hist) o.res_hist[outer] = rel;
+        if (f2 == 0.0 || rel <= o.rtol) { status = MFWQ_OK; break; }
+        if (outer >= o.maxit) break;
+        ST(to_f32_scaled(r64, h->dnorm, r32, N, s));
+        int it = 0, ist = MFWQ_OK;
+        double irel = 0.0;
+        ST(bicgstab<float>(A, P, r32, d32, false, inner_rtol, inner_maxit, bufs32(h), h->dsc, h->hsc, h->part, N, s, 4,
+                           nullptr, &it, &irel, &ist));
+        inner_total += it;
+        if (ist == MFWQ_ENAN) { status = MFWQ_ENAN; break; }
+        ST(add_f32_scaled(u, d32, h->dnorm, N, s));
+        ++outer;
+    }
+    if (info) {
+        info->status = status;
+        info->iterations = inner_total;
+        info->outer_iterations = outer;
+        info->rel_residual = rel;
+    }
+    return status;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+const char* mfwq_status_string(int st) {
+    switch (st) {
+        case MFWQ_OK: return "ok";
+        case MFWQ_EINVAL: return "invalid argument";
+        case MFWQ_ENOMEM: return "out of memory";
+        case MFWQ_ECUDA: return "CUDA error";
+        case MFWQ_ESETUP: return "setup failed (weights or eigensolve)";
+        case MFWQ_EBREAKDOWN: return "BiCGStab breakdown";
+        case MFWQ_ENOCONV: return "not converged";
+        case MFWQ_ETIMEOUT: return "device wait timed out";
+        case MFWQ_ENAN: return "NaN or Inf encountered";
+        case MFWQ_EINTERNAL: return "internal error";
+        default: return "unknown status";
+    }
+}
+
+const char* mfwq_last_error(void) { return g_last_error.c_str(); }
+
+int mfwq_setup(const mfwq_setup_desc* desc, mfwq_handle* out) {
+    if (!desc || !out) return fail(MFWQ_EINVAL, "NULL argument");
+    *out = nullptr;
+    mfwq_handle h = new (std::nothrow) mfwq_handle_s();
+    if (!h) return fail(MFWQ_ENOMEM, "host allocation failed");
+    int st = setup_impl(desc, h);
+    if (st != MFWQ_OK) {
+        free_handle(h);
+        return st;
+    }
+    *out = h;
+    return MFWQ_OK;
+}
+
+void mfwq_destroy(mfwq_handle h) {
+    if (h && h->stream) cudaStreamSynchronize(h->stream);
+    else if (h) cudaDeviceSynchronize();
+    free_handle(h);
+}
+
+int mfwq_sizes(mfwq_handle h, int n[3], int nq[3]) {
+    if (!h) return fail(MFWQ_EINVAL, "NULL handle");
+    for (int l = 0; l < 3; ++l) {
+        if (n) n[l] = h->n[l];
+        if (nq) nq[l] = h->nq[l];
+    }
+    return MFWQ_OK;
+}
+
+int mfwq_quad_points(mfwq_handle h, int dir, double* xq_host) {
+    if (!h || dir < 0 || dir > 2 || !xq_host) return fail(MFWQ_EINVAL, "bad argument");
+    std::memcpy(xq_host, h->dir[dir].xq.data(), sizeof(double) * h->nq[dir]);
+    return MFWQ_OK;
+}
+
+int mfwq_eval_coeff(mfwq_handle h, int geometry, const double* modes_host, int nmodes, double kscale, double* C_dev) {
+    ProfScope _ps(h ? &h->prof : nullptr);
+    if (!h || !C_dev || nmodes < 0 || nmodes > 32 || (nmodes > 0 && !modes_host)) return fail(MFWQ_EINVAL, "bad argument");
+    if (geometry != MFWQ_GEOM_CUBE && geometry != MFWQ_GEOM_RING) return fail(MFWQ_EINVAL, "unknown geometry");
+    if (!aligned16(C_dev)) return fail(MFWQ_EINVAL, "C_dev must be 16-byte aligned");
+    const double* xq[3] = {h->d64[0].xq, h->d64[1].xq, h->d64[2].xq};
+    return run_eval_coeff(h->nq, xq, geometry, modes_host, nmodes, kscale, C_dev, h->stream);
+}
+
+namespace {
+__global__ void k_to_f32(const double* __restrict__ x, float* __restrict__ y, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) y[i] = (float)x[i];
+}
+}  // namespace
+
+int mfwq_set_coeff(mfwq_handle h, const double* C_dev) {
+    ProfScope _ps(h ? &h->prof : nullptr);
+    if (!h || !C_dev) return fail(MFWQ_EINVAL, "bad argument");
+    CU(cudaMemcpyAsync(h->C64, C_dev, sizeof(double) * 6 * h->Nq, cudaMemcpyDeviceToDevice, h->stream));
+    if (h->mixed) {
+        launch_begin(S_SETUP, h->stream);
+        k_to_f32<<<1024, 256, 0, h->stream>>>(C_dev, h->C32, 6 * h->Nq);
+        launch_end(S_SETUP, h->stream);
+        CU(cudaGetLastError());
+    }
+    return MFWQ_OK;
+}
+
+int mfwq_load_vector(mfwq_handle h, int geometry, int forcing, double* f_dev) {
+    ProfScope _ps(h ? &h->prof : nullptr);
+    if (!h || !f_dev) return fail(MFWQ_EINVAL, "bad argument");
+    if (geometry != MFWQ_GEOM_CUBE && geometry != MFWQ_GEOM_RING) return fail(MFWQ_EINVAL, "unknown geometry");
+    if (forcing != MFWQ_FORCING_SINES && forcing != MFWQ_FORCING_RING_EXACT) return fail(MFWQ_EINVAL, "unknown forcing");
+    return run_load_vector(h->d64, geometry, forcing, static_cast<double*>(h->scratch), f_dev, h->stream);
+}
+
+int mfwq_apply(mfwq_handle h, const double* x_dev, double* y_dev) {
+    ProfScope _ps(h ? &h->prof : nullptr);
+    if (!h || !x_dev || !y_dev || x_dev == y_dev) return fail(MFWQ_EINVAL, "bad argument");
+    return run_apply<double>(ctx64(h), x_dev, y_dev, nullptr);
+}
+
+int mfwq_apply_T(mfwq_handle h, const double* x_dev, double* y_dev) {
+    ProfScope _ps(h ? &h->prof : nullptr);
+    if (!h || !x_dev || !y_dev || x_dev == y_dev) return fail(MFWQ_EINVAL, "bad argument");
+    return run_apply_T<double>(ctx64(h), x_dev, y_dev, nullptr);
+}
+
+int mfwq_apply_f32(mfwq_handle h, const float* x_dev, float* y_dev) {
+    ProfScope _ps(h ? &h->prof : nullptr);
+    if (!h || !x_dev || !y_dev || x_dev == (const float*)y_dev) return fail(MFWQ_EINVAL, "bad argument");
+    if (!h->mixed) return fail(MFWQ_EINVAL, "handle was set up without mixed = 1");
+    return run_apply<float>(ctx32(h), x_dev, y_dev, nullptr);
+}
+
+int fd_precond(mfwq_handle h, const double* r_dev, double* z_dev) {
+    ProfScope _ps(h ? &h->prof : nullptr);
+    if (!h || !r_dev || !z_dev || r_dev == z_dev) return fail(MFWQ_EINVAL, "bad argument");
+    return run_fd64(h->d64, r_dev, z_dev, h->fd_tmp64, nullptr, h->stream);
+}
+
+int fd_precond_f32(mfwq_handle h, const float* r_dev, float* z_dev) {
+    ProfScope _ps(h ? &h->prof : nullptr);
+    if (!h || !r_dev || !z_dev || r_dev == (const float*)z_dev) return fail(MFWQ_EINVAL, "bad argument");
+    if (!h->mixed) return fail(MFWQ_EINVAL, "handle was set up without mixed = 1");
+    return run_fd32_simt(h->d32, r_dev, z_dev, h->fd_tmp32, nullptr, h->stream);
+}
+
+int mfwq_solve(mfwq_handle h, const double* f_dev, double* u_dev, const mfwq_solve_opts* opts, mfwq_solve_info* info) {
+    ProfScope _ps(h ? &h->prof : nullptr);
+    if (!h || !f_dev || !u_dev || f_dev == u_dev) return fail(MFWQ_EINVAL, "bad argument");
+    mfwq_solve_opts o = opts ? *opts : default_opts();
+    if (!(o.rtol > 0) || o.maxit < 0) return fail(MFWQ_EINVAL, "rtol must be > 0 and maxit >= 0");
+    if (h->mixed && !o.force_fp64) return solve_mixed(h, f_dev, u_dev, o, info);
+    return solve64(h, f_dev, u_dev, o, info, false);
+}
+
+int mfwq_solve_T(mfwq_handle h, const double* g_dev, double* lambda_dev, const mfwq_solve_opts* opts, mfwq_solve_info* info) {
+    ProfScope _ps(h ? &h->prof : nullptr);
+    if (!h || !g_dev || !lambda_dev || g_dev == lambda_dev) return fail(MFWQ_EINVAL, "bad argument");
+    mfwq_solve_opts o = opts ? *opts : default_opts();
+    if (!(o.rtol > 0) || o.maxit < 0) return fail(MFWQ_EINVAL, "rtol must be > 0 and maxit >= 0");
+    return solve64(h, g_dev, lambda_dev, o, info, true);
+}
+
+int mfwq_solve_host(mfwq_handle h, const double* f_host, double* u_host, const mfwq_solve_opts* opts, mfwq_solve_info* info) {
+    ProfScope _ps(h ? &h->prof : nullptr);
+    if (!h || !f_host || !u_host) return fail(MFWQ_EINVAL, "bad argument");
+    if (!h->host_io) ST(dmalloc((void**)&h->host_io, sizeof(double) * 2 * h->N));
+    double* f = h->host_io;
+    double* u = h->host_io + h->N;
+    CU(cudaMemcpyAsync(f, f_host, sizeof(double) * h->N, cudaMemcpyHostToDevice, h->stream));
+    mfwq_solve_opts o = opts ? *opts : default_opts();
+    if (o.use_initial_guess) CU(cudaMemcpyAsync(u, u_host, sizeof(double) * h->N, cudaMemcpyHostToDevice, h->stream));
+    int st = mfwq_solve(h, f, u, &o, info);
+    if (st != MFWQ_OK && st != MFWQ_ENOCONV) return st;
+    CU(cudaMemcpyAsync(u_host, u, sizeof(double) * h->N, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return st;
+}
+
+int mfwq_grad_coeff(mfwq_handle h, const double* lambda_dev, const double* u_dev, double* gC_dev) {
+    ProfScope _ps(h ? &h->prof : nullptr);
+    if (!h || !lambda_dev || !u_dev || !gC_dev) return fail(MFWQ_EINVAL, "bad argument");
+    return run_grad<double>(ctx64(h), lambda_dev, u_dev, gC_dev);
+}
+
+static const char* kStageNames[S_NTAGS] = {
+    "trial_z", "trial_y", "xstage", "test_y", "test_z", "test_zT", "test_yT", "xstage_T", "trial_yT", "trial_zT",
+    "xstage_grad", "fd_dim1", "fd_dim23", "fd_tc", "krylov", "setup"};
+
+const char* mfwq_stage_name(int stage) { return stage >= 0 && stage < S_NTAGS ? kStageNames[stage] : ""; }
+
+int mfwq_profile_enable(mfwq_handle h, int on) {
+    if (!h) return fail(MFWQ_EINVAL, "NULL handle");
+    h->prof.on = on != 0;
+    return MFWQ_OK;
+}
+
+int mfwq_profile_read(mfwq_handle h, mfwq_profile_stats* out, int reset) {
+    if (!h || !out) return fail(MFWQ_EINVAL, "bad argument");
+    h->prof.drain();
+    std::memset(out, 0, sizeof *out);
+    for (int i = 0; i < S_NTAGS && i < MFWQ_NSTAGES; ++i) {
+        out->ms[i] = h->prof.ms[i];
+        out->launches[i] = h->prof.launches[i];
+    }
+    if (reset) {
+        for (int i = 0; i < S_NTAGS; ++i) {
+            h->prof.ms[i] = 0.0;
+            h->prof.launches[i] = 0;
+        }
+    }
+    return MFWQ_OK;
+}
+
+long long mfwq_kernel_launches(void) { return total_launches(); }
+
+int mfwq_sync(mfwq_handle h) {
+    if (!h) return fail(MFWQ_EINVAL, "NULL handle");
+    CU(cudaStreamSynchronize(h->stream));
+    CU(cudaGetLastError());
+    return MFWQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,46 @@
+// Device-side BiCGStab (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <functional>
+
+#include "kernels.h"
+
+namespace mfwq {
+
+constexpr int kRedBlocks = 1024;  // fixed reduction grid (deterministic sums)
+
+// Scalars of one BiCGStab solve, resident in device memory.
+struct KScal {
+    double rtol, tol2;
+    double rho, rho_old, alpha, omega, beta;
+    double s2, r2, f2;
+    int skip1;   // solve finished: every kernel of the iteration returns at once
+    int skip2;   // finished or converged on the half step: second half skipped
+    int half, status, iters, pad;
+};
+
+template <typename T>
+using LinOp = std::function<int(const T* in, T* out, const int* skip)>;
+
+template <typename T>
+struct KrylovBufs {
+    T *r, *rhat, *p, *v, *s, *t, *ph, *sh;
+};
+
+// Solves A x = f with P as right preconditioner.  Synchronous.  *status is an
+// MFWQ_* code (MFWQ_ENOCONV when maxit is reached); the return value reports
+// launch failures only.
+template <typename T>
+int bicgstab(const LinOp<T>& A, const LinOp<T>& P, const T* f, T* x, bool x_given, double rtol, int maxit,
+             const KrylovBufs<T>& b, KScal* dsc, KScal* hsc, double* part, size_t N, cudaStream_t s, int check_every,
+             double* hist, int* iters, double* relres, int* status);
+
+template <typename T>
+int axpby_into(const T* f, const T* v, T* r, size_t N, cudaStream_t s);  // r = f - v
+int norm2_into(const double* x, size_t N, double* part, double* out, cudaStream_t s);  // *out = |x|^2
+int to_f32_scaled(const double* x, const double* nrm2, float* y, size_t N, cudaStream_t s);   // y = x / |x|
+int add_f32_scaled(double* u, const float* d, const double* nrm2, size_t N, cudaStream_t s);  // u += |x| d
+
+}  // namespace mfwq

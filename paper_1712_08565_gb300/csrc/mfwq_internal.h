@@ -1,0 +1,72 @@
+// Internal declarations of the MF-WQ library (not part of the C ABI).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/mfwq.h"
+
+#ifdef __CUDACC__
+#define MFWQ_HD __host__ __device__
+#else
+#define MFWQ_HD
+#endif
+
+namespace mfwq {
+
+constexpr int kMaxDegree = 12;
+
+// One direction's 1D data (Section 2.2 and Algorithm 2's setup), host side.
+// Bands store, for every row, the first column and the number of columns that
+// may be nonzero; values are padded to the band width with zeros.
+struct Band1D {
+    int rows = 0, cols = 0, width = 0, fams = 0;
+    std::vector<int> start, len;
+    std::vector<double> val;  // [fams][rows][width]
+    double& at(int f, int r, int t) { return val[((size_t)f * rows + r) * width + t]; }
+    double at(int f, int r, int t) const { return val[((size_t)f * rows + r) * width + t]; }
+};
+
+struct Dir1D {
+    int p = 0, nel = 0, m = 0, n = 0, nq = 0, ng = 0;
+    std::vector<double> t;      // knots
+    std::vector<double> xq;     // WQ points
+    std::vector<double> xg, wg; // Gauss points / weights (p+1 per span), load vector
+    Band1D B;    // rows q -> interior columns j, fams: 0 = values, 1 = derivatives
+    Band1D BT;   // rows j -> points q, transposed B
+    Band1D W;    // rows i -> points q, fams f = 2a+b
+    Band1D WT;   // rows q -> rows i, transposed W
+    Band1D GT;   // rows j -> Gauss points g, value b_j(x_g) * w_g
+    std::vector<double> U, UT, lam;  // FD: U [n][n] row-major, UT = U^T, lam[n]
+};
+
+// Host setup (setup_host.cpp).  Return MFWQ_* codes; `why` gets a message.
+int validate_knots(int p, int nknots, const double* knots, std::string& why);
+int build_dir(int p, int nknots, const double* knots, Dir1D& d, std::string& why);
+
+// Device view of a band (values of type T).
+template <typename T>
+struct BandD {
+    const int* start;
+    const int* len;
+    const T* val;      // [fams][rows][width]
+    int rows, width;
+    MFWQ_HD const T* row(int f, int r) const {
+        return val + ((size_t)f * rows + r) * width;
+    }
+};
+
+template <typename T>
+struct DirD {
+    int n, nq, ng;
+    BandD<T> B, BT, W, WT, GT;
+    const T* U;     // [n][n]
+    const T* UT;    // [n][n]
+    const T* lam;   // [n]
+    const double* xq;  // points (always FP64)
+    const double* xg;  // Gauss points (always FP64)
+};
+
+}  // namespace mfwq

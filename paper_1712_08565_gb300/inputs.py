@@ -51,3 +51,15 @@ def batch_patches(count: int = 64, seed: int = 0, p_range=(2, 6), nel_range=(16,
         nel = tuple(int(v) for v in g.integers(nel_range[0], nel_range[1] + 1, size=3))
         out.append((p, nel))
     return out
+
+
+def open_uniform_knots(p: int, nel: int) -> np.ndarray:
+    """Open knot vector of degree p with nel equal spans on [0, 1]."""
+    return np.concatenate([np.zeros(p), np.linspace(0.0, 1.0, nel + 1), np.ones(p)])
+
+
+def jittered_knots(p: int, nel: int, seed: int, amount: float = 0.3) -> np.ndarray:
+    """Open knot vector whose break points k/nel are moved by up to amount/nel."""
+    g = rng(seed)
+    u = np.arange(1, nel) / nel + g.uniform(-amount, amount, size=nel - 1) / nel
+    return np.concatenate([np.zeros(p + 1), u, np.ones(p + 1)])

@@ -1,0 +1,399 @@
+"""Thin Python binding of libmfwq.so (include/mfwq.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module checks tensor shapes,
+dtypes and devices, passes raw pointers and sizes through ctypes, and turns
+status codes into exceptions.  PyTorch provides device memory and streams.
+There is no fallback: if the library is missing or no GPU is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmfwq.so")
+
+MFWQ_OK = 0
+STATUS = {0: "MFWQ_OK", -1: "MFWQ_EINVAL", -2: "MFWQ_ENOMEM", -3: "MFWQ_ECUDA", -4: "MFWQ_ESETUP",
+          -5: "MFWQ_EBREAKDOWN", -6: "MFWQ_ENOCONV", -7: "MFWQ_ETIMEOUT", -8: "MFWQ_ENAN", -9: "MFWQ_EINTERNAL"}
+FD_PRECISION = {"fp64": 0, "tf32": 1, "bf16": 2}
+GEOMETRY = {"cube": 0, "ring": 1}
+FORCING = {"sines": 0, "ring_exact": 1}
+
+_c_int3 = ctypes.c_int * 3
+_c_dptr = ctypes.POINTER(ctypes.c_double)
+
+
+class SetupDesc(ctypes.Structure):
+    _fields_ = [("degree", ctypes.c_int * 3), ("nknots", ctypes.c_int * 3), ("knots", _c_dptr * 3),
+                ("mixed", ctypes.c_int), ("fd_precision", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("inner_rtol", ctypes.c_double),
+                ("inner_maxit", ctypes.c_int), ("use_initial_guess", ctypes.c_int), ("force_fp64", ctypes.c_int),
+                ("res_hist", _c_dptr)]
+
+
+class ProfileStats(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 16), ("launches", ctypes.c_longlong * 16)]
+
+
+class SolveInfoC(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int), ("outer_iterations", ctypes.c_int),
+                ("rel_residual", ctypes.c_double)]
+
+
+@dataclass
+class SolveInfo:
+    status: int
+    iterations: int
+    outer_iterations: int
+    rel_residual: float
+    history: list | None = None
+
+    @property
+    def converged(self) -> bool:
+        return self.status == MFWQ_OK
+
+
+class MfwqError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_LIB = None
+
+# (name, restype, argtypes)
+_SIGS = [
+    ("mfwq_setup", ctypes.c_int, [ctypes.POINTER(SetupDesc), ctypes.POINTER(ctypes.c_void_p)]),
+    ("mfwq_destroy", None, [ctypes.c_void_p]),
+    ("mfwq_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("mfwq_last_error", ctypes.c_char_p, []),
+    ("mfwq_sizes", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("mfwq_quad_points", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]),
+    ("mfwq_tables_1d", ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+     + [ctypes.c_void_p] * 6),
+    ("mfwq_eval_coeff", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
+                                       ctypes.c_void_p]),
+    ("mfwq_set_coeff", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("mfwq_load_vector", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
+    ("mfwq_apply", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("mfwq_apply_T", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("mfwq_apply_f32", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("fd_precond", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("fd_precond_f32", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("mfwq_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(SolveOpts),
+                                  ctypes.POINTER(SolveInfoC)]),
+    ("mfwq_solve_T", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(SolveOpts),
+                                    ctypes.POINTER(SolveInfoC)]),
+    ("mfwq_solve_host", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(SolveOpts),
+                                       ctypes.POINTER(SolveInfoC)]),
+    ("mfwq_grad_coeff", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("mfwq_sync", ctypes.c_int, [ctypes.c_void_p]),
+    ("mfwq_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("mfwq_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ProfileStats), ctypes.c_int]),
+    ("mfwq_stage_name", ctypes.c_char_p, [ctypes.c_int]),
+    ("mfwq_kernel_launches", ctypes.c_longlong, []),
+]
+
+
+def kernel_launches() -> int:
+    """Kernels the library has launched in this process (all handles)."""
+    return int(lib().mfwq_kernel_launches())
+
+
+def lib():
+    """Load libmfwq.so (built in-tree by paper_1712_08565_gb300.build)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1712_08565_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, res, args in _SIGS:
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(st: int):
+    if st != MFWQ_OK:
+        msg = lib().mfwq_last_error().decode() or lib().mfwq_status_string(st).decode()
+        raise MfwqError(st, msg)
+
+
+def tables_1d(degree: int, knots) -> dict:
+    """Host-only 1D tables of the library (no GPU needed): points, B0, B1,
+    the four weight families (index 2a+b), FD eigenvectors and eigenvalues."""
+    k = np.ascontiguousarray(knots, dtype=np.float64)
+    n, nq = ctypes.c_int(), ctypes.c_int()
+    _check(lib().mfwq_tables_1d(degree, len(k), k.ctypes.data, ctypes.byref(n), ctypes.byref(nq),
+                                None, None, None, None, None, None))
+    n, nq = n.value, nq.value
+    out = dict(xq=np.zeros(nq), B0=np.zeros((nq, n)), B1=np.zeros((nq, n)), W=np.zeros((4, n, nq)),
+               U=np.zeros((n, n)), lam=np.zeros(n))
+    _check(lib().mfwq_tables_1d(degree, len(k), k.ctypes.data, ctypes.byref(ctypes.c_int()), ctypes.byref(ctypes.c_int()),
+                                *(out[x].ctypes.data for x in ("xq", "B0", "B1", "W", "U", "lam"))))
+    return out
+
+
+def _ptr(t, dtype, numel=None, device=None):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if not t.is_cuda:
+        raise ValueError("tensor must be on a CUDA device")
+    if device is not None and t.device != device:
+        raise ValueError(f"tensor on {t.device}, operator on {device}")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Operator:
+    """One MF-WQ patch: tables, coefficient and workspace on one GPU.
+
+    degree: int or 3 ints; knots: 3 open knot vectors (direction 1, 2, 3).
+    mixed: also build the FP32 operator and tensor-core FD for the
+    mixed-precision solve; fd_precision: 'tf32' or 'bf16'.
+    """
+
+    def __init__(self, degree, knots, mixed: bool = False, fd_precision: str = "tf32", device=None, stream=None):
+        import torch
+        if device is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        else:
+            self.device = torch.device(device)
+            if self.device.index is None:
+                self.device = torch.device("cuda", torch.cuda.current_device())
+        degs = [int(degree)] * 3 if np.ndim(degree) == 0 else [int(d) for d in degree]
+        self._knots = [np.ascontiguousarray(k, dtype=np.float64) for k in knots]
+        desc = SetupDesc()
+        for l in range(3):
+            desc.degree[l] = degs[l]
+            desc.nknots[l] = len(self._knots[l])
+            desc.knots[l] = self._knots[l].ctypes.data_as(_c_dptr)
+        desc.mixed = 1 if mixed else 0
+        desc.fd_precision = FD_PRECISION[fd_precision] if mixed else 0
+        with torch.cuda.device(self.device):
+            s = stream if stream is not None else torch.cuda.current_stream(self.device)
+            self.stream = s
+            desc.stream = ctypes.c_void_p(s.cuda_stream)
+            h = ctypes.c_void_p()
+            _check(lib().mfwq_setup(ctypes.byref(desc), ctypes.byref(h)))
+        self._h = h
+        self.degree = degs
+        self.mixed = bool(mixed)
+        self.fd_precision = fd_precision if mixed else "fp64"
+        n, nq = _c_int3(), _c_int3()
+        _check(lib().mfwq_sizes(self._h, n, nq))
+        self.n = tuple(n)
+        self.nq = tuple(nq)
+        self.shape = (self.n[2], self.n[1], self.n[0])
+        self.qshape = (self.nq[2], self.nq[1], self.nq[0])
+        self.N = self.n[0] * self.n[1] * self.n[2]
+        self.Nq = self.nq[0] * self.nq[1] * self.nq[2]
+
+    # ------------------------------------------------------------ lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mfwq_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ helpers
+    def _new(self, shape, dtype):
+        import torch
+        return torch.empty(shape, dtype=dtype, device=self.device)
+
+    def quad_points(self, direction: int) -> np.ndarray:
+        out = np.zeros(self.nq[direction])
+        _check(lib().mfwq_quad_points(self._h, direction, out.ctypes.data))
+        return out
+
+    # ------------------------------------------------------------ setup helpers
+    def eval_coeff(self, geometry: str = "ring", modes=None, kscale: float = 0.0, out=None):
+        import torch
+        out = out if out is not None else self._new((6,) + self.qshape, torch.float64)
+        m = np.ascontiguousarray(modes if modes is not None else np.zeros((0, 5)), dtype=np.float64)
+        _check(lib().mfwq_eval_coeff(self._h, GEOMETRY[geometry], m.ctypes.data if m.size else None, int(m.shape[0]),
+                                     float(kscale), _ptr(out, torch.float64, 6 * self.Nq, self.device)))
+        return out
+
+    def set_coeff(self, C):
+        import torch
+        _check(lib().mfwq_set_coeff(self._h, _ptr(C, torch.float64, 6 * self.Nq, self.device)))
+
+    def load_vector(self, geometry: str = "ring", forcing: str = "sines", out=None):
+        import torch
+        out = out if out is not None else self._new(self.shape, torch.float64)
+        _check(lib().mfwq_load_vector(self._h, GEOMETRY[geometry], FORCING[forcing], _ptr(out, torch.float64, self.N, self.device)))
+        return out
+
+    # ------------------------------------------------------------ hot path
+    def apply(self, x, out=None):
+        import torch
+        out = out if out is not None else self._new(self.shape, torch.float64)
+        _check(lib().mfwq_apply(self._h, _ptr(x, torch.float64, self.N, self.device), _ptr(out, torch.float64, self.N, self.device)))
+        return out
+
+    def apply_T(self, x, out=None):
+        import torch
+        out = out if out is not None else self._new(self.shape, torch.float64)
+        _check(lib().mfwq_apply_T(self._h, _ptr(x, torch.float64, self.N, self.device), _ptr(out, torch.float64, self.N, self.device)))
+        return out
+
+    def apply_f32(self, x, out=None):
+        import torch
+        out = out if out is not None else self._new(self.shape, torch.float32)
+        _check(lib().mfwq_apply_f32(self._h, _ptr(x, torch.float32, self.N, self.device), _ptr(out, torch.float32, self.N, self.device)))
+        return out
+
+    def fd_precond(self, r, out=None):
+        import torch
+        out = out if out is not None else self._new(self.shape, torch.float64)
+        _check(lib().fd_precond(self._h, _ptr(r, torch.float64, self.N, self.device), _ptr(out, torch.float64, self.N, self.device)))
+        return out
+
+    def fd_precond_f32(self, r, out=None):
+        import torch
+        out = out if out is not None else self._new(self.shape, torch.float32)
+        _check(lib().fd_precond_f32(self._h, _ptr(r, torch.float32, self.N, self.device), _ptr(out, torch.float32, self.N, self.device)))
+        return out
+
+    def _opts(self, rtol, maxit, inner_rtol, inner_maxit, x0, force_fp64, history):
+        o = SolveOpts()
+        o.rtol = rtol
+        o.maxit = maxit
+        o.inner_rtol = inner_rtol
+        o.inner_maxit = inner_maxit
+        o.use_initial_guess = 1 if x0 else 0
+        o.force_fp64 = 1 if force_fp64 else 0
+        hist = None
+        if history:
+            hist = np.zeros(maxit + 2)
+            o.res_hist = hist.ctypes.data_as(_c_dptr)
+        return o, hist
+
+    def _solve(self, fn, f, u, rtol, maxit, inner_rtol, inner_maxit, force_fp64, history, check):
+        import torch
+        x0 = u is not None
+        u = u if u is not None else self._new(self.shape, torch.float64)
+        o, hist = self._opts(rtol, maxit, inner_rtol, inner_maxit, x0, force_fp64, history)
+        info = SolveInfoC()
+        st = fn(self._h, _ptr(f, torch.float64, self.N, self.device), _ptr(u, torch.float64, self.N, self.device),
+                ctypes.byref(o), ctypes.byref(info))
+        if st not in (MFWQ_OK, -6, -5, -8) or (check and st != MFWQ_OK):
+            _check(st)
+        h = None
+        if hist is not None:
+            last = info.outer_iterations if (self.mixed and not force_fp64) else info.iterations
+            h = list(hist[: last + 1])
+        return u, SolveInfo(info.status, info.iterations, info.outer_iterations, info.rel_residual, h)
+
+    def solve(self, f, u=None, rtol=1e-10, maxit=500, inner_rtol=0.0, inner_maxit=0, force_fp64=False,
+              history=False, check=False):
+        """Solve K~ u = f (FP64 BiCGStab + FD, or mixed refinement on a mixed
+        operator).  u, if given, is the initial guess and receives the result."""
+        return self._solve(lib().mfwq_solve, f, u, rtol, maxit, inner_rtol, inner_maxit, force_fp64, history, check)
+
+    def solve_T(self, g, lam=None, rtol=1e-10, maxit=500, history=False, check=False):
+        """Solve the adjoint system K~^T lambda = g (FP64)."""
+        return self._solve(lib().mfwq_solve_T, g, lam, rtol, maxit, 0.0, 0, True, history, check)
+
+    def solve_host(self, f_host: np.ndarray, u_host: np.ndarray | None = None, rtol=1e-10, maxit=500,
+                   inner_rtol=0.0, inner_maxit=0, force_fp64=False):
+        """mfwq_solve with host arrays (copies inside the call)."""
+        f = np.ascontiguousarray(f_host, dtype=np.float64)
+        x0 = u_host is not None
+        u = u_host if u_host is not None else np.empty(self.shape)
+        o, _ = self._opts(rtol, maxit, inner_rtol, inner_maxit, x0, force_fp64, False)
+        info = SolveInfoC()
+        st = lib().mfwq_solve_host(self._h, f.ctypes.data, u.ctypes.data, ctypes.byref(o), ctypes.byref(info))
+        if st not in (MFWQ_OK, -6):
+            _check(st)
+        return u, SolveInfo(info.status, info.iterations, info.outer_iterations, info.rel_residual)
+
+    def grad_coeff(self, lam, u, out=None):
+        import torch
+        out = out if out is not None else self._new((6,) + self.qshape, torch.float64)
+        _check(lib().mfwq_grad_coeff(self._h, _ptr(lam, torch.float64, self.N, self.device), _ptr(u, torch.float64, self.N, self.device),
+                                     _ptr(out, torch.float64, 6 * self.Nq, self.device)))
+        return out
+
+    def sync(self):
+        _check(lib().mfwq_sync(self._h))
+
+    def profile(self, on: bool = True):
+        """Bracket every later kernel launch with CUDA events (per-stage timing)."""
+        _check(lib().mfwq_profile_enable(self._h, 1 if on else 0))
+
+    def profile_read(self, reset: bool = True) -> dict:
+        """{stage name: (device ms summed, launches)} since the last reset."""
+        st = ProfileStats()
+        _check(lib().mfwq_profile_read(self._h, ctypes.byref(st), 1 if reset else 0))
+        out = {}
+        for i in range(16):
+            if st.launches[i]:
+                out[lib().mfwq_stage_name(i).decode()] = (st.ms[i], int(st.launches[i]))
+        return out
+
+
+def _make_solve_function():
+    import torch
+
+    class MfwqSolve(torch.autograd.Function):
+        """u = K~(C)^-1 f with gradients for C (6 symmetric fields at the WQ
+        points) and f.  Backward solves the adjoint K~^T lambda = dL/du and
+        returns dL/dC = -fold((W^T lambda) (B u)) and dL/df = lambda."""
+
+        @staticmethod
+        def forward(ctx, C6, f, op: Operator, rtol: float):
+            op.set_coeff(C6.contiguous())
+            u, info = op.solve(f.contiguous(), rtol=rtol, force_fp64=True)
+            if not info.converged:
+                raise MfwqError(info.status, "forward solve did not converge")
+            ctx.op = op
+            ctx.rtol = rtol
+            ctx.save_for_backward(C6, u)
+            return u
+
+        @staticmethod
+        def backward(ctx, grad_u):
+            C6, u = ctx.saved_tensors
+            op = ctx.op
+            op.set_coeff(C6.contiguous())
+            lam, info = op.solve_T(grad_u.contiguous(), rtol=ctx.rtol)
+            if not info.converged:
+                raise MfwqError(info.status, "adjoint solve did not converge")
+            gC = op.grad_coeff(lam, u)
+            return gC, lam, None, None
+
+    return MfwqSolve
+
+
+_SOLVE_FN = None
+
+
+def solve_fn():
+    """torch.autograd.Function applying u = K~(C)^-1 f: solve_fn().apply(C6, f, op, rtol)."""
+    global _SOLVE_FN
+    if _SOLVE_FN is None:
+        _SOLVE_FN = _make_solve_function()
+    return _SOLVE_FN
