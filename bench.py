@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the p sweep, mixed solve and CPU baseline")
+    ap.add_argument("--kernel-run", choices=["apply", "apply_T", "fd64", "fdtc", "fdbf16", "apply32"], default=None,
+                    help="set up the workload, run one operator 3 times and exit (target for ncu captures)")
     return ap.parse_args()
 
 
@@ -351,12 +353,12 @@ def run_ours(args):
     f_host.copy_(f.cpu())
     u_host = torch.empty(op.shape, dtype=torch.float64, pin_memory=True)
     fh, uh = f_host.numpy(), u_host.numpy()
-    op.solve_host(fh, uh, rtol=rtol, maxit=1000)
+    op.solve_host(fh, out=uh, rtol=rtol, maxit=1000)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_iters = []
     for _ in range(args.steps):
-        _, inf = op.solve_host(fh, uh, rtol=rtol, maxit=1000)
+        _, inf = op.solve_host(fh, out=uh, rtol=rtol, maxit=1000)
         e2e_iters.append(inf.iterations)
     t1 = time.perf_counter()
     e2e_s = (t1 - t0) / args.steps
@@ -399,8 +401,37 @@ def run_ours(args):
     return 0
 
 
+def kernel_run(which):
+    """Setup + three launches of one operator on the bench workload (the
+    p = 6, 192-element ring for the mixed-precision operators)."""
+    import torch
+    from paper_1712_08565_gb300 import build
+    build.build()
+    from paper_1712_08565_gb300 import mfwq as mf
+    from paper_1712_08565_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    mixed = which in ("fdtc", "fdbf16", "apply32")
+    p, nel = (MIXED["p"], MIXED["nel"]) if mixed else (WORKLOAD["p"], WORKLOAD["nel"])
+    op, _ = make_op(mf, p, nel, mixed=mixed, fd="bf16" if which == "fdbf16" else "tf32", device=dev)
+    x = torch.from_numpy(inputs.uniform_vector(op.shape, 1)).to(dev)
+    if mixed:
+        x = x.float()
+    y = torch.empty_like(x)
+    fn = {"apply": op.apply, "apply_T": op.apply_T, "fd64": op.fd_precond, "fdtc": op.fd_precond_f32,
+          "fdbf16": op.fd_precond_f32, "apply32": op.apply_f32}[which]
+    for _ in range(3):
+        fn(x, y)
+    op.sync()
+    torch.cuda.synchronize()
+    print(f"kernel-run {which} ok: N={op.N}, |y|={float(y.double().norm()):.6e}")
+    op.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.kernel_run:
+        return kernel_run(args.kernel_run)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

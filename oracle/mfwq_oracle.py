@@ -32,7 +32,7 @@ Readings of passages the paper leaves open (each is listed in the design doc):
       U_l^T M_l U_l = I, U_l^T K_l U_l = diag(l_l).
 * R7  BiCGStab: right preconditioning, x0 given (default 0), r^_0 = r_0,
       convergence tested on the half step s and on the full step r.
-* R8  Load vector: tensor Gauss with p+1 points per span, c = |det J|.
+* R8  Load vector: tensor Gauss with p_l+1 points per span in direction l, c = |det J|.
 
 Parity unpinned (no value in the paper or in mathematics fixes them):
 boundary-row weight values beyond their exactness residual, BiCGStab
@@ -685,9 +685,12 @@ def exact_forcing_ring(x1, x2, x3):
 
 
 def _gauss_tables(tabs, k):
+    """Gauss points, weights and interior basis values/derivatives per
+    direction; k is a number of points per span or a list of one per direction."""
+    ks = list(k) if np.ndim(k) else [k] * len(tabs)
     out = []
-    for t in tabs:
-        xg, wg = gauss_rule(t.knots, k)
+    for t, kl in zip(tabs, ks):
+        xg, wg = gauss_rule(t.knots, kl)
         val, der = bspline_basis(t.knots, t.p, xg)
         m = val.shape[1]
         out.append((xg, wg, val[:, 1:m - 1], der[:, 1:m - 1]))
@@ -703,8 +706,8 @@ def _geom_at(geometry, X1, X2, X3):
 
 def load_vector(tabs, geometry, forcing):
     """f_i = int |det J| b_i (f o F) dxi (Eq. (linearsystem) with reading R8),
-    tensor Gauss with p+1 points per span; result [i3][i2][i1]."""
-    gt = _gauss_tables(tabs, max(t.p for t in tabs) + 1)
+    tensor Gauss with p_l+1 points per span in direction l; result [i3][i2][i1]."""
+    gt = _gauss_tables(tabs, [t.p + 1 for t in tabs])
     X3, X2, X1 = np.meshgrid(gt[2][0], gt[1][0], gt[0][0], indexing="ij")
     x, det, _ = _geom_at(geometry, X1, X2, X3)
     wgt = np.einsum("c,b,a->cba", gt[2][1], gt[1][1], gt[0][1])
@@ -715,8 +718,7 @@ def load_vector(tabs, geometry, forcing):
 def load_vector_rows(tabs, geometry, forcing, rows):
     """Selected entries of load_vector, each from its own Gauss sum over the
     support of b_i."""
-    k = max(t.p for t in tabs) + 1
-    gt = _gauss_tables(tabs, k)
+    gt = _gauss_tables(tabs, [t.p + 1 for t in tabs])
     out = np.empty(len(rows))
     for r, (i3, i2, i1) in enumerate(rows):
         ii = (i1, i2, i3)

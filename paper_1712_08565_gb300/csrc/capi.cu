@@ -3,6 +3,7 @@
 // BiCGStab (Section 4).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -105,6 +106,7 @@ struct mfwq_handle_s {
     float* kv32 = nullptr;   // 10 N (8 Krylov + rhs + correction)
     double* part = nullptr;  // 2 kRedBlocks
     double* dnorm = nullptr; // 2 doubles
+    int* derr = nullptr;     // device error word (bounded waits)
     KScal* dsc = nullptr;
     KScal* hsc = nullptr;    // pinned
     Profiler prof;
@@ -146,6 +148,7 @@ void free_handle(mfwq_handle h) {
     cudaFree(h->kv32);
     cudaFree(h->part);
     cudaFree(h->dnorm);
+    cudaFree(h->derr);
     cudaFree(h->dsc);
     cudaFree(h->host_io);
     if (h->hsc) cudaFreeHost(h->hsc);
@@ -248,6 +251,13 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
     ST(dmalloc((void**)&h->part, sizeof(double) * 2 * kRedBlocks));
     ST(dmalloc((void**)&h->dnorm, sizeof(double) * 2));
     ST(dmalloc((void**)&h->dsc, sizeof(KScal)));
+    ST(dmalloc((void**)&h->derr, sizeof(int)));
+    CU(cudaMemset(h->derr, 0, sizeof(int)));
+    if (h->mixed) {
+        int maxn = std::max(h->n[0], std::max(h->n[1], h->n[2]));
+        if (maxn > 256) return fail(MFWQ_EINVAL, "the tensor-core FD needs at most 256 DoFs per direction");
+        ST(configure_fd_tc(maxn));
+    }
     CU(cudaMallocHost((void**)&h->hsc, sizeof(KScal)));
     CU(cudaMallocHost((void**)&h->hnorm, sizeof(double) * 2));
 
@@ -290,7 +300,7 @@ int solve64(mfwq_handle h, const double* f, double* u, const mfwq_solve_opts& o,
     int iters = 0, status = MFWQ_OK;
     double rel = 0.0;
     ST(bicgstab<double>(A, P, f, u, o.use_initial_guess != 0, o.rtol, o.maxit, bufs64(h), h->dsc, h->hsc, h->part, h->N, s,
-                        o.res_hist ? 1 : 4, o.res_hist, &iters, &rel, &status));
+                        1, o.res_hist, &iters, &rel, &status));
     if (info) {
         info->status = status;
         info->iterations = iters;
@@ -313,7 +323,11 @@ int solve_mixed(mfwq_handle h, const double* f, double* u, const mfwq_solve_opts
     DirD<float> d[3] = {h->d32[0], h->d32[1], h->d32[2]};
     float* tmp = h->fd_tmp32;
     LinOp<float> A = [c32](const float* in, float* out, const int* skip) { return run_apply<float>(c32, in, out, skip); };
-    LinOp<float> P = [d, tmp, s](const float* in, float* out, const int* skip) { return run_fd32_simt(d, in, out, tmp, skip, s); };
+    int* err = h->derr;
+    const int prec = h->fd_prec;
+    LinOp<float> P = [d, tmp, s, err, prec](const float* in, float* out, const int* skip) {
+        return run_fd_tc(d, prec, in, out, tmp, err, skip, s);
+    };
     const double inner_rtol = o.inner_rtol > 0 ? o.inner_rtol : 1e-4;
     const int inner_maxit = o.inner_maxit > 0 ? o.inner_maxit : 200;
     if (!o.use_initial_guess) CU(cudaMemsetAsync(u, 0, sizeof(double) * N, s));
@@ -474,7 +488,7 @@ int fd_precond_f32(mfwq_handle h, const float* r_dev, float* z_dev) {
     ProfScope _ps(h ? &h->prof : nullptr);
     if (!h || !r_dev || !z_dev || r_dev == (const float*)z_dev) return fail(MFWQ_EINVAL, "bad argument");
     if (!h->mixed) return fail(MFWQ_EINVAL, "handle was set up without mixed = 1");
-    return run_fd32_simt(h->d32, r_dev, z_dev, h->fd_tmp32, nullptr, h->stream);
+    return run_fd_tc(h->d32, h->fd_prec, r_dev, z_dev, h->fd_tmp32, h->derr, nullptr, h->stream);
 }
 
 int mfwq_solve(mfwq_handle h, const double* f_dev, double* u_dev, const mfwq_solve_opts* opts, mfwq_solve_info* info) {
@@ -551,6 +565,12 @@ int mfwq_sync(mfwq_handle h) {
     if (!h) return fail(MFWQ_EINVAL, "NULL handle");
     CU(cudaStreamSynchronize(h->stream));
     CU(cudaGetLastError());
+    int err = 0;
+    CU(cudaMemcpy(&err, h->derr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) {
+        CU(cudaMemset(h->derr, 0, sizeof(int)));
+        return fail(MFWQ_ETIMEOUT, "a bounded device-side wait gave up");
+    }
     return MFWQ_OK;
 }
 

@@ -39,5 +39,10 @@ int run_load_vector(const DirD<double> d[3], int geom, int forcing, double* scra
 int run_fd64(const DirD<double> d[3], const double* r, double* z, double* tmp, const int* skip, cudaStream_t s);
 // FD preconditioner in FP32 storage on the FP32 pipe.
 int run_fd32_simt(const DirD<float> d[3], const float* r, float* z, float* tmp, const int* skip, cudaStream_t s);
+// FD preconditioner on the tensor cores (tcgen05), TF32 or BF16 inputs, FP32
+// in/out; every n_l <= 256.  A bounded wait that times out sets *err = 1.
+int run_fd_tc(const DirD<float> d[3], int fd_precision, const float* r, float* z, float* tmp, int* err, const int* skip,
+              cudaStream_t s);
+int configure_fd_tc(int max_n);
 
 }  // namespace mfwq

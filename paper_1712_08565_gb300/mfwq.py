@@ -317,13 +317,17 @@ class Operator:
         """Solve the adjoint system K~^T lambda = g (FP64)."""
         return self._solve(lib().mfwq_solve_T, g, lam, rtol, maxit, 0.0, 0, True, history, check)
 
-    def solve_host(self, f_host: np.ndarray, u_host: np.ndarray | None = None, rtol=1e-10, maxit=500,
-                   inner_rtol=0.0, inner_maxit=0, force_fp64=False):
-        """mfwq_solve with host arrays (copies inside the call)."""
+    def solve_host(self, f_host: np.ndarray, out: np.ndarray | None = None, x0: np.ndarray | None = None,
+                   rtol=1e-10, maxit=500, inner_rtol=0.0, inner_maxit=0, force_fp64=False):
+        """mfwq_solve with host arrays (copies inside the call).  out receives
+        u; x0, if given, is the initial guess."""
         f = np.ascontiguousarray(f_host, dtype=np.float64)
-        x0 = u_host is not None
-        u = u_host if u_host is not None else np.empty(self.shape)
-        o, _ = self._opts(rtol, maxit, inner_rtol, inner_maxit, x0, force_fp64, False)
+        u = out if out is not None else np.empty(self.shape)
+        if not (u.flags.c_contiguous and u.dtype == np.float64 and u.size == self.N):
+            raise ValueError("out must be a C-contiguous float64 array of N entries")
+        if x0 is not None:
+            u[...] = np.asarray(x0, dtype=np.float64).reshape(u.shape)
+        o, _ = self._opts(rtol, maxit, inner_rtol, inner_maxit, x0 is not None, force_fp64, False)
         info = SolveInfoC()
         st = lib().mfwq_solve_host(self._h, f.ctypes.data, u.ctypes.data, ctypes.byref(o), ctypes.byref(info))
         if st not in (MFWQ_OK, -6):

@@ -83,7 +83,7 @@ def case(mf, request):
 def test_shapes(case):
     assert case.shape == (case.tabs[2].n, case.tabs[1].n, case.tabs[0].n)
     for l in range(3):
-        np.testing.assert_array_equal(case.op.quad_points(l), case.tabs[l].xq)
+        np.testing.assert_allclose(case.op.quad_points(l), case.tabs[l].xq, rtol=4e-16, atol=0)
 
 
 def test_coefficient(case):
@@ -130,20 +130,31 @@ def test_load_vector(case):
 
 
 def test_solve_matches_direct(case):
+    """At rtol 1e-12 the solution is within 1e-9 of a direct sparse solve; at
+    rtol 1e-10 it is as close as the oracle's own BiCGStab gets at that
+    tolerance (the WQ matrix of a small high-degree patch has condition
+    numbers up to 1e7, so a 1e-10 residual bounds the error only to
+    kappa * 1e-10), and its true residual, measured by the oracle, is 1e-10."""
     import scipy.sparse.linalg as spla
     K = O.stiffness_wq(case.tabs, O.full_coeff(case.C6)).tocsc()
     F = O.load_vector(case.tabs, case.geom, O.forcing_sines)
     ref = spla.spsolve(K, F.ravel()).reshape(case.shape)
+    patch = O.Patch(case.tabs, case.C6, O.fd_setup(case.tabs))
+    u_or, _ = patch.solve(F, 1e-10, maxit=400)
+    err_or = np.linalg.norm(u_or - ref) / np.linalg.norm(ref)
     u, info = case.op.solve(_dev(F), rtol=1e-10, maxit=400, history=True)
     assert info.converged, info
     assert info.rel_residual <= 1e-10
     un = u.cpu().numpy()
     err = np.linalg.norm(un - ref) / np.linalg.norm(ref)
-    assert err <= SOLVE_TOL, err
-    # the true residual, measured by the oracle
+    assert err <= max(SOLVE_TOL, 5 * err_or), (err, err_or)
     res = np.linalg.norm(F.ravel() - K @ un.ravel()) / np.linalg.norm(F)
     assert res <= 2e-10, res
     assert info.history is not None and abs(info.history[-1] - info.rel_residual) <= 1e-12 + 1e-6 * info.rel_residual
+    u12, info12 = case.op.solve(_dev(F), rtol=1e-12, maxit=600)
+    assert info12.converged
+    err12 = np.linalg.norm(u12.cpu().numpy() - ref) / np.linalg.norm(ref)
+    assert err12 <= SOLVE_TOL, err12
 
 
 def test_adjoint_solve(case):
@@ -151,10 +162,12 @@ def test_adjoint_solve(case):
     K = O.stiffness_wq(case.tabs, O.full_coeff(case.C6)).tocsc()
     g = inputs.uniform_vector(case.shape, 7)
     ref = spla.spsolve(K.T.tocsc(), g.ravel()).reshape(case.shape)
-    lam, info = case.op.solve_T(_dev(g), rtol=1e-10, maxit=400)
+    lam, info = case.op.solve_T(_dev(g), rtol=1e-12, maxit=600)
     assert info.converged, info
     err = np.linalg.norm(lam.cpu().numpy() - ref) / np.linalg.norm(ref)
     assert err <= SOLVE_TOL, err
+    res = np.linalg.norm(g.ravel() - K.T @ lam.cpu().numpy().ravel()) / np.linalg.norm(g)
+    assert res <= 2e-12, res
 
 
 # ---------------------------------------------------------------- specific properties
@@ -208,6 +221,8 @@ def test_solve_host_matches_device(mf):
     f = c.op.load_vector("ring", "sines")
     u, info = c.op.solve(f, rtol=1e-10)
     uh, infoh = c.op.solve_host(f.cpu().numpy(), rtol=1e-10)
+    uh2, infoh2 = c.op.solve_host(f.cpu().numpy(), out=uh, rtol=1e-10)
+    assert infoh2.iterations == info.iterations  # `out` is an output, not an initial guess
     assert infoh.converged and infoh.iterations == info.iterations
     assert np.abs(uh - u.cpu().numpy()).max() <= 1e-14 * float(u.abs().max())
     c.op.close()
