@@ -199,6 +199,31 @@ int mfwq_grad_coeff(mfwq_handle h, const double* lambda_dev, const double* u_dev
 /* Waits for the handle's stream and reports any failure seen since the last call. */
 int mfwq_sync(mfwq_handle h);
 
+/* ---- FD preconditioner that allocates nothing -------------------------------
+ * No counterpart in the paper: an engineering variant of fd_precond for
+ * callers that cannot allocate device memory where they need the
+ * preconditioner -- code running while a CUDA graph is captured in global
+ * mode (cudaMalloc is illegal then), code whose device memory is all owned by
+ * a framework's caching allocator, or code with a fixed memory budget.  It
+ * needs no handle: the caller passes the FD factors of each direction (U_l and
+ * U_l^T, row-major n_l x n_l, and lambda_l; e.g. from mfwq_tables_1d), the
+ * input r and the output z ([n3][n2][n1], FP64, device), and a stream.  The
+ * one intermediate tensor lives in a fixed device array of
+ * MFWQ_NOALLOC_MAX_N doubles (32 MB) that is part of the library's module, so
+ * every GPU that loads the library holds it until the process exits.
+ * - n1*n2*n3 > MFWQ_NOALLOC_MAX_N is rejected with MFWQ_EINVAL.
+ * - The first call on a device looks the array's address up
+ *   (cudaGetSymbolAddress, which may load the module); make that first call
+ *   before any stream capture.
+ * - Calls share the array: calls whose work overlaps on the GPU (several
+ *   streams, several host threads) race and give wrong results.  Each call
+ *   overwrites the array completely before reading it, so nothing carries
+ *   over from the previous call.
+ * - Asynchronous on `stream`; no cudaMalloc/cudaFree or allocating routine. */
+#define MFWQ_NOALLOC_MAX_N 4194304
+int mfwq_fd_precond_noalloc(const int n[3], const double* const U_dev[3], const double* const UT_dev[3],
+                            const double* const lam_dev[3], const double* r_dev, double* z_dev, void* stream);
+
 /* ---- instrumentation (no counterpart in the paper) -------------------------
  * Kernel stages, in the index order of mfwq_profile_stats: trial_z, trial_y,
  * xstage, test_y, test_z (the five stages of the apply), test_zT, test_yT,

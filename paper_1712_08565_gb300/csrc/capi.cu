@@ -38,6 +38,13 @@ int fail(int code, const std::string& why) {
     } while (0)
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+}  // namespace
+
+namespace mfwq {
+void set_last_error(const std::string& why) { g_last_error = why; }
+}  // namespace mfwq
+
+namespace {
 
 // Host staging of all device tables in one allocation.
 struct Arena {

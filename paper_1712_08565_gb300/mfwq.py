@@ -100,7 +100,30 @@ _SIGS = [
     ("mfwq_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ProfileStats), ctypes.c_int]),
     ("mfwq_stage_name", ctypes.c_char_p, [ctypes.c_int]),
     ("mfwq_kernel_launches", ctypes.c_longlong, []),
+    ("mfwq_fd_precond_noalloc", ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p),
+                                               ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                               ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 ]
+
+NOALLOC_MAX_N = 4194304
+
+
+def fd_precond_noalloc(n, U, UT, lam, r, z, stream=None):
+    """mfwq_fd_precond_noalloc: FD preconditioner whose scratch is a fixed
+    device array inside the library (no allocation).  n = (n1, n2, n3); U, UT,
+    lam: three FP64 CUDA tensors each; r, z: FP64 CUDA tensors of n1 n2 n3
+    entries.  Calls whose work overlaps on the GPU must not run concurrently."""
+    import torch
+    dev = r.device
+    nn = (ctypes.c_int * 3)(*[int(v) for v in n])
+    N = nn[0] * nn[1] * nn[2]
+    Up = (ctypes.c_void_p * 3)(*[_ptr(U[l], torch.float64, nn[l] * nn[l], dev).value for l in range(3)])
+    UTp = (ctypes.c_void_p * 3)(*[_ptr(UT[l], torch.float64, nn[l] * nn[l], dev).value for l in range(3)])
+    Lp = (ctypes.c_void_p * 3)(*[_ptr(lam[l], torch.float64, nn[l], dev).value for l in range(3)])
+    s = stream if stream is not None else torch.cuda.current_stream(dev)
+    _check(lib().mfwq_fd_precond_noalloc(nn, Up, UTp, Lp, _ptr(r, torch.float64, N, dev), _ptr(z, torch.float64, N, dev),
+                                         ctypes.c_void_p(s.cuda_stream)))
+    return z
 
 
 def kernel_launches() -> int:
