@@ -245,6 +245,7 @@ def p_sweep(mf, device):
 
 def mixed_vs_fp64(mf, device):
     import torch
+    from paper_1712_08565_gb300 import inputs
     res = {"workload": MIXED["name"], "rtol": MIXED["rtol"]}
     op, _ = make_op(mf, MIXED["p"], MIXED["nel"], mixed=True, fd="tf32", device=device)
     f = op.load_vector("ring", "sines")
@@ -252,17 +253,30 @@ def mixed_vs_fp64(mf, device):
     for name, kw in (("fp64", dict(force_fp64=True)), ("mixed_tf32", dict(inner_rtol=1e-4))):
         op.solve(f, rtol=MIXED["rtol"], maxit=2000, **kw)  # warm-up
         torch.cuda.synchronize()
+        op.profile(True)
+        op.profile_read(reset=True)
         t0 = time.perf_counter()
         u, info = op.solve(f, rtol=MIXED["rtol"], maxit=2000, **kw)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        st = op.profile_read(reset=True)
+        op.profile(False)
         res[name] = {"time_s": dt, "iterations": info.iterations, "outer": info.outer_iterations,
-                     "rel_residual": info.rel_residual, "converged": info.converged}
+                     "rel_residual": info.rel_residual, "converged": info.converged,
+                     "stages_ms": {k: round(v[0], 3) for k, v in st.items()},
+                     "stages_launches": {k: v[1] for k, v in st.items()}}
         if name == "fp64":
             u64 = u.clone()
         else:
             res[name]["rel_err_vs_fp64"] = float(torch.linalg.vector_norm(u - u64) / torch.linalg.vector_norm(u64))
     res["speedup"] = res["fp64"]["time_s"] / res["mixed_tf32"]["time_s"]
+    x = torch.from_numpy(inputs.uniform_vector(op.shape, 1)).to(device)
+    x32 = x.float()
+    y, y32 = torch.empty_like(x), torch.empty_like(x32)
+    res["op_ms"] = {"apply_f64": event_time(op.stream, lambda: op.apply(x, y), 5),
+                    "apply_f32": event_time(op.stream, lambda: op.apply_f32(x32, y32), 10),
+                    "fd_f64": event_time(op.stream, lambda: op.fd_precond(x, y), 5),
+                    "fd_tf32": event_time(op.stream, lambda: op.fd_precond_f32(x32, y32), 10)}
     op.close()
     torch.cuda.empty_cache()
     return res

@@ -224,13 +224,46 @@ int mfwq_sync(mfwq_handle h);
 int mfwq_fd_precond_noalloc(const int n[3], const double* const U_dev[3], const double* const UT_dev[3],
                             const double* const lam_dev[3], const double* r_dev, double* z_dev, void* stream);
 
+/* ---- autotuner and batched solve --------------------------------------------
+ * No counterpart in the paper (which solves one patch sequentially); multi-patch
+ * independence is the uncoupled case of the multi-patch setting the paper
+ * names as future work in its conclusions. */
+
+/* Times the forward x stage of mfwq_apply with 2, 4 and 8 (q3,q2) lines per
+ * block on this handle's sizes and keeps the fastest (*xlines_out, may be
+ * NULL).  cache_path (may be NULL) is a file of JSON lines
+ * {"key": "...", "xlines": L}: a hit skips the timing, a miss appends the
+ * result.  Uses the handle's Krylov work vectors, so call it between solves.
+ * Synchronous. */
+int mfwq_autotune(mfwq_handle h, const char* cache_path, int* xlines_out);
+
+typedef struct mfwq_batch_s* mfwq_batch;
+
+/* A batch of independent patches, each set up (and given its coefficient) as a
+ * handle of its own; the handles stay owned by the caller and must outlive the
+ * batch.  The batch owns one stream per patch. */
+int mfwq_batch_create(int count, const mfwq_handle* patches, mfwq_batch* out);
+void mfwq_batch_destroy(mfwq_batch b);
+
+/* Solves K~_i u_i = f_i for every patch with FP64 FD-preconditioned BiCGStab
+ * (as mfwq_solve with force_fp64).  One BiCGStab iteration of all patches is
+ * captured into a single CUDA graph (each patch on its own stream) and
+ * launched once per sweep; every patch keeps its own device-resident scalars,
+ * and the kernels of a converged patch return at once.  f_dev[i], u_dev[i]:
+ * device vectors of patch i.  infos (count entries, may be NULL) receive each
+ * patch's status, iterations and residual; outer_iterations holds the number
+ * of sweeps.  Returns the first failing patch status (MFWQ_OK if all
+ * converged).  Synchronous. */
+int mfwq_batch_solve(mfwq_batch b, const double* const* f_dev, double* const* u_dev, const mfwq_solve_opts* opts,
+                     mfwq_solve_info* infos);
+
 /* ---- instrumentation (no counterpart in the paper) -------------------------
  * Kernel stages, in the index order of mfwq_profile_stats: trial_z, trial_y,
  * xstage, test_y, test_z (the five stages of the apply), test_zT, test_yT,
  * xstage_T, trial_yT, trial_zT (the transpose), xstage_grad, fd_dim1,
  * fd_dim23, fd_tc (FD mode products), krylov (BiCGStab vector and scalar
- * kernels), setup. */
-#define MFWQ_NSTAGES 16
+ * kernels), setup, fd_fold (even/odd folding of the FP64 FD). */
+#define MFWQ_NSTAGES 24
 typedef struct {
     double ms[MFWQ_NSTAGES];           /* summed device time per stage (CUDA events) */
     long long launches[MFWQ_NSTAGES];  /* kernel launches per stage */

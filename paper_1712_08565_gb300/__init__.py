@@ -3,6 +3,6 @@
 The compute lives in libmfwq.so (CUDA, C ABI in include/mfwq.h); this package
 holds the in-tree build, the ctypes binding and the seeded input generators.
 """
-from .mfwq import MfwqError, Operator, SolveInfo, kernel_launches, lib, solve_fn, tables_1d  # noqa: F401
+from .mfwq import Batch, MfwqError, Operator, SolveInfo, kernel_launches, lib, solve_fn, tables_1d  # noqa: F401
 
-__all__ = ["Operator", "MfwqError", "SolveInfo", "kernel_launches", "lib", "solve_fn", "tables_1d"]
+__all__ = ["Batch", "Operator", "MfwqError", "SolveInfo", "kernel_launches", "lib", "solve_fn", "tables_1d"]

@@ -304,14 +304,21 @@ struct XArgs {
 constexpr int kLines = 4;
 
 // Forward x stage: Y (3 inputs [line][n1]) -> T (9 outputs [line][n1]).
-template <typename T>
+// The nine products are formed three at a time, one trial direction beta at a
+// time: G_b on the line's points (B1 in direction 1 for beta = 1, else B0),
+// H^(ab) = C_ab G_b for alpha = 1..3 in shared memory, then the three test
+// contractions with W1^(a1,b1).  Per line the block keeps 3 n1 + 3 nq1
+// values in shared memory, so several blocks share an SM and their load,
+// product and contraction phases overlap.
+template <typename T, int LINES>
 __global__ void __launch_bounds__(kThreads) k_xstage_apply(XArgs<T> a, const T* __restrict__ y0, const T* __restrict__ y1,
-                                                           const T* __restrict__ y2, Ptr9<T> tout,
+                                                           const T* __restrict__ y2, T* __restrict__ tout, size_t tstride,
                                                            const int* skip) {
     if (skip && *skip) return;
+    constexpr int kLines = LINES;
     extern __shared__ unsigned char smem_raw[];
     T* sY = reinterpret_cast<T*>(smem_raw);        // [3][kLines][n1]
-    T* sH = sY + 3 * kLines * a.n1;                // [9][kLines][nq1]
+    T* sH = sY + 3 * kLines * a.n1;                // [3][kLines][nq1]
     const int line0 = blockIdx.x * kLines;
     const int nl = min(kLines, a.nlines - line0);
     const int n1 = a.n1, nq1 = a.nq1;
@@ -322,64 +329,38 @@ __global__ void __launch_bounds__(kThreads) k_xstage_apply(XArgs<T> a, const T* 
         sY[(1 * kLines + l) * n1 + j] = y1[gi];
         sY[(2 * kLines + l) * n1 + j] = y2[gi];
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nl * nq1; e += blockDim.x) {
-        const int l = e / nq1, q = e - l * nq1;
-        const int s = a.B.start[q], L = a.B.len[q];
-        const T* b0 = a.B.row(0, q);
-        const T* b1 = a.B.row(1, q);
-        const T* Y0 = sY + (0 * kLines + l) * n1 + s;
-        const T* Y1 = sY + (1 * kLines + l) * n1 + s;
-        const T* Y2 = sY + (2 * kLines + l) * n1 + s;
-        T g1 = 0, g2 = 0, g3 = 0;
-        for (int t = 0; t < L; ++t) {
-            g1 = fmaT(b1[t], Y0[t], g1);
-            g2 = fmaT(b0[t], Y1[t], g2);
-            g3 = fmaT(b0[t], Y2[t], g3);
+    for (int b = 0; b < 3; ++b) {
+        __syncthreads();
+        const int bfam = b == 0 ? 1 : 0;
+        for (int e = threadIdx.x; e < nl * nq1; e += blockDim.x) {
+            const int l = e / nq1, q = e - l * nq1;
+            const int s = a.B.start[q], L = a.B.len[q];
+            const T* bb = a.B.row(bfam, q);
+            const T* Y = sY + (b * kLines + l) * n1 + s;
+            T g = 0;
+            for (int t = 0; t < L; ++t) g = fmaT(bb[t], Y[t], g);
+            const size_t pt = (size_t)(line0 + l) * nq1 + q;
+            T* H = sH + l * nq1 + q;
+            const int hs = kLines * nq1;
+            // symmetric-storage slot of C_(alpha,beta): alpha for alpha = beta, else 2 + alpha + beta
+            H[0 * hs] = a.C[(b == 0 ? 0 : 2 + b) * a.Nq + pt] * g;
+            H[1 * hs] = a.C[(b == 1 ? 1 : 3 + b) * a.Nq + pt] * g;
+            H[2 * hs] = a.C[(b == 2 ? 2 : 4 + b) * a.Nq + pt] * g;
         }
-        const size_t pt = (size_t)(line0 + l) * nq1 + q;
-        const T c11 = a.C[pt], c22 = a.C[a.Nq + pt], c33 = a.C[2 * a.Nq + pt];
-        const T c12 = a.C[3 * a.Nq + pt], c13 = a.C[4 * a.Nq + pt], c23 = a.C[5 * a.Nq + pt];
-        T* H = sH + l * nq1 + q;
-        const int fs = kLines * nq1;
-        H[0 * fs] = c11 * g1;
-        H[1 * fs] = c12 * g2;
-        H[2 * fs] = c13 * g3;
-        H[3 * fs] = c12 * g1;
-        H[4 * fs] = c22 * g2;
-        H[5 * fs] = c23 * g3;
-        H[6 * fs] = c13 * g1;
-        H[7 * fs] = c23 * g2;
-        H[8 * fs] = c33 * g3;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nl * n1; e += blockDim.x) {
-        const int l = e / n1, i = e - l * n1;
-        const int s = a.W.start[i], L = a.W.len[i];
-        const T* w00 = a.W.row(0, i);
-        const T* w01 = a.W.row(1, i);
-        const T* w10 = a.W.row(2, i);
-        const T* w11 = a.W.row(3, i);
-        const int fs = kLines * nq1;
-        const T* H = sH + l * nq1 + s;
-        T acc[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) acc[k] = 0;
-        for (int t = 0; t < L; ++t) {
-            const T f00 = w00[t], f01 = w01[t], f10 = w10[t], f11 = w11[t];
-            acc[0] = fmaT(f11, H[0 * fs + t], acc[0]);  // 11: (1,1)
-            acc[1] = fmaT(f10, H[1 * fs + t], acc[1]);  // 12: (1,0)
-            acc[2] = fmaT(f10, H[2 * fs + t], acc[2]);  // 13: (1,0)
-            acc[3] = fmaT(f01, H[3 * fs + t], acc[3]);  // 21: (0,1)
-            acc[4] = fmaT(f00, H[4 * fs + t], acc[4]);  // 22: (0,0)
-            acc[5] = fmaT(f00, H[5 * fs + t], acc[5]);  // 23: (0,0)
-            acc[6] = fmaT(f01, H[6 * fs + t], acc[6]);  // 31: (0,1)
-            acc[7] = fmaT(f00, H[7 * fs + t], acc[7]);  // 32: (0,0)
-            acc[8] = fmaT(f00, H[8 * fs + t], acc[8]);  // 33: (0,0)
+        __syncthreads();
+        // items (alpha, line, i1); x-family (a1, b1) = ([alpha = 1], [beta = 1])
+        const int per = nl * n1;
+        for (int e = threadIdx.x; e < 3 * per; e += blockDim.x) {
+            const int al = e / per, rem = e - al * per;
+            const int l = rem / n1, i = rem - l * n1;
+            const int fam = 2 * (al == 0 ? 1 : 0) + bfam;
+            const int s = a.W.start[i], L = a.W.len[i];
+            const T* w = a.W.row(fam, i);
+            const T* H = sH + (al * kLines + l) * nq1 + s;
+            T acc = 0;
+            for (int t = 0; t < L; ++t) acc = fmaT(w[t], H[t], acc);
+            tout[(size_t)(3 * al + b) * tstride + (size_t)(line0 + l) * n1 + i] = acc;
         }
-        const size_t go = (size_t)(line0 + l) * n1 + i;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) tout.p[k][go] = acc[k];
     }
 }
 
@@ -682,15 +663,16 @@ int run_apply(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
     // trial y
     OpTrialY<T> oy{d2.B, Z0, Z1, Y[0], Y[1], Y[2]};
     if ((e = launch_slow(S_TRIAL_Y, oy, q3, n2, q2, n1, skip, c.stream)) != cudaSuccess) return MFWQ_ECUDA;
-    // x stage
+    // x stage (lines per block chosen by the autotuner: 2, 4 or 8)
     {
         XArgs<T> a = xargs(d1, q3 * q2, c.Nq, c.C);
-        size_t sm = sizeof(T) * ((size_t)3 * kLines * n1 + (size_t)9 * kLines * q1);
-        Ptr9<T> tp;
-        for (int k = 0; k < 9; ++k) tp.p[k] = Tt[k];
-        dim3 grid((q3 * q2 + kLines - 1) / kLines);
+        const int L = c.xlines == 2 || c.xlines == 8 ? c.xlines : 4;
+        size_t sm = sizeof(T) * ((size_t)3 * L * n1 + (size_t)3 * L * q1);
+        dim3 grid((q3 * q2 + L - 1) / L);
         launch_begin(S_XSTAGE, c.stream);
-        k_xstage_apply<T><<<grid, kThreads, sm, c.stream>>>(a, Y[0], Y[1], Y[2], tp, skip);
+        if (L == 2) k_xstage_apply<T, 2><<<grid, kThreads, sm, c.stream>>>(a, Y[0], Y[1], Y[2], Tt[0], SP, skip);
+        else if (L == 8) k_xstage_apply<T, 8><<<grid, kThreads, sm, c.stream>>>(a, Y[0], Y[1], Y[2], Tt[0], SP, skip);
+        else k_xstage_apply<T, 4><<<grid, kThreads, sm, c.stream>>>(a, Y[0], Y[1], Y[2], Tt[0], SP, skip);
         launch_end(S_XSTAGE, c.stream);
         if (cudaGetLastError() != cudaSuccess) return MFWQ_ECUDA;
     }
@@ -799,22 +781,33 @@ size_t rhs_scratch_elems(const int n[3], const int ng[3]) {
     return (size_t)ng[2] * ng[1] * n[0] + (size_t)ng[2] * n[1] * n[0];
 }
 
-int xstage_smem_bytes(int elem_size, int n1, int nq1) {
-    size_t a = (size_t)3 * kLines * n1 + (size_t)9 * kLines * nq1;
-    size_t b = (size_t)9 * kLines * n1 + (size_t)3 * kLines * nq1;
-    size_t c = (size_t)12 * kLines * n1;
-    size_t m = a > b ? a : b;
-    m = m > c ? m : c;
-    return (int)(m * elem_size);
+int xstage_smem_bytes(int elem_size, int n1, int nq1, int lines) {
+    return (int)(((size_t)3 * lines * n1 + (size_t)3 * lines * nq1) * elem_size);
 }
 
+int xstage_aux_smem_bytes(int elem_size, int n1, int nq1) {
+    size_t b = (size_t)9 * kLines * n1 + (size_t)3 * kLines * nq1;  // transposed x stage
+    size_t c = (size_t)12 * kLines * n1;                             // gradient x stage
+    return (int)((b > c ? b : c) * elem_size);
+}
+
+// The dynamic shared-memory limit is a per-kernel attribute shared by all
+// handles, so it only ever grows.
 int configure_xstage_smem(int bytes) {
+    static int configured = 0;
+    if (bytes <= configured) return MFWQ_OK;
     cudaError_t e = cudaSuccess;
-    e = cudaFuncSetAttribute(k_xstage_apply<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_applyT<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_grad<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_applyT<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    e = cudaFuncSetAttribute(k_xstage_apply<double, 2>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<double, 4>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<double, 8>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 2>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 4>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 8>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_applyT<double>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_grad<double>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_applyT<float>, A, bytes);
+    if (e == cudaSuccess) configured = bytes;
     return e == cudaSuccess ? MFWQ_OK : MFWQ_ECUDA;
 }
 

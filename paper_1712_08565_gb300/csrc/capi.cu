@@ -7,7 +7,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
 #include <new>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -114,6 +116,7 @@ struct mfwq_handle_s {
     double* part = nullptr;  // 2 kRedBlocks
     double* dnorm = nullptr; // 2 doubles
     int* derr = nullptr;     // device error word (bounded waits)
+    int xlines = 4, max_xlines = 4;  // forward x-stage lines per block (autotuned)
     KScal* dsc = nullptr;
     KScal* hsc = nullptr;    // pinned
     Profiler prof;
@@ -130,6 +133,7 @@ OpCtx<double> ctx64(mfwq_handle h) {
     c.Nq = h->Nq;
     c.scratch = static_cast<double*>(h->scratch);
     c.stream = h->stream;
+    c.xlines = h->xlines;
     return c;
 }
 
@@ -140,6 +144,7 @@ OpCtx<float> ctx32(mfwq_handle h) {
     c.Nq = h->Nq;
     c.scratch = static_cast<float*>(h->scratch);
     c.stream = h->stream;
+    c.xlines = h->xlines;
     return c;
 }
 
@@ -194,6 +199,7 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
     Arena a;
     BandOff bo[3][5];
     size_t U64[3], UT64[3], L64[3], U32[3], UT32[3], L32[3], XQ[3], XG[3];
+    size_t VE[3] = {}, VET[3] = {}, VO[3] = {}, VOT[3] = {}, LS[3] = {};
     for (int l = 0; l < 3; ++l) {
         const Dir1D& d = h->dir[l];
         bo[l][0] = stage_band(a, d.B);
@@ -209,6 +215,13 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
         L32[l] = a.add_vec(convert<float>(d.lam));
         XQ[l] = a.add_vec(d.xq);
         XG[l] = a.add_vec(d.xg);
+        if (d.sym) {
+            VE[l] = a.add_vec(d.Ve);
+            VET[l] = a.add_vec(d.VeT);
+            VO[l] = a.add_vec(d.Vo);
+            VOT[l] = a.add_vec(d.VoT);
+            LS[l] = a.add_vec(d.lam_split);
+        }
     }
     ST(dmalloc((void**)&h->d_tables, a.bytes.size()));
     CU(cudaMemcpy(h->d_tables, a.bytes.data(), a.bytes.size(), cudaMemcpyHostToDevice));
@@ -236,6 +249,19 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
         y.UT = reinterpret_cast<const float*>(base + UT32[l]);
         y.lam = reinterpret_cast<const float*>(base + L32[l]);
         x.xq = y.xq = reinterpret_cast<const double*>(base + XQ[l]);
+        x.sym = h->dir[l].sym ? 1 : 0;
+        y.sym = 0;
+        x.he = y.he = h->dir[l].he;
+        x.ho = y.ho = h->dir[l].ho;
+        x.Ve = x.VeT = x.Vo = x.VoT = x.lam_split = nullptr;
+        y.Ve = y.VeT = y.Vo = y.VoT = y.lam_split = nullptr;
+        if (h->dir[l].sym) {
+            x.Ve = reinterpret_cast<const double*>(base + VE[l]);
+            x.VeT = reinterpret_cast<const double*>(base + VET[l]);
+            x.Vo = reinterpret_cast<const double*>(base + VO[l]);
+            x.VoT = reinterpret_cast<const double*>(base + VOT[l]);
+            x.lam_split = reinterpret_cast<const double*>(base + LS[l]);
+        }
         x.xg = y.xg = reinterpret_cast<const double*>(base + XG[l]);
     }
 
@@ -268,8 +294,14 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
     CU(cudaMallocHost((void**)&h->hsc, sizeof(KScal)));
     CU(cudaMallocHost((void**)&h->hnorm, sizeof(double) * 2));
 
-    int smem = xstage_smem_bytes(8, h->n[0], h->nq[0]);
-    if (smem > 227 * 1024) return fail(MFWQ_EINVAL, "direction-1 size too large for the x-stage tile");
+    const int kSmemMax = 227 * 1024;
+    int smem = std::max(xstage_smem_bytes(8, h->n[0], h->nq[0], 4), xstage_aux_smem_bytes(8, h->n[0], h->nq[0]));
+    if (smem > kSmemMax) return fail(MFWQ_EINVAL, "direction-1 size too large for the x-stage tile");
+    h->max_xlines = 4;
+    if (xstage_smem_bytes(8, h->n[0], h->nq[0], 8) <= kSmemMax) {
+        smem = std::max(smem, xstage_smem_bytes(8, h->n[0], h->nq[0], 8));
+        h->max_xlines = 8;
+    }
     ST(configure_xstage_smem(smem));
     CU(cudaDeviceSynchronize());
     return MFWQ_OK;
@@ -539,7 +571,7 @@ int mfwq_grad_coeff(mfwq_handle h, const double* lambda_dev, const double* u_dev
 
 static const char* kStageNames[S_NTAGS] = {
     "trial_z", "trial_y", "xstage", "test_y", "test_z", "test_zT", "test_yT", "xstage_T", "trial_yT", "trial_zT",
-    "xstage_grad", "fd_dim1", "fd_dim23", "fd_tc", "krylov", "setup"};
+    "xstage_grad", "fd_dim1", "fd_dim23", "fd_tc", "krylov", "setup", "fd_fold"};
 
 const char* mfwq_stage_name(int stage) { return stage >= 0 && stage < S_NTAGS ? kStageNames[stage] : ""; }
 
@@ -582,3 +614,238 @@ int mfwq_sync(mfwq_handle h) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- autotuner
+namespace {
+std::string tune_key(mfwq_handle h) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "xstage_fp64 p=%d n1=%d nq1=%d nq2=%d nq3=%d", h->dir[0].p, h->n[0], h->nq[0], h->nq[1],
+                  h->nq[2]);
+    return buf;
+}
+
+// Cache file: one JSON object per line, {"key": "...", "xlines": L}.
+bool cache_lookup(const char* path, const std::string& key, int* val) {
+    if (!path || !*path) return false;
+    std::ifstream in(path);
+    std::string line;
+    const std::string k = "\"key\": \"" + key + "\"";
+    while (std::getline(in, line)) {
+        if (line.find(k) == std::string::npos) continue;
+        size_t p = line.find("\"xlines\":");
+        if (p == std::string::npos) continue;
+        int v = std::atoi(line.c_str() + p + 9);
+        if (v == 2 || v == 4 || v == 8) {
+            *val = v;
+            return true;
+        }
+    }
+    return false;
+}
+
+void cache_store(const char* path, const std::string& key, int val) {
+    if (!path || !*path) return;
+    std::ofstream out(path, std::ios::app);
+    out << "{\"key\": \"" << key << "\", \"xlines\": " << val << "}\n";
+}
+}  // namespace
+
+extern "C" int mfwq_autotune(mfwq_handle h, const char* cache_path, int* xlines_out) {
+    if (!h) return fail(MFWQ_EINVAL, "NULL handle");
+    ProfScope _ps(nullptr);
+    const std::string key = tune_key(h);
+    int best = 4;
+    if (!cache_lookup(cache_path, key, &best)) {
+        double* x = h->kv64;  // the Krylov work vectors serve as timing buffers
+        double* y = h->kv64 + h->N;
+        CU(cudaMemsetAsync(x, 0, sizeof(double) * h->N, h->stream));
+        cudaEvent_t e0, e1;
+        CU(cudaEventCreate(&e0));
+        CU(cudaEventCreate(&e1));
+        float best_ms = 1e30f;
+        for (int L : {2, 4, 8}) {
+            if (L > h->max_xlines) continue;
+            h->xlines = L;
+            OpCtx<double> c = ctx64(h);
+            ST(run_apply<double>(c, x, y, nullptr));
+            CU(cudaEventRecord(e0, h->stream));
+            for (int r = 0; r < 3; ++r) ST(run_apply<double>(c, x, y, nullptr));
+            CU(cudaEventRecord(e1, h->stream));
+            CU(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CU(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = L;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        cache_store(cache_path, key, best);
+    }
+    h->xlines = best > h->max_xlines ? h->max_xlines : best;
+    if (xlines_out) *xlines_out = h->xlines;
+    return MFWQ_OK;
+}
+
+// ---------------------------------------------------------------- batched solve
+struct mfwq_batch_s {
+    std::vector<mfwq_handle> h;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> join;
+    cudaStream_t origin = nullptr;
+    cudaEvent_t fork = nullptr;
+    KScal* dsc = nullptr;
+    KScal* hsc = nullptr;
+};
+
+namespace {
+void free_batch(mfwq_batch b) {
+    if (!b) return;
+    for (cudaStream_t s : b->streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+    if (b->origin) cudaStreamDestroy(b->origin);
+    if (b->fork) cudaEventDestroy(b->fork);
+    cudaFree(b->dsc);
+    if (b->hsc) cudaFreeHost(b->hsc);
+    delete b;
+}
+
+// Operators of patch i on the batch's stream i.
+struct PatchOps {
+    LinOp<double> A, P;
+};
+PatchOps patch_ops(mfwq_handle h, cudaStream_t s) {
+    OpCtx<double> c = ctx64(h);
+    c.stream = s;
+    DirD<double> d[3] = {h->d64[0], h->d64[1], h->d64[2]};
+    double* tmp = h->fd_tmp64;
+    PatchOps o;
+    o.A = [c](const double* in, double* out, const int* skip) { return run_apply<double>(c, in, out, skip); };
+    o.P = [d, tmp, s](const double* in, double* out, const int* skip) { return run_fd64(d, in, out, tmp, skip, s); };
+    return o;
+}
+}  // namespace
+
+extern "C" int mfwq_batch_create(int count, const mfwq_handle* patches, mfwq_batch* out) {
+    if (count < 1 || !patches || !out) return fail(MFWQ_EINVAL, "bad argument");
+    *out = nullptr;
+    mfwq_batch b = new (std::nothrow) mfwq_batch_s();
+    if (!b) return fail(MFWQ_ENOMEM, "host allocation failed");
+    int st = MFWQ_OK;
+    for (int i = 0; i < count && st == MFWQ_OK; ++i) {
+        if (!patches[i]) st = fail(MFWQ_EINVAL, "NULL patch handle");
+        b->h.push_back(patches[i]);
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        if (st == MFWQ_OK && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) st = fail(MFWQ_ECUDA, "stream");
+        if (st == MFWQ_OK && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) st = fail(MFWQ_ECUDA, "event");
+        if (s) b->streams.push_back(s);
+        if (e) b->join.push_back(e);
+    }
+    if (st == MFWQ_OK && cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess) st = fail(MFWQ_ECUDA, "stream");
+    if (st == MFWQ_OK && cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) st = fail(MFWQ_ECUDA, "event");
+    if (st == MFWQ_OK) st = dmalloc((void**)&b->dsc, sizeof(KScal) * count);
+    if (st == MFWQ_OK && cudaMallocHost((void**)&b->hsc, sizeof(KScal) * count) != cudaSuccess) st = fail(MFWQ_ENOMEM, "pinned");
+    if (st != MFWQ_OK) {
+        cudaGetLastError();
+        free_batch(b);
+        return st;
+    }
+    *out = b;
+    return MFWQ_OK;
+}
+
+extern "C" void mfwq_batch_destroy(mfwq_batch b) {
+    if (b && b->origin) cudaStreamSynchronize(b->origin);
+    free_batch(b);
+}
+
+extern "C" int mfwq_batch_solve(mfwq_batch b, const double* const* f_dev, double* const* u_dev, const mfwq_solve_opts* opts,
+                                mfwq_solve_info* infos) {
+    if (!b || !f_dev || !u_dev) return fail(MFWQ_EINVAL, "bad argument");
+    ProfScope _ps(nullptr);
+    const int count = (int)b->h.size();
+    mfwq_solve_opts o = opts ? *opts : default_opts();
+    if (!(o.rtol > 0) || o.maxit < 0) return fail(MFWQ_EINVAL, "rtol must be > 0 and maxit >= 0");
+    for (int i = 0; i < count; ++i)
+        if (!f_dev[i] || !u_dev[i] || f_dev[i] == u_dev[i]) return fail(MFWQ_EINVAL, "bad patch vectors");
+    std::vector<PatchOps> ops;
+    for (int i = 0; i < count; ++i) ops.push_back(patch_ops(b->h[i], b->streams[i]));
+    // initial residuals, every patch on its own stream
+    CU(cudaEventRecord(b->fork, b->origin));
+    for (int i = 0; i < count; ++i) {
+        mfwq_handle h = b->h[i];
+        CU(cudaStreamWaitEvent(b->streams[i], b->fork, 0));
+        ST(krylov_enqueue_init<double>(ops[i].A, f_dev[i], u_dev[i], o.use_initial_guess != 0, o.rtol, bufs64(h), &b->dsc[i],
+                                       h->part, h->N, b->streams[i]));
+        CU(cudaEventRecord(b->join[i], b->streams[i]));
+        CU(cudaStreamWaitEvent(b->origin, b->join[i], 0));
+    }
+    CU(cudaMemcpyAsync(b->hsc, b->dsc, sizeof(KScal) * count, cudaMemcpyDeviceToHost, b->origin));
+    CU(cudaStreamSynchronize(b->origin));
+    auto all_done = [&]() {
+        for (int i = 0; i < count; ++i)
+            if (!b->hsc[i].skip1) return false;
+        return true;
+    };
+    int sweeps = 0;
+    if (!all_done() && o.maxit > 0) {
+        // one BiCGStab iteration of every patch, captured once into a graph
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        CU(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+        int cst = MFWQ_OK;
+        if (cudaEventRecord(b->fork, b->origin) != cudaSuccess) cst = MFWQ_ECUDA;
+        for (int i = 0; i < count && cst == MFWQ_OK; ++i) {
+            mfwq_handle h = b->h[i];
+            if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) cst = MFWQ_ECUDA;
+            if (cst == MFWQ_OK)
+                cst = krylov_enqueue_iter<double>(ops[i].A, ops[i].P, f_dev[i], u_dev[i], bufs64(h), &b->dsc[i], h->part, h->N,
+                                                  b->streams[i]);
+            if (cst == MFWQ_OK && cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess) cst = MFWQ_ECUDA;
+            if (cst == MFWQ_OK && cudaStreamWaitEvent(b->origin, b->join[i], 0) != cudaSuccess) cst = MFWQ_ECUDA;
+        }
+        cudaError_t ce = cudaStreamEndCapture(b->origin, &graph);
+        if (cst != MFWQ_OK || ce != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return fail(MFWQ_ECUDA, "capture of the batched iteration failed");
+        }
+        if (cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            cudaGetLastError();
+            return fail(MFWQ_ECUDA, "cudaGraphInstantiate failed");
+        }
+        int st = MFWQ_OK;
+        for (sweeps = 0; sweeps < o.maxit; ++sweeps) {
+            if (cudaGraphLaunch(exec, b->origin) != cudaSuccess ||
+                cudaMemcpyAsync(b->hsc, b->dsc, sizeof(KScal) * count, cudaMemcpyDeviceToHost, b->origin) != cudaSuccess ||
+                cudaStreamSynchronize(b->origin) != cudaSuccess) {
+                st = fail(MFWQ_ECUDA, "batched sweep failed");
+                break;
+            }
+            if (all_done()) {
+                ++sweeps;
+                break;
+            }
+        }
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        if (st != MFWQ_OK) return st;
+    }
+    int worst = MFWQ_OK;
+    for (int i = 0; i < count; ++i) {
+        int it = 0, status = MFWQ_OK;
+        double rel = 0.0;
+        krylov_result(b->hsc[i], &it, &rel, &status);
+        if (infos) {
+            infos[i].status = status;
+            infos[i].iterations = it;
+            infos[i].outer_iterations = sweeps;
+            infos[i].rel_residual = rel;
+        }
+        if (status != MFWQ_OK && worst == MFWQ_OK) worst = status;
+    }
+    return worst;
+}

@@ -15,6 +15,7 @@ struct OpCtx {
     size_t Nq;
     T* scratch;        // apply_scratch_elems() elements of T
     cudaStream_t stream;
+    int xlines = 4;    // (q3, q2) lines per block of the forward x stage: 2, 4 or 8
 };
 
 // y = K~ x, y = K~^T x, g6 = dJ/dC (Algorithm 2 and its transpose).  A nonzero
@@ -28,7 +29,8 @@ int run_grad(const OpCtx<T>& c, const T* lam, const T* u, T* g6);
 
 size_t apply_scratch_elems(const int n[3], const int nq[3]);
 size_t rhs_scratch_elems(const int n[3], const int ng[3]);
-int xstage_smem_bytes(int elem_size, int n1, int nq1);
+int xstage_smem_bytes(int elem_size, int n1, int nq1, int lines);  // forward x stage
+int xstage_aux_smem_bytes(int elem_size, int n1, int nq1);         // transposed and gradient x stages
 int configure_xstage_smem(int bytes);
 
 int run_eval_coeff(const int nq[3], const double* const xq[3], int geom, const double* modes, int nmodes, double kscale,

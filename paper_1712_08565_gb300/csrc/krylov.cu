@@ -233,9 +233,7 @@ cudaError_t fin(KScal* sc, const double* part, cudaStream_t s) {
     } while (0)
 
 template <typename T>
-int bicgstab(const LinOp<T>& A, const LinOp<T>& P, const T* f, T* x, bool x_given, double rtol, int maxit,
-             const KrylovBufs<T>& b, KScal* dsc, KScal* hsc, double* part, size_t N, cudaStream_t s, int check_every,
-             double* hist, int* iters, double* relres, int* status) {
+static VArgs<T> vargs(const KrylovBufs<T>& b, const T* f, T* x, bool x_given, size_t N) {
     VArgs<T> a;
     a.N = N;
     a.f = f;
@@ -249,39 +247,67 @@ int bicgstab(const LinOp<T>& A, const LinOp<T>& P, const T* f, T* x, bool x_give
     a.ph = b.ph;
     a.sh = b.sh;
     a.x_given = x_given ? 1 : 0;
-    // scalars: rtol is set from the host, everything else by the init finish
+    return a;
+}
+
+template <typename T>
+int krylov_enqueue_init(const LinOp<T>& A, const T* f, T* x, bool x_given, double rtol, const KrylovBufs<T>& b,
+                        KScal* dsc, double* part, size_t N, cudaStream_t s) {
+    VArgs<T> a = vargs(b, f, x, x_given, N);
     KScal init{};
-    init.rtol = rtol;
+    init.rtol = rtol;  // everything else is set by the init finish kernel
     KTRY(cudaMemcpyAsync(dsc, &init, sizeof(KScal), cudaMemcpyHostToDevice, s));
     if (x_given) {
-        // r = f - A x0 (in r), using a zero skip flag
-        STRY(A(x, b.v, nullptr));
+        STRY(A(x, b.v, nullptr));  // r = f - A x0
         STRY(axpby_into(f, b.v, b.r, N, s));
     }
     KTRY((vec<T, V_INIT>(a, dsc, part, s)));
     KTRY(fin<V_INIT>(dsc, part, s));
+    return MFWQ_OK;
+}
+
+template <typename T>
+int krylov_enqueue_iter(const LinOp<T>& A, const LinOp<T>& P, const T* f, T* x, const KrylovBufs<T>& b, KScal* dsc,
+                        double* part, size_t N, cudaStream_t s) {
+    VArgs<T> a = vargs(b, f, x, false, N);
+    const int* skip1 = &dsc->skip1;
+    const int* skip2 = &dsc->skip2;
+    KTRY((vec<T, V_P>(a, dsc, part, s)));
+    STRY(P(b.p, b.ph, skip1));
+    STRY(A(b.ph, b.v, skip1));
+    KTRY((vec<T, V_DOT_RV>(a, dsc, part, s)));
+    KTRY(fin<V_DOT_RV>(dsc, part, s));
+    KTRY((vec<T, V_S>(a, dsc, part, s)));
+    KTRY(fin<V_S>(dsc, part, s));
+    STRY(P(b.s, b.sh, skip2));
+    STRY(A(b.sh, b.t, skip2));
+    KTRY((vec<T, V_DOT_TS>(a, dsc, part, s)));
+    KTRY(fin<V_DOT_TS>(dsc, part, s));
+    KTRY((vec<T, V_XR>(a, dsc, part, s)));
+    KTRY(fin<V_XR>(dsc, part, s));
+    return MFWQ_OK;
+}
+
+void krylov_result(const KScal& h, int* iters, double* relres, int* status) {
+    *iters = h.iters;
+    *relres = h.f2 > 0 ? std::sqrt(h.r2 / h.f2) : 0.0;
+    int st = h.status;
+    if (st == MFWQ_OK && !(h.r2 <= h.tol2) && h.f2 > 0) st = MFWQ_ENOCONV;
+    *status = st;
+}
+
+template <typename T>
+int bicgstab(const LinOp<T>& A, const LinOp<T>& P, const T* f, T* x, bool x_given, double rtol, int maxit,
+             const KrylovBufs<T>& b, KScal* dsc, KScal* hsc, double* part, size_t N, cudaStream_t s, int check_every,
+             double* hist, int* iters, double* relres, int* status) {
+    STRY(krylov_enqueue_init<T>(A, f, x, x_given, rtol, b, dsc, part, N, s));
     KTRY(cudaMemcpyAsync(hsc, dsc, sizeof(KScal), cudaMemcpyDeviceToHost, s));
     KTRY(cudaStreamSynchronize(s));
     if (hist) hist[0] = hsc->f2 > 0 ? std::sqrt(hsc->r2 / hsc->f2) : 0.0;
-    int it = 0;
     if (!hsc->skip1) {
-        const int* skip1 = &dsc->skip1;
-        const int* skip2 = &dsc->skip2;
         if (check_every < 1) check_every = 1;
-        for (it = 0; it < maxit; ++it) {
-            KTRY((vec<T, V_P>(a, dsc, part, s)));
-            STRY(P(b.p, b.ph, skip1));
-            STRY(A(b.ph, b.v, skip1));
-            KTRY((vec<T, V_DOT_RV>(a, dsc, part, s)));
-            KTRY(fin<V_DOT_RV>(dsc, part, s));
-            KTRY((vec<T, V_S>(a, dsc, part, s)));
-            KTRY(fin<V_S>(dsc, part, s));
-            STRY(P(b.s, b.sh, skip2));
-            STRY(A(b.sh, b.t, skip2));
-            KTRY((vec<T, V_DOT_TS>(a, dsc, part, s)));
-            KTRY(fin<V_DOT_TS>(dsc, part, s));
-            KTRY((vec<T, V_XR>(a, dsc, part, s)));
-            KTRY(fin<V_XR>(dsc, part, s));
+        for (int it = 0; it < maxit; ++it) {
+            STRY(krylov_enqueue_iter<T>(A, P, f, x, b, dsc, part, N, s));
             if ((it + 1) % check_every == 0 || it + 1 == maxit || hist) {
                 KTRY(cudaMemcpyAsync(hsc, dsc, sizeof(KScal), cudaMemcpyDeviceToHost, s));
                 KTRY(cudaStreamSynchronize(s));
@@ -292,11 +318,7 @@ int bicgstab(const LinOp<T>& A, const LinOp<T>& P, const T* f, T* x, bool x_give
     }
     KTRY(cudaMemcpyAsync(hsc, dsc, sizeof(KScal), cudaMemcpyDeviceToHost, s));
     KTRY(cudaStreamSynchronize(s));
-    *iters = hsc->iters;
-    *relres = hsc->f2 > 0 ? std::sqrt(hsc->r2 / hsc->f2) : 0.0;
-    int st = hsc->status;
-    if (st == MFWQ_OK && !(hsc->r2 <= hsc->tol2) && hsc->f2 > 0) st = MFWQ_ENOCONV;
-    *status = st;
+    krylov_result(*hsc, iters, relres, status);
     return MFWQ_OK;
 }
 
@@ -366,6 +388,14 @@ int add_f32_scaled(double* u, const float* d, const double* nrm2, size_t N, cuda
 
 template int axpby_into<double>(const double*, const double*, double*, size_t, cudaStream_t);
 template int axpby_into<float>(const float*, const float*, float*, size_t, cudaStream_t);
+template int krylov_enqueue_init<double>(const LinOp<double>&, const double*, double*, bool, double,
+                                          const KrylovBufs<double>&, KScal*, double*, size_t, cudaStream_t);
+template int krylov_enqueue_init<float>(const LinOp<float>&, const float*, float*, bool, double, const KrylovBufs<float>&,
+                                         KScal*, double*, size_t, cudaStream_t);
+template int krylov_enqueue_iter<double>(const LinOp<double>&, const LinOp<double>&, const double*, double*,
+                                          const KrylovBufs<double>&, KScal*, double*, size_t, cudaStream_t);
+template int krylov_enqueue_iter<float>(const LinOp<float>&, const LinOp<float>&, const float*, float*,
+                                         const KrylovBufs<float>&, KScal*, double*, size_t, cudaStream_t);
 template int bicgstab<double>(const LinOp<double>&, const LinOp<double>&, const double*, double*, bool, double, int,
                               const KrylovBufs<double>&, KScal*, KScal*, double*, size_t, cudaStream_t, int, double*, int*,
                               double*, int*);

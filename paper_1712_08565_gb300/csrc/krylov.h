@@ -37,6 +37,17 @@ int bicgstab(const LinOp<T>& A, const LinOp<T>& P, const T* f, T* x, bool x_give
              const KrylovBufs<T>& b, KScal* dsc, KScal* hsc, double* part, size_t N, cudaStream_t s, int check_every,
              double* hist, int* iters, double* relres, int* status);
 
+// Enqueue-only pieces of the same solver (no host synchronisation), for
+// callers that capture iterations into CUDA graphs: the init kernels, one
+// iteration, and the conversion of a scalar block read back to the host.
+template <typename T>
+int krylov_enqueue_init(const LinOp<T>& A, const T* f, T* x, bool x_given, double rtol, const KrylovBufs<T>& b,
+                        KScal* dsc, double* part, size_t N, cudaStream_t s);
+template <typename T>
+int krylov_enqueue_iter(const LinOp<T>& A, const LinOp<T>& P, const T* f, T* x, const KrylovBufs<T>& b, KScal* dsc,
+                        double* part, size_t N, cudaStream_t s);
+void krylov_result(const KScal& h, int* iters, double* relres, int* status);
+
 template <typename T>
 int axpby_into(const T* f, const T* v, T* r, size_t N, cudaStream_t s);  // r = f - v
 int norm2_into(const double* x, size_t N, double* part, double* out, cudaStream_t s);  // *out = |x|^2

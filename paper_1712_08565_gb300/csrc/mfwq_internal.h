@@ -40,6 +40,12 @@ struct Dir1D {
     Band1D WT;   // rows q -> rows i, transposed W
     Band1D GT;   // rows j -> Gauss points g, value b_j(x_g) * w_g
     std::vector<double> U, UT, lam;  // FD: U [n][n] row-major, UT = U^T, lam[n]
+    // FD even/odd split (knots symmetric about 1/2): he = n - n/2 even and
+    // ho = n/2 odd modes; Ve [he][he], Vo [ho][ho] act on the folded vector
+    // (x_j + x_{n-1-j}, middle; x_j - x_{n-1-j}); lam_split = (lam_even, lam_odd).
+    bool sym = false;
+    int he = 0, ho = 0;
+    std::vector<double> Ve, VeT, Vo, VoT, lam_split;
 };
 
 // Host setup (setup_host.cpp).  Return MFWQ_* codes; `why` gets a message.
@@ -65,6 +71,12 @@ struct DirD {
     const T* U;     // [n][n]
     const T* UT;    // [n][n]
     const T* lam;   // [n]
+    int sym, he, ho;   // FD even/odd split (FP64 only)
+    const double* Ve;
+    const double* VeT;
+    const double* Vo;
+    const double* VoT;
+    const double* lam_split;
     const double* xq;  // points (always FP64)
     const double* xg;  // Gauss points (always FP64)
 };

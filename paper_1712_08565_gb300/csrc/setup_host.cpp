@@ -390,6 +390,44 @@ bool jacobi_eig(std::vector<double>& A, int n, std::vector<double>& ev, std::vec
     return false;
 }
 
+// Generalized symmetric eigenproblem K U = M U diag(lam) with U^T M U = I:
+// M = L L^T, L^-1 K L^-T = V diag(lam) V^T (cyclic Jacobi), U = L^-T V.
+bool gen_eig(const std::vector<double>& K, const std::vector<double>& M, int n, std::vector<double>& lam,
+             std::vector<double>& U, std::string& why) {
+    std::vector<double> L;
+    if (!cholesky(L, M, n)) { why = "1D mass matrix is not SPD"; return false; }
+    std::vector<double> X((size_t)n * n), A((size_t)n * n);
+    for (int c = 0; c < n; ++c)  // X = L^-1 K
+        for (int i = 0; i < n; ++i) {
+            double s = K[(size_t)i * n + c];
+            for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * X[(size_t)k * n + c];
+            X[(size_t)i * n + c] = s / L[(size_t)i * n + i];
+        }
+    for (int r = 0; r < n; ++r)  // A = X L^-T
+        for (int i = 0; i < n; ++i) {
+            double s = X[(size_t)r * n + i];
+            for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * A[(size_t)r * n + k];
+            A[(size_t)r * n + i] = s / L[(size_t)i * n + i];
+        }
+    for (int i = 0; i < n; ++i)
+        for (int j = i + 1; j < n; ++j) {
+            double s = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
+            A[(size_t)i * n + j] = A[(size_t)j * n + i] = s;
+        }
+    std::vector<double> V;
+    if (!jacobi_eig(A, n, lam, V)) { why = "Jacobi eigensolver did not converge"; return false; }
+    U.assign((size_t)n * n, 0.0);
+    for (int c = 0; c < n; ++c)  // U = L^-T V
+        for (int i = n - 1; i >= 0; --i) {
+            double s = V[(size_t)i * n + c];
+            for (int k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * U[(size_t)k * n + c];
+            U[(size_t)i * n + c] = s / L[(size_t)i * n + i];
+        }
+    for (int i = 0; i < n; ++i)
+        if (!(lam[i] > 0.0)) { why = "FD eigenvalue not positive"; return false; }
+    return true;
+}
+
 }  // namespace
 
 int validate_knots(int p, int nknots, const double* t, std::string& why) {
@@ -637,47 +675,65 @@ int build_dir(int p, int nknots, const double* knots, Dir1D& d, std::string& why
         transpose_band(S, d.GT);
     }
 
-    // FD factors: K_l = G^{11}, M_l = G^{00}; M = L L^T, L^-1 K L^-T = V Lambda V^T,
-    // U = L^-T V, so U^T M U = I and U^T K U = Lambda.
-    {
-        std::vector<double> L;
-        if (!cholesky(L, Gal[0], n)) { why = "1D mass matrix is not SPD"; return MFWQ_ESETUP; }
-        const std::vector<double>& K = Gal[3];
-        // X = L^-1 K  (forward substitution, column by column)
-        std::vector<double> X((size_t)n * n), A((size_t)n * n);
-        for (int c = 0; c < n; ++c)
-            for (int i = 0; i < n; ++i) {
-                double s = K[(size_t)i * n + c];
-                for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * X[(size_t)k * n + c];
-                X[(size_t)i * n + c] = s / L[(size_t)i * n + i];
-            }
-        // A = X L^-T = (L^-1 X^T)^T ; A symmetric
-        for (int r = 0; r < n; ++r)
-            for (int i = 0; i < n; ++i) {
-                double s = X[(size_t)r * n + i];
-                for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * A[(size_t)r * n + k];
-                A[(size_t)r * n + i] = s / L[(size_t)i * n + i];
-            }
-        for (int i = 0; i < n; ++i)
-            for (int j = i + 1; j < n; ++j) {
-                double s = 0.5 * (A[(size_t)i * n + j] + A[(size_t)j * n + i]);
-                A[(size_t)i * n + j] = A[(size_t)j * n + i] = s;
-            }
-        std::vector<double> V;
-        if (!jacobi_eig(A, n, d.lam, V)) { why = "Jacobi eigensolver did not converge"; return MFWQ_ESETUP; }
-        // U = L^-T V (back substitution with L^T)
-        d.U.assign((size_t)n * n, 0.0);
-        for (int c = 0; c < n; ++c)
-            for (int i = n - 1; i >= 0; --i) {
-                double s = V[(size_t)i * n + c];
-                for (int k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * d.U[(size_t)k * n + c];
-                d.U[(size_t)i * n + c] = s / L[(size_t)i * n + i];
-            }
-        d.UT.assign((size_t)n * n, 0.0);
-        for (int i = 0; i < n; ++i)
-            for (int j = 0; j < n; ++j) d.UT[(size_t)j * n + i] = d.U[(size_t)i * n + j];
-        for (int i = 0; i < n; ++i)
-            if (!(d.lam[i] > 0.0)) { why = "FD eigenvalue not positive"; return MFWQ_ESETUP; }
+    // FD factors: K_l = G^{11}, M_l = G^{00}; U^T M U = I, U^T K U = diag(lambda).
+    if (!gen_eig(Gal[3], Gal[0], n, d.lam, d.U, why)) return MFWQ_ESETUP;
+    d.UT.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) d.UT[(size_t)j * n + i] = d.U[(size_t)i * n + j];
+
+    // Even/odd split for knot vectors symmetric about 1/2: then K_l and M_l
+    // commute with the index reversal J, the eigenvectors can be taken even
+    // (Ju = u) or odd (Ju = -u), and U^T x splits into two half-size products
+    // on the folded vector x_j +- x_{n-1-j}.  Even basis: (e_j + e_{n-1-j})/sqrt2
+    // (j < h) and e_h (odd n); odd basis: (e_j - e_{n-1-j})/sqrt2.
+    d.sym = true;
+    for (int i = 0; i < nknots; ++i)
+        if (std::fabs(t[i] + t[nknots - 1 - i] - 1.0) > 1e-14) d.sym = false;
+    if (d.sym) {
+        const int h = n / 2, he = n - h, ho = h;
+        d.he = he;
+        d.ho = ho;
+        const double r2 = std::sqrt(0.5);
+        auto basis = [&](int parity, int col, int row) -> double {  // column col of E (parity 0) or O (1)
+            if (parity == 0 && col == h) return row == h ? 1.0 : 0.0;  // middle (odd n)
+            if (row == col) return r2;
+            if (row == n - 1 - col) return parity == 0 ? r2 : -r2;
+            return 0.0;
+        };
+        for (int parity = 0; parity < 2; ++parity) {
+            const int m2 = parity == 0 ? he : ho;
+            std::vector<double> Kh((size_t)m2 * m2, 0.0), Mh((size_t)m2 * m2, 0.0);
+            for (int a = 0; a < m2; ++a)
+                for (int b = 0; b < m2; ++b) {
+                    double sk = 0.0, sm = 0.0;
+                    for (int i = 0; i < n; ++i) {
+                        const double ea = basis(parity, a, i);
+                        if (ea == 0.0) continue;
+                        for (int j = 0; j < n; ++j) {
+                            const double eb = basis(parity, b, j);
+                            if (eb == 0.0) continue;
+                            sk += ea * Gal[3][(size_t)i * n + j] * eb;
+                            sm += ea * Gal[0][(size_t)i * n + j] * eb;
+                        }
+                    }
+                    Kh[(size_t)a * m2 + b] = sk;
+                    Mh[(size_t)a * m2 + b] = sm;
+                }
+            std::vector<double> lh, Uh;
+            if (!gen_eig(Kh, Mh, m2, lh, Uh, why)) return MFWQ_ESETUP;
+            // V = D U with D the folding scale: 1/sqrt2 on paired rows, 1 on the middle row
+            std::vector<double>& V = parity == 0 ? d.Ve : d.Vo;
+            std::vector<double>& VT = parity == 0 ? d.VeT : d.VoT;
+            V.assign((size_t)m2 * m2, 0.0);
+            VT.assign((size_t)m2 * m2, 0.0);
+            for (int i = 0; i < m2; ++i)
+                for (int j = 0; j < m2; ++j) {
+                    const double sc = (parity == 0 && i == h) ? 1.0 : r2;
+                    V[(size_t)i * m2 + j] = sc * Uh[(size_t)i * m2 + j];
+                    VT[(size_t)j * m2 + i] = V[(size_t)i * m2 + j];
+                }
+            for (int i = 0; i < m2; ++i) d.lam_split.push_back(lh[i]);
+        }
     }
     return MFWQ_OK;
 }

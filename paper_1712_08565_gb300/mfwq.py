@@ -40,7 +40,7 @@ class SolveOpts(ctypes.Structure):
 
 
 class ProfileStats(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 16), ("launches", ctypes.c_longlong * 16)]
+    _fields_ = [("ms", ctypes.c_double * 24), ("launches", ctypes.c_longlong * 24)]
 
 
 class SolveInfoC(ctypes.Structure):
@@ -100,6 +100,11 @@ _SIGS = [
     ("mfwq_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ProfileStats), ctypes.c_int]),
     ("mfwq_stage_name", ctypes.c_char_p, [ctypes.c_int]),
     ("mfwq_kernel_launches", ctypes.c_longlong, []),
+    ("mfwq_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]),
+    ("mfwq_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p)]),
+    ("mfwq_batch_destroy", None, [ctypes.c_void_p]),
+    ("mfwq_batch_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                        ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfoC)]),
     ("mfwq_fd_precond_noalloc", ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p),
                                                ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -367,6 +372,12 @@ class Operator:
     def sync(self):
         _check(lib().mfwq_sync(self._h))
 
+    def autotune(self, cache_path: str | None = None) -> int:
+        """Pick the x-stage lines per block by timing (mfwq_autotune); returns it."""
+        v = ctypes.c_int()
+        _check(lib().mfwq_autotune(self._h, cache_path.encode() if cache_path else None, ctypes.byref(v)))
+        return v.value
+
     def profile(self, on: bool = True):
         """Bracket every later kernel launch with CUDA events (per-stage timing)."""
         _check(lib().mfwq_profile_enable(self._h, 1 if on else 0))
@@ -376,7 +387,7 @@ class Operator:
         st = ProfileStats()
         _check(lib().mfwq_profile_read(self._h, ctypes.byref(st), 1 if reset else 0))
         out = {}
-        for i in range(16):
+        for i in range(24):
             if st.launches[i]:
                 out[lib().mfwq_stage_name(i).decode()] = (st.ms[i], int(st.launches[i]))
         return out
@@ -424,3 +435,42 @@ def solve_fn():
     if _SOLVE_FN is None:
         _SOLVE_FN = _make_solve_function()
     return _SOLVE_FN
+
+
+class Batch:
+    """Independent patches solved together (mfwq_batch_*): one CUDA graph
+    launch per BiCGStab sweep over all patches.  The operators stay owned by
+    the caller and must outlive the batch."""
+
+    def __init__(self, ops):
+        self.ops = list(ops)
+        arr = (ctypes.c_void_p * len(self.ops))(*[op._h.value for op in self.ops])
+        h = ctypes.c_void_p()
+        _check(lib().mfwq_batch_create(len(self.ops), arr, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mfwq_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, fs, us=None, rtol=1e-8, maxit=500, check=False):
+        import torch
+        n = len(self.ops)
+        us = us if us is not None else [torch.empty_like(f) for f in fs]
+        fp = (ctypes.c_void_p * n)(*[_ptr(fs[i], torch.float64, self.ops[i].N, self.ops[i].device).value for i in range(n)])
+        up = (ctypes.c_void_p * n)(*[_ptr(us[i], torch.float64, self.ops[i].N, self.ops[i].device).value for i in range(n)])
+        o = SolveOpts()
+        o.rtol = rtol
+        o.maxit = maxit
+        infos = (SolveInfoC * n)()
+        st = lib().mfwq_batch_solve(self._h, fp, up, ctypes.byref(o), infos)
+        if st not in (MFWQ_OK, -6, -5, -8) or (check and st != MFWQ_OK):
+            _check(st)
+        return us, [SolveInfo(x.status, x.iterations, x.outer_iterations, x.rel_residual) for x in infos]

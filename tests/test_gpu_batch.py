@@ -1,0 +1,89 @@
+"""GPU tests of the batched solve of independent patches (one CUDA graph
+launch per BiCGStab sweep) and of the x-stage autotuner."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1712_08565_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def mf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1712_08565_gb300 import build
+    build.build()
+    from paper_1712_08565_gb300 import mfwq
+    return mfwq
+
+
+def _patch(mf, p, nel, seed):
+    knots = [inputs.open_uniform_knots(p, nel[l]) for l in range(3)]
+    op = mf.Operator(p, knots, device=DEV)
+    modes = inputs.fourier_modes(seed)
+    op.set_coeff(op.eval_coeff("ring", modes, 0.3))
+    return op
+
+
+def test_batch_equals_separate_solves(mf):
+    """Patches of uneven degree and size (the shape of the 64-patch workload,
+    scaled down): the batched solve gives bit-for-bit the separate solves
+    (same kernels, same deterministic reductions, independent patches)."""
+    specs = inputs.batch_patches(count=6, seed=3, nel_range=(3, 12))
+    ops = [_patch(mf, p, nel, i) for i, (p, nel) in enumerate(specs)]
+    fs = [op.load_vector("ring", "sines") for op in ops]
+    ref = [op.solve(f, rtol=1e-8, force_fp64=True) for op, f in zip(ops, fs)]
+    b = mf.Batch(ops)
+    us, infos = b.solve(fs, rtol=1e-8, maxit=500)
+    for (u0, i0), u, i in zip(ref, us, infos):
+        assert i.converged and i0.converged
+        assert i.iterations == i0.iterations
+        assert torch.equal(u, u0)
+    assert max(i.outer_iterations for i in infos) == max(i.iterations for i in infos)
+    b.close()
+    # and the solutions satisfy each patch's system, checked by the oracle
+    for (p, nel), op, f, u in zip(specs, ops, fs, us):
+        tabs = [O.tables_1d(inputs.open_uniform_knots(p, nel[l]), p) for l in range(3)]
+        C6 = O.coefficient_grid(tabs, "ring", inputs.fourier_modes(ops.index(op)), 0.3)
+        K = O.stiffness_wq(tabs, O.full_coeff(C6))
+        fn = f.cpu().numpy().ravel()
+        res = np.linalg.norm(fn - K @ u.cpu().numpy().ravel()) / np.linalg.norm(fn)
+        assert res <= 2e-8
+        op.close()
+
+
+def test_batch_with_converged_patch_and_maxit(mf):
+    ops = [_patch(mf, 3, (5, 6, 7), 0), _patch(mf, 2, (8, 4, 6), 1)]
+    fs = [torch.zeros(ops[0].shape, dtype=torch.float64, device=DEV), ops[1].load_vector("ring", "sines")]
+    b = mf.Batch(ops)
+    us, infos = b.solve(fs, rtol=1e-10)
+    assert infos[0].converged and infos[0].iterations == 0 and float(us[0].abs().max()) == 0.0
+    assert infos[1].converged and infos[1].iterations > 0
+    us, infos = b.solve(fs, rtol=1e-14, maxit=1)
+    assert infos[1].status == -6 and infos[1].iterations == 1
+    b.close()
+    for op in ops:
+        op.close()
+
+
+def test_autotune_keeps_parity(mf, tmp_path):
+    p, nel = 4, (9, 8, 10)
+    op = _patch(mf, p, nel, 2)
+    cache = str(tmp_path / "tune.jsonl")
+    L = op.autotune(cache)
+    assert L in (2, 4, 8)
+    assert os.path.exists(cache) and '"xlines": %d' % L in open(cache).read()
+    assert op.autotune(cache) == L  # cache hit
+    tabs = [O.tables_1d(inputs.open_uniform_knots(p, nel[l]), p) for l in range(3)]
+    C6 = O.coefficient_grid(tabs, "ring", inputs.fourier_modes(2), 0.3)
+    x = inputs.uniform_vector(op.shape, 9)
+    ref = O.apply_alg2(tabs, O.full_coeff(C6), x)
+    y = op.apply(torch.from_numpy(x).to(DEV)).cpu().numpy()
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    op.close()
