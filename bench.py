@@ -39,6 +39,7 @@ METRIC = "MF-WQ apply DoF/s & FD-precond solve time, p=2-6; mixed vs FP64 at 1e-
 WORKLOAD = dict(name="ring-p4-nel128", p=4, nel=128, geometry="ring", forcing="sines", rtol=1e-10)
 SWEEP_P = (2, 3, 4, 5, 6)
 MIXED = dict(name="ring-p6-nel192", p=6, nel=192, rtol=1e-8)
+BATCH = dict(name="ring-batch64", count=64, seed=0, rtol=1e-8, kscale=0.3)
 NUM_SMS = 152
 SM_MAX_MHZ_NOMINAL = 2070.0
 FP64_FLOP_PER_CLK_SM = 4  # 2 FP64 FMA per clock per SM: 1.25 TFLOP/s nominal / (152 SMs x 2.07 GHz)
@@ -114,6 +115,21 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def reduce_over_ranks(ms_step, units, device=None):
+    """Replica timing across ranks: the slowest rank's time per step and the
+    units (DoF-applies) processed by all ranks together.  Single process:
+    returned unchanged."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms_step, units
+    t = torch.tensor([ms_step], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def band_lens(dense_rows):
     """Band length (first to last nonzero) of each row of a dense table."""
     out = []
@@ -149,51 +165,63 @@ def fp64_peak_tflops(sm_mhz=None):
 
 
 # --------------------------------------------------------------------------- oracle (CPU) baseline
-def oracle_iteration_sample(reps=1):
-    """Time the oracle's Algorithm-2 apply and FD apply at the full workload
-    size on the host cores; one BiCGStab iteration costs two of each."""
-    import oracle as O
-    from paper_1712_08565_gb300 import inputs
-    p, nel = WORKLOAD["p"], WORKLOAD["nel"]
-    tabs = O.uniform_tables(p, nel)
-    C6 = O.coefficient_grid(tabs, WORKLOAD["geometry"])
-    Cf = O.full_coeff(C6)
-    fd = O.fd_setup(tabs)
-    V = inputs.uniform_vector((tabs[2].n, tabs[1].n, tabs[0].n), 1)
-    ta, tf = [], []
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        O.apply_alg2(tabs, Cf, V)
-        t1 = time.perf_counter()
-        O.fd_apply(fd, V)
-        t2 = time.perf_counter()
-        ta.append(t1 - t0)
-        tf.append(t2 - t1)
-    N = tabs[0].n * tabs[1].n * tabs[2].n
-    t_iter = 2 * (min(ta) + min(tf))
-    return {"value": 2 * N / t_iter, "unit": "DoF/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"oracle Algorithm-2 apply ({min(ta):.2f} s) and FD apply ({min(tf):.2f} s) at the full "
-                       f"{WORKLOAD['name']} size (numpy/BLAS on all host cores); one BiCGStab iteration = 2 of each, "
-                       f"value = 2N / iteration time"),
-            "apply_s": min(ta), "fd_s": min(tf)}
+class OracleIteration:
+    """The oracle's Algorithm-2 apply and FD apply at the full workload size on
+    the host cores (numpy/BLAS); one BiCGStab iteration costs two of each.
+    Setup (tables, coefficient, FD factors) happens once, outside the timing."""
+
+    def __init__(self):
+        import oracle as O
+        from paper_1712_08565_gb300 import inputs
+        self.O = O
+        p, nel = WORKLOAD["p"], WORKLOAD["nel"]
+        self.tabs = O.uniform_tables(p, nel)
+        self.Cf = O.full_coeff(O.coefficient_grid(self.tabs, WORKLOAD["geometry"]))
+        self.fd = O.fd_setup(self.tabs)
+        self.V = inputs.uniform_vector((self.tabs[2].n, self.tabs[1].n, self.tabs[0].n), 1)
+        self.N = self.V.size
+
+    def step(self):
+        """One sample: 2 applies + 2 FD applies; returns (apply_s, fd_s) of the faster half."""
+        ta, tf = [], []
+        for _ in range(2):
+            t0 = time.perf_counter()
+            self.O.apply_alg2(self.tabs, self.Cf, self.V)
+            t1 = time.perf_counter()
+            self.O.fd_apply(self.fd, self.V)
+            t2 = time.perf_counter()
+            ta.append(t1 - t0)
+            tf.append(t2 - t1)
+        return sum(ta), sum(tf)
+
+    def describe(self, t_apply, t_fd):
+        t_iter = t_apply + t_fd
+        return {"value": 2 * self.N / t_iter, "unit": "DoF/s", "cores": os.cpu_count(), "kind": "oracle",
+                "sample": (f"one BiCGStab iteration's operators on the host: 2 oracle Algorithm-2 applies "
+                           f"({t_apply:.2f} s) + 2 oracle FD applies ({t_fd:.2f} s) at the full {WORKLOAD['name']} size "
+                           f"(numpy/BLAS on all host cores); value = 2N / that time")}
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    it = OracleIteration()
     for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state; setup is outside the timed region
+        it.step()
     t0 = time.perf_counter()
-    samples = [oracle_iteration_sample(1) for _ in range(max(1, args.steps))]
+    samples = [it.step() for _ in range(max(1, args.steps))]
     t1 = time.perf_counter()
-    best = max(samples, key=lambda s: s["value"])
-    line = {"impl": "reference", "metric": METRIC, "value": best["value"], "unit": "DoF/s", "n_gpus": args.gpus,
+    ta = statistics.mean(a for a, _ in samples)
+    tf = statistics.mean(f for _, f in samples)
+    cb = it.describe(ta, tf)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "DoF/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * (t1 - t0) / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"], "p": WORKLOAD["p"], "nel": WORKLOAD["nel"]},
-            "cpu_baseline": {k: best[k] for k in ("value", "unit", "cores", "kind", "sample")},
-            "e2e": {"value": best["value"], "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": {"workload": WORKLOAD["name"], "p": WORKLOAD["p"], "nel": WORKLOAD["nel"],
+                       "step": "the operators of one BiCGStab iteration (2 applies + 2 FD applies), oracle on the host"},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -282,6 +310,58 @@ def mixed_vs_fp64(mf, device):
     return res
 
 
+def batched(mf, device):
+    """64 independent ring patches of uneven degree and size, each with its own
+    K = exp(0.3 g) field: one batched FP64 solve (one CUDA graph launch per
+    BiCGStab sweep) against the same solves run one after the other."""
+    import torch
+    from paper_1712_08565_gb300 import inputs
+    specs = inputs.batch_patches(count=BATCH["count"], seed=BATCH["seed"])
+    ops, fs = [], []
+    t0 = time.perf_counter()
+    tune = os.path.join(tempfile.gettempdir(), "mfwq_autotune.jsonl")
+    lines = {}
+    for i, (p, nel) in enumerate(specs):
+        knots = [inputs.open_uniform_knots(p, nel[l]) for l in range(3)]
+        op = mf.Operator(p, knots, device=device)
+        op.set_coeff(op.eval_coeff("ring", inputs.fourier_modes(1000 + i), BATCH["kscale"]))
+        L = op.autotune(tune)
+        lines[L] = lines.get(L, 0) + 1
+        ops.append(op)
+        fs.append(op.load_vector("ring", "sines"))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    N = sum(op.N for op in ops)
+    b = mf.Batch(ops)
+    us = [torch.empty_like(f) for f in fs]
+    b.solve(fs, us, rtol=BATCH["rtol"])  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, infos = b.solve(fs, us, rtol=BATCH["rtol"])
+    torch.cuda.synchronize()
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    seq_iters = []
+    for op, f, u in zip(ops, fs, us):
+        _, inf = op.solve(f, u=None, rtol=BATCH["rtol"], force_fp64=True)
+        seq_iters.append(inf.iterations)
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    applies = 2 * sum(i.iterations for i in infos)
+    res = {"workload": BATCH["name"], "patches": len(ops), "N_total": N, "rtol": BATCH["rtol"],
+           "setup_s": setup_s, "batched_s": tb, "sequential_s": ts, "speedup_vs_sequential": ts / tb,
+           "sweeps": max(i.outer_iterations for i in infos), "iterations_min_max": [min(i.iterations for i in infos), max(i.iterations for i in infos)],
+           "all_converged": all(i.converged for i in infos),
+           "apply_dof_per_s": sum(2 * i.iterations * op.N for i, op in zip(infos, ops)) / tb,
+           "autotuned_xlines": {str(k): v for k, v in sorted(lines.items())}}
+    b.close()
+    for op in ops:
+        op.close()
+    del fs, us
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -337,13 +417,9 @@ def run_ours(args):
     stages = op.profile_read(reset=True)
     op.profile(False)
     ms_step = ms_total / args.steps
-    if ws > 1:
-        t = torch.tensor([ms_step], device=device)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
     applies_per_solve = 2 * statistics.mean(iters)
-    value_rank = op.N * applies_per_solve / (ms_step * 1e-3)
-    value = value_rank * ws
+    ms_step, units = reduce_over_ranks(ms_step, op.N * applies_per_solve, device)
+    value = units / (ms_step * 1e-3)
 
     # roofline of the dominant kernel (largest share of the timed region)
     flops, n, nq = stage_flops(mf, p, knots)
@@ -388,6 +464,7 @@ def run_ours(args):
     if not args.no_extras:
         extras["p_sweep_nel128"] = p_sweep(mf, device)
         extras["mixed_vs_fp64"] = mixed_vs_fp64(mf, device)
+        extras["batched_64"] = batched(mf, device)
     line = {
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -407,7 +484,9 @@ def run_ours(args):
     }
     line.update(extras)
     if rank == 0 and not args.no_extras:
-        line["cpu_baseline"] = {k: v for k, v in oracle_iteration_sample(1).items() if k in ("value", "unit", "cores", "kind", "sample")}
+        it = OracleIteration()
+        ta, tf = it.step()
+        line["cpu_baseline"] = it.describe(ta, tf)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -335,10 +335,9 @@ __global__ void __launch_bounds__(kThreads) k_xstage_apply(XArgs<T> a, const T* 
         for (int e = threadIdx.x; e < nl * nq1; e += blockDim.x) {
             const int l = e / nq1, q = e - l * nq1;
             const int s = a.B.start[q], L = a.B.len[q];
-            const T* bb = a.B.row(bfam, q);
             const T* Y = sY + (b * kLines + l) * n1 + s;
             T g = 0;
-            for (int t = 0; t < L; ++t) g = fmaT(bb[t], Y[t], g);
+            for (int t = 0; t < L; ++t) g = fmaT(a.B.lane(bfam, q, t), Y[t], g);
             const size_t pt = (size_t)(line0 + l) * nq1 + q;
             T* H = sH + l * nq1 + q;
             const int hs = kLines * nq1;
@@ -355,10 +354,9 @@ __global__ void __launch_bounds__(kThreads) k_xstage_apply(XArgs<T> a, const T* 
             const int l = rem / n1, i = rem - l * n1;
             const int fam = 2 * (al == 0 ? 1 : 0) + bfam;
             const int s = a.W.start[i], L = a.W.len[i];
-            const T* w = a.W.row(fam, i);
             const T* H = sH + (al * kLines + l) * nq1 + s;
             T acc = 0;
-            for (int t = 0; t < L; ++t) acc = fmaT(w[t], H[t], acc);
+            for (int t = 0; t < L; ++t) acc = fmaT(a.W.lane(fam, i, t), H[t], acc);
             tout[(size_t)(3 * al + b) * tstride + (size_t)(line0 + l) * n1 + i] = acc;
         }
     }
@@ -387,17 +385,13 @@ __global__ void __launch_bounds__(kThreads) k_xstage_applyT(XArgs<T> a, Ptr9<T> 
     for (int e = threadIdx.x; e < nl * nq1; e += blockDim.x) {
         const int l = e / nq1, q = e - l * nq1;
         const int s = a.WT.start[q], L = a.WT.len[q];
-        const T* w00 = a.WT.row(0, q);
-        const T* w01 = a.WT.row(1, q);
-        const T* w10 = a.WT.row(2, q);
-        const T* w11 = a.WT.row(3, q);
         const int fs = kLines * n1;
         const T* R = sR + l * n1 + s;
         T S[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) S[k] = 0;
         for (int t = 0; t < L; ++t) {
-            const T f00 = w00[t], f01 = w01[t], f10 = w10[t], f11 = w11[t];
+            const T f00 = a.WT.lane(0, q, t), f01 = a.WT.lane(1, q, t), f10 = a.WT.lane(2, q, t), f11 = a.WT.lane(3, q, t);
             S[0] = fmaT(f11, R[0 * fs + t], S[0]);
             S[1] = fmaT(f10, R[1 * fs + t], S[1]);
             S[2] = fmaT(f10, R[2 * fs + t], S[2]);
@@ -421,15 +415,14 @@ __global__ void __launch_bounds__(kThreads) k_xstage_applyT(XArgs<T> a, Ptr9<T> 
     for (int e = threadIdx.x; e < nl * n1; e += blockDim.x) {
         const int l = e / n1, j = e - l * n1;
         const int s = a.BT.start[j], L = a.BT.len[j];
-        const T* b0 = a.BT.row(0, j);
-        const T* b1 = a.BT.row(1, j);
         const int es = kLines * nq1;
         const T* E = sE + l * nq1 + s;
         T o1 = 0, o2 = 0, o3 = 0;
         for (int t = 0; t < L; ++t) {
-            o1 = fmaT(b1[t], E[0 * es + t], o1);
-            o2 = fmaT(b0[t], E[1 * es + t], o2);
-            o3 = fmaT(b0[t], E[2 * es + t], o3);
+            const T b0 = a.BT.lane(0, j, t), b1 = a.BT.lane(1, j, t);
+            o1 = fmaT(b1, E[0 * es + t], o1);
+            o2 = fmaT(b0, E[1 * es + t], o2);
+            o3 = fmaT(b0, E[2 * es + t], o3);
         }
         const size_t go = (size_t)(line0 + l) * n1 + j;
         x1[go] = o1;
@@ -465,13 +458,12 @@ __global__ void __launch_bounds__(kThreads) k_xstage_grad(XArgs<T> a, const T* _
         T g1 = 0, g2 = 0, g3 = 0;
         {
             const int s = a.B.start[q], L = a.B.len[q];
-            const T* b0 = a.B.row(0, q);
-            const T* b1 = a.B.row(1, q);
             const T* Y = sY + l * n1 + s;
             for (int t = 0; t < L; ++t) {
-                g1 = fmaT(b1[t], Y[0 * fs + t], g1);
-                g2 = fmaT(b0[t], Y[1 * fs + t], g2);
-                g3 = fmaT(b0[t], Y[2 * fs + t], g3);
+                const T b0 = a.B.lane(0, q, t), b1 = a.B.lane(1, q, t);
+                g1 = fmaT(b1, Y[0 * fs + t], g1);
+                g2 = fmaT(b0, Y[1 * fs + t], g2);
+                g3 = fmaT(b0, Y[2 * fs + t], g3);
             }
         }
         T S[9];
@@ -479,13 +471,9 @@ __global__ void __launch_bounds__(kThreads) k_xstage_grad(XArgs<T> a, const T* _
         for (int k = 0; k < 9; ++k) S[k] = 0;
         {
             const int s = a.WT.start[q], L = a.WT.len[q];
-            const T* w00 = a.WT.row(0, q);
-            const T* w01 = a.WT.row(1, q);
-            const T* w10 = a.WT.row(2, q);
-            const T* w11 = a.WT.row(3, q);
             const T* R = sR + l * n1 + s;
             for (int t = 0; t < L; ++t) {
-                const T f00 = w00[t], f01 = w01[t], f10 = w10[t], f11 = w11[t];
+                const T f00 = a.WT.lane(0, q, t), f01 = a.WT.lane(1, q, t), f10 = a.WT.lane(2, q, t), f11 = a.WT.lane(3, q, t);
                 S[0] = fmaT(f11, R[0 * fs + t], S[0]);
                 S[1] = fmaT(f10, R[1 * fs + t], S[1]);
                 S[2] = fmaT(f10, R[2 * fs + t], S[2]);
@@ -632,9 +620,8 @@ __global__ void __launch_bounds__(kThreads) k_rhs_x(int geom, int forcing, BandD
     __syncthreads();
     for (int j = threadIdx.x; j < n1; j += blockDim.x) {
         const int s = GT1.start[j], L = GT1.len[j];
-        const double* b = GT1.row(0, j);
         double acc = 0.0;
-        for (int t = 0; t < L; ++t) acc = fmaT(b[t], sF[s + t], acc);
+        for (int t = 0; t < L; ++t) acc = fmaT(GT1.lane(0, j, t), sF[s + t], acc);
         out[(size_t)line * n1 + j] = acc;
     }
 }

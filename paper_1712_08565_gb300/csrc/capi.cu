@@ -69,7 +69,7 @@ std::vector<T> convert(const std::vector<double>& v) {
 }
 
 struct BandOff {
-    size_t start, len, v64, v32;
+    size_t start, len, v64, v32, t64, t32;
     int rows, width;
 };
 
@@ -79,6 +79,12 @@ BandOff stage_band(Arena& a, const Band1D& b) {
     o.len = a.add_vec(b.len);
     o.v64 = a.add_vec(b.val);
     o.v32 = a.add_vec(convert<float>(b.val));
+    std::vector<double> t(b.val.size());  // lane-major copy [fams][width][rows]
+    for (int f = 0; f < b.fams; ++f)
+        for (int r = 0; r < b.rows; ++r)
+            for (int k = 0; k < b.width; ++k) t[((size_t)f * b.width + k) * b.rows + r] = b.at(f, r, k);
+    o.t64 = a.add_vec(t);
+    o.t32 = a.add_vec(convert<float>(t));
     o.rows = b.rows;
     o.width = b.width;
     return o;
@@ -90,6 +96,7 @@ BandD<T> band_at(unsigned char* base, const BandOff& o) {
     b.start = reinterpret_cast<const int*>(base + o.start);
     b.len = reinterpret_cast<const int*>(base + o.len);
     b.val = reinterpret_cast<const T*>(base + (sizeof(T) == 8 ? o.v64 : o.v32));
+    b.valT = reinterpret_cast<const T*>(base + (sizeof(T) == 8 ? o.t64 : o.t32));
     b.rows = o.rows;
     b.width = o.width;
     return b;

@@ -131,32 +131,47 @@ struct TcArgs {
 
 // Stage one K chunk (kc) of rows [row0, row0 + rows) of a row-major matrix
 // src[nrows][ncols] into the canonical layout at dst (row-major core
-// matrices: byte (r/8)*1024 + (kb/16)*128 + (r%8)*16 + kb%16).
+// matrices: byte (r/8)*1024 + (kb/16)*128 + (r%8)*16 + kb%16).  A warp covers
+// 4 rows x 8 consecutive elements per step; each thread issues its loads 16
+// at a time into registers before storing them, so the loads are in flight
+// together instead of one load-store pair after another.
 template <int KIND>
 __device__ __forceinline__ void stage_chunk(unsigned char* dst, const float* __restrict__ src, int nrows, int ncols,
                                             int row0, int rows, int kc) {
-    constexpr int EB = KIND == 0 ? 4 : 2;         // operand bytes
-    constexpr int KE = kChunkBytes / EB;          // elements per chunk row
+    constexpr int EB = KIND == 0 ? 4 : 2;  // operand bytes
+    constexpr int KE = kChunkBytes / EB;   // elements per chunk row
+    constexpr int GROUPS = KE / 8;         // 8-element groups per row
+    constexpr int BATCH = 16;
     const int tid = threadIdx.x;
-    // a warp covers 4 rows x 8 consecutive elements per step
-    const int total = rows * KE;
-    for (int e = tid; e < total; e += kTcThreads) {
-        const int warp_e = e >> 5, lane = e & 31;
-        const int per_row_groups = KE / 8;
-        const int rg = warp_e / per_row_groups;       // group of 4 rows
-        const int kg = warp_e - rg * per_row_groups;  // group of 8 elements
-        const int r = rg * 4 + (lane >> 3);
-        const int k = kg * 8 + (lane & 7);
-        if (r >= rows) continue;
-        const int gr = row0 + r, gk = kc * KE + k;
-        float v = 0.f;
-        if (gr < nrows && gk < ncols) v = src[(size_t)gr * ncols + gk];
-        const int kb = k * EB;
-        unsigned char* p = dst + (r >> 3) * 1024 + (kb >> 4) * 128 + (r & 7) * 16 + (kb & 15);
-        if (KIND == 0) {
-            *reinterpret_cast<float*>(p) = v;
-        } else {
-            *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(v);
+    const int per_thread = rows * KE / kTcThreads;  // rows is a multiple of 16
+    for (int base = 0; base < per_thread; base += BATCH) {
+        float v[BATCH];
+        int off[BATCH];
+#pragma unroll
+        for (int j = 0; j < BATCH; ++j) {
+            const int idx = base + j;
+            v[j] = 0.f;
+            off[j] = -1;
+            if (idx < per_thread) {
+                const int e = tid + idx * kTcThreads;
+                const int warp_e = e >> 5, lane = e & 31;
+                const int rg = warp_e / GROUPS, kg = warp_e - rg * GROUPS;
+                const int r = rg * 4 + (lane >> 3);
+                const int k = kg * 8 + (lane & 7);
+                const int gr = row0 + r, gk = kc * KE + k;
+                if (gr < nrows && gk < ncols) v[j] = src[(size_t)gr * ncols + gk];
+                const int kb = k * EB;
+                off[j] = (r >> 3) * 1024 + (kb >> 4) * 128 + (r & 7) * 16 + (kb & 15);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < BATCH; ++j) {
+            if (off[j] < 0) continue;
+            if (KIND == 0) {
+                *reinterpret_cast<float*>(dst + off[j]) = v[j];
+            } else {
+                *reinterpret_cast<__nv_bfloat16*>(dst + off[j]) = __float2bfloat16_rn(v[j]);
+            }
         }
     }
 }

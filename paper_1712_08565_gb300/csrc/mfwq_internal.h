@@ -57,11 +57,14 @@ template <typename T>
 struct BandD {
     const int* start;
     const int* len;
-    const T* val;      // [fams][rows][width]
+    const T* val;      // [fams][rows][width]: a row's values contiguous (one row per block)
+    const T* valT;     // [fams][width][rows]: the same values lane-major (consecutive rows per warp)
     int rows, width;
     MFWQ_HD const T* row(int f, int r) const {
         return val + ((size_t)f * rows + r) * width;
     }
+    // value t of row r, family f, from the lane-major copy
+    MFWQ_HD T lane(int f, int r, int t) const { return valT[((size_t)f * width + t) * rows + r]; }
 };
 
 template <typename T>
