@@ -353,7 +353,7 @@ def batched(mf, device):
            "sweeps": max(i.outer_iterations for i in infos), "iterations_min_max": [min(i.iterations for i in infos), max(i.iterations for i in infos)],
            "all_converged": all(i.converged for i in infos),
            "apply_dof_per_s": sum(2 * i.iterations * op.N for i, op in zip(infos, ops)) / tb,
-           "autotuned_xlines": {str(k): v for k, v in sorted(lines.items())}}
+           "autotuned_xstage": {str(k): v for k, v in sorted(lines.items())}}
     b.close()
     for op in ops:
         op.close()

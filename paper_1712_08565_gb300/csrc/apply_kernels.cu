@@ -305,61 +305,121 @@ constexpr int kLines = 4;
 
 // Forward x stage: Y (3 inputs [line][n1]) -> T (9 outputs [line][n1]).
 // The nine products are formed three at a time, one trial direction beta at a
-// time: G_b on the line's points (B1 in direction 1 for beta = 1, else B0),
+// time: G_b on the lines' points (B1 in direction 1 for beta = 1, else B0),
 // H^(ab) = C_ab G_b for alpha = 1..3 in shared memory, then the three test
-// contractions with W1^(a1,b1).  Per line the block keeps 3 n1 + 3 nq1
-// values in shared memory, so several blocks share an SM and their load,
-// product and contraction phases overlap.
-template <typename T, int LINES>
+// contractions with W1^(a1,b1).  Two work mappings (chosen by the autotuner):
+//  MODE 0: a thread owns one (line, point) or one (alpha, line, i) item
+//          (most items in flight; best for the FP64 pipe);
+//  MODE 1: a thread owns one point or one (alpha, i) output for all LINES
+//          lines, so each band coefficient it loads serves LINES multiply-adds
+//          (fewest loads; best when the FP32 pipe leaves the loads exposed).
+template <typename T, int LINES, int MODE>
 __global__ void __launch_bounds__(kThreads) k_xstage_apply(XArgs<T> a, const T* __restrict__ y0, const T* __restrict__ y1,
                                                            const T* __restrict__ y2, T* __restrict__ tout, size_t tstride,
                                                            const int* skip) {
     if (skip && *skip) return;
-    constexpr int kLines = LINES;
     extern __shared__ unsigned char smem_raw[];
-    T* sY = reinterpret_cast<T*>(smem_raw);        // [3][kLines][n1]
-    T* sH = sY + 3 * kLines * a.n1;                // [3][kLines][nq1]
-    const int line0 = blockIdx.x * kLines;
-    const int nl = min(kLines, a.nlines - line0);
+    T* sY = reinterpret_cast<T*>(smem_raw);  // [3][LINES][n1]
+    T* sH = sY + 3 * LINES * a.n1;           // [3][LINES][nq1]
+    const int line0 = blockIdx.x * LINES;
+    const int nl = min(LINES, a.nlines - line0);
     const int n1 = a.n1, nq1 = a.nq1;
+    const int hs = LINES * nq1;
     for (int e = threadIdx.x; e < nl * n1; e += blockDim.x) {
         const int l = e / n1, j = e - l * n1;
         const size_t gi = (size_t)(line0 + l) * n1 + j;
-        sY[(0 * kLines + l) * n1 + j] = y0[gi];
-        sY[(1 * kLines + l) * n1 + j] = y1[gi];
-        sY[(2 * kLines + l) * n1 + j] = y2[gi];
+        sY[(0 * LINES + l) * n1 + j] = y0[gi];
+        sY[(1 * LINES + l) * n1 + j] = y1[gi];
+        sY[(2 * LINES + l) * n1 + j] = y2[gi];
     }
     for (int b = 0; b < 3; ++b) {
         __syncthreads();
         const int bfam = b == 0 ? 1 : 0;
-        for (int e = threadIdx.x; e < nl * nq1; e += blockDim.x) {
-            const int l = e / nq1, q = e - l * nq1;
-            const int s = a.B.start[q], L = a.B.len[q];
-            const T* Y = sY + (b * kLines + l) * n1 + s;
-            T g = 0;
-            for (int t = 0; t < L; ++t) g = fmaT(a.B.lane(bfam, q, t), Y[t], g);
-            const size_t pt = (size_t)(line0 + l) * nq1 + q;
-            T* H = sH + l * nq1 + q;
-            const int hs = kLines * nq1;
-            // symmetric-storage slot of C_(alpha,beta): alpha for alpha = beta, else 2 + alpha + beta
-            H[0 * hs] = a.C[(b == 0 ? 0 : 2 + b) * a.Nq + pt] * g;
-            H[1 * hs] = a.C[(b == 1 ? 1 : 3 + b) * a.Nq + pt] * g;
-            H[2 * hs] = a.C[(b == 2 ? 2 : 4 + b) * a.Nq + pt] * g;
+        // symmetric-storage slots of C_(alpha,beta), alpha = 1..3: alpha if alpha = beta, else 2 + alpha + beta
+        const size_t c0 = (size_t)(b == 0 ? 0 : 2 + b) * a.Nq;
+        const size_t c1 = (size_t)(b == 1 ? 1 : 3 + b) * a.Nq;
+        const size_t c2 = (size_t)(b == 2 ? 2 : 4 + b) * a.Nq;
+        if (MODE == 0) {
+            for (int e = threadIdx.x; e < nl * nq1; e += blockDim.x) {
+                const int l = e / nq1, q = e - l * nq1;
+                const int s = a.B.start[q], L = a.B.len[q];
+                const T* Y = sY + (b * LINES + l) * n1 + s;
+                T g = 0;
+                for (int t = 0; t < L; ++t) g = fmaT(a.B.lane(bfam, q, t), Y[t], g);
+                const size_t pt = (size_t)(line0 + l) * nq1 + q;
+                T* H = sH + l * nq1 + q;
+                H[0 * hs] = a.C[c0 + pt] * g;
+                H[1 * hs] = a.C[c1 + pt] * g;
+                H[2 * hs] = a.C[c2 + pt] * g;
+            }
+        } else {
+            for (int q = threadIdx.x; q < nq1; q += blockDim.x) {
+                const int s = a.B.start[q], L = a.B.len[q];
+                T g[LINES];
+#pragma unroll
+                for (int l = 0; l < LINES; ++l) g[l] = 0;
+                const T* Y = sY + (b * LINES) * n1 + s;
+                for (int t = 0; t < L; ++t) {
+                    const T bt = a.B.lane(bfam, q, t);
+#pragma unroll
+                    for (int l = 0; l < LINES; ++l) g[l] = fmaT(bt, Y[l * n1 + t], g[l]);
+                }
+#pragma unroll
+                for (int l = 0; l < LINES; ++l) {
+                    if (l >= nl) break;
+                    const size_t pt = (size_t)(line0 + l) * nq1 + q;
+                    T* H = sH + l * nq1 + q;
+                    H[0 * hs] = a.C[c0 + pt] * g[l];
+                    H[1 * hs] = a.C[c1 + pt] * g[l];
+                    H[2 * hs] = a.C[c2 + pt] * g[l];
+                }
+            }
         }
         __syncthreads();
-        // items (alpha, line, i1); x-family (a1, b1) = ([alpha = 1], [beta = 1])
-        const int per = nl * n1;
-        for (int e = threadIdx.x; e < 3 * per; e += blockDim.x) {
-            const int al = e / per, rem = e - al * per;
-            const int l = rem / n1, i = rem - l * n1;
-            const int fam = 2 * (al == 0 ? 1 : 0) + bfam;
-            const int s = a.W.start[i], L = a.W.len[i];
-            const T* H = sH + (al * kLines + l) * nq1 + s;
-            T acc = 0;
-            for (int t = 0; t < L; ++t) acc = fmaT(a.W.lane(fam, i, t), H[t], acc);
-            tout[(size_t)(3 * al + b) * tstride + (size_t)(line0 + l) * n1 + i] = acc;
+        // outputs; x-family (a1, b1) = ([alpha = 1], [beta = 1])
+        if (MODE == 0) {
+            const int per = nl * n1;
+            for (int e = threadIdx.x; e < 3 * per; e += blockDim.x) {
+                const int al = e / per, rem = e - al * per;
+                const int l = rem / n1, i = rem - l * n1;
+                const int fam = 2 * (al == 0 ? 1 : 0) + bfam;
+                const int s = a.W.start[i], L = a.W.len[i];
+                const T* H = sH + (al * LINES + l) * nq1 + s;
+                T acc = 0;
+                for (int t = 0; t < L; ++t) acc = fmaT(a.W.lane(fam, i, t), H[t], acc);
+                tout[(size_t)(3 * al + b) * tstride + (size_t)(line0 + l) * n1 + i] = acc;
+            }
+        } else {
+            for (int e = threadIdx.x; e < 3 * n1; e += blockDim.x) {
+                const int al = e / n1, i = e - al * n1;
+                const int fam = 2 * (al == 0 ? 1 : 0) + bfam;
+                const int s = a.W.start[i], L = a.W.len[i];
+                const T* H = sH + (al * LINES) * nq1 + s;
+                T acc[LINES];
+#pragma unroll
+                for (int l = 0; l < LINES; ++l) acc[l] = 0;
+                for (int t = 0; t < L; ++t) {
+                    const T wt = a.W.lane(fam, i, t);
+#pragma unroll
+                    for (int l = 0; l < LINES; ++l) acc[l] = fmaT(wt, H[l * nq1 + t], acc[l]);
+                }
+                T* o = tout + (size_t)(3 * al + b) * tstride + (size_t)line0 * n1 + i;
+#pragma unroll
+                for (int l = 0; l < LINES; ++l) {
+                    if (l >= nl) break;
+                    o[(size_t)l * n1] = acc[l];
+                }
+            }
         }
     }
+}
+
+template <typename T, int MODE>
+void launch_xstage(int L, dim3 grid, size_t sm, cudaStream_t st, const XArgs<T>& a, const T* y0, const T* y1, const T* y2,
+                   T* tout, size_t tstride, const int* skip) {
+    if (L == 2) k_xstage_apply<T, 2, MODE><<<grid, kThreads, sm, st>>>(a, y0, y1, y2, tout, tstride, skip);
+    else if (L == 8) k_xstage_apply<T, 8, MODE><<<grid, kThreads, sm, st>>>(a, y0, y1, y2, tout, tstride, skip);
+    else k_xstage_apply<T, 4, MODE><<<grid, kThreads, sm, st>>>(a, y0, y1, y2, tout, tstride, skip);
 }
 
 // Transposed x stage: R (9 inputs [line][n1]) -> S^(ab) = W1^T R at q1 ->
@@ -657,9 +717,8 @@ int run_apply(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
         size_t sm = sizeof(T) * ((size_t)3 * L * n1 + (size_t)3 * L * q1);
         dim3 grid((q3 * q2 + L - 1) / L);
         launch_begin(S_XSTAGE, c.stream);
-        if (L == 2) k_xstage_apply<T, 2><<<grid, kThreads, sm, c.stream>>>(a, Y[0], Y[1], Y[2], Tt[0], SP, skip);
-        else if (L == 8) k_xstage_apply<T, 8><<<grid, kThreads, sm, c.stream>>>(a, Y[0], Y[1], Y[2], Tt[0], SP, skip);
-        else k_xstage_apply<T, 4><<<grid, kThreads, sm, c.stream>>>(a, Y[0], Y[1], Y[2], Tt[0], SP, skip);
+        if (c.xmode == 1) launch_xstage<T, 1>(L, grid, sm, c.stream, a, Y[0], Y[1], Y[2], Tt[0], SP, skip);
+        else launch_xstage<T, 0>(L, grid, sm, c.stream, a, Y[0], Y[1], Y[2], Tt[0], SP, skip);
         launch_end(S_XSTAGE, c.stream);
         if (cudaGetLastError() != cudaSuccess) return MFWQ_ECUDA;
     }
@@ -785,12 +844,18 @@ int configure_xstage_smem(int bytes) {
     if (bytes <= configured) return MFWQ_OK;
     cudaError_t e = cudaSuccess;
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    e = cudaFuncSetAttribute(k_xstage_apply<double, 2>, A, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<double, 4>, A, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<double, 8>, A, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 2>, A, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 4>, A, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 8>, A, bytes);
+    e = cudaFuncSetAttribute(k_xstage_apply<double, 2, 0>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<double, 4, 0>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<double, 8, 0>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 2, 0>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 4, 0>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 8, 0>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<double, 2, 1>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<double, 4, 1>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<double, 8, 1>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 2, 1>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 4, 1>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 8, 1>, A, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_applyT<double>, A, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_grad<double>, A, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_applyT<float>, A, bytes);

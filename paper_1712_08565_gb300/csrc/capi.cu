@@ -123,7 +123,9 @@ struct mfwq_handle_s {
     double* part = nullptr;  // 2 kRedBlocks
     double* dnorm = nullptr; // 2 doubles
     int* derr = nullptr;     // device error word (bounded waits)
-    int xlines = 4, max_xlines = 4;  // forward x-stage lines per block (autotuned)
+    int xlines = 4, max_xlines = 4;  // forward x-stage lines per block, FP64 (autotuned)
+    int xmode = 0;                   // FP64 x-stage work mapping (autotuned)
+    int xlines32 = 4, xmode32 = 1;   // the same for the FP32 operator
     KScal* dsc = nullptr;
     KScal* hsc = nullptr;    // pinned
     Profiler prof;
@@ -141,6 +143,7 @@ OpCtx<double> ctx64(mfwq_handle h) {
     c.scratch = static_cast<double*>(h->scratch);
     c.stream = h->stream;
     c.xlines = h->xlines;
+    c.xmode = h->xmode;
     return c;
 }
 
@@ -151,7 +154,8 @@ OpCtx<float> ctx32(mfwq_handle h) {
     c.Nq = h->Nq;
     c.scratch = static_cast<float*>(h->scratch);
     c.stream = h->stream;
-    c.xlines = h->xlines;
+    c.xlines = h->xlines32;
+    c.xmode = h->xmode32;
     return c;
 }
 
@@ -626,12 +630,11 @@ int mfwq_sync(mfwq_handle h) {
 namespace {
 std::string tune_key(mfwq_handle h) {
     char buf[160];
-    std::snprintf(buf, sizeof buf, "xstage_fp64 p=%d n1=%d nq1=%d nq2=%d nq3=%d", h->dir[0].p, h->n[0], h->nq[0], h->nq[1],
-                  h->nq[2]);
+    std::snprintf(buf, sizeof buf, "xstage p=%d n1=%d nq1=%d nq2=%d nq3=%d", h->dir[0].p, h->n[0], h->nq[0], h->nq[1], h->nq[2]);
     return buf;
 }
 
-// Cache file: one JSON object per line, {"key": "...", "xlines": L}.
+// Cache file: one JSON object per line, {"key": "...", "xstage": 10 * mode + lines}.
 bool cache_lookup(const char* path, const std::string& key, int* val) {
     if (!path || !*path) return false;
     std::ifstream in(path);
@@ -639,10 +642,10 @@ bool cache_lookup(const char* path, const std::string& key, int* val) {
     const std::string k = "\"key\": \"" + key + "\"";
     while (std::getline(in, line)) {
         if (line.find(k) == std::string::npos) continue;
-        size_t p = line.find("\"xlines\":");
+        size_t p = line.find("\"xstage\":");
         if (p == std::string::npos) continue;
         int v = std::atoi(line.c_str() + p + 9);
-        if (v == 2 || v == 4 || v == 8) {
+        if (v % 10 == 2 || v % 10 == 4 || v % 10 == 8) {
             *val = v;
             return true;
         }
@@ -653,45 +656,76 @@ bool cache_lookup(const char* path, const std::string& key, int* val) {
 void cache_store(const char* path, const std::string& key, int val) {
     if (!path || !*path) return;
     std::ofstream out(path, std::ios::app);
-    out << "{\"key\": \"" << key << "\", \"xlines\": " << val << "}\n";
+    out << "{\"key\": \"" << key << "\", \"xstage\": " << val << "}\n";
+}
+}  // namespace
+
+namespace {
+// Times the forward apply for every (lines, mode) pair in one precision and
+// returns the fastest encoded as 10 * mode + lines.
+template <typename T>
+int tune_xstage(mfwq_handle h, bool f32, int* err) {
+    T* x = reinterpret_cast<T*>(f32 ? (void*)h->kv32 : (void*)h->kv64);  // Krylov work vectors as timing buffers
+    T* y = x + h->N;
+    *err = MFWQ_OK;
+    if (cudaMemsetAsync(x, 0, sizeof(T) * h->N, h->stream) != cudaSuccess) { *err = MFWQ_ECUDA; return 4; }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) { *err = MFWQ_ECUDA; return 4; }
+    float best_ms = 1e30f;
+    int best = f32 ? 14 : 4;
+    for (int mode = 0; mode < 2; ++mode)
+        for (int L : {2, 4, 8}) {
+            if (L > h->max_xlines) continue;
+            OpCtx<T> c;
+            for (int l = 0; l < 3; ++l) c.d[l] = f32 ? *(DirD<T>*)&h->d32[l] : *(DirD<T>*)&h->d64[l];
+            c.C = f32 ? (const T*)h->C32 : (const T*)h->C64;
+            c.Nq = h->Nq;
+            c.scratch = static_cast<T*>(h->scratch);
+            c.stream = h->stream;
+            c.xlines = L;
+            c.xmode = mode;
+            if (run_apply<T>(c, x, y, nullptr) != MFWQ_OK) { *err = MFWQ_ECUDA; break; }
+            cudaEventRecord(e0, h->stream);
+            for (int r = 0; r < 3; ++r) run_apply<T>(c, x, y, nullptr);
+            cudaEventRecord(e1, h->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = 10 * mode + L;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cudaGetLastError() != cudaSuccess) *err = MFWQ_ECUDA;
+    return best;
 }
 }  // namespace
 
 extern "C" int mfwq_autotune(mfwq_handle h, const char* cache_path, int* xlines_out) {
     if (!h) return fail(MFWQ_EINVAL, "NULL handle");
     ProfScope _ps(nullptr);
-    const std::string key = tune_key(h);
-    int best = 4;
-    if (!cache_lookup(cache_path, key, &best)) {
-        double* x = h->kv64;  // the Krylov work vectors serve as timing buffers
-        double* y = h->kv64 + h->N;
-        CU(cudaMemsetAsync(x, 0, sizeof(double) * h->N, h->stream));
-        cudaEvent_t e0, e1;
-        CU(cudaEventCreate(&e0));
-        CU(cudaEventCreate(&e1));
-        float best_ms = 1e30f;
-        for (int L : {2, 4, 8}) {
-            if (L > h->max_xlines) continue;
-            h->xlines = L;
-            OpCtx<double> c = ctx64(h);
-            ST(run_apply<double>(c, x, y, nullptr));
-            CU(cudaEventRecord(e0, h->stream));
-            for (int r = 0; r < 3; ++r) ST(run_apply<double>(c, x, y, nullptr));
-            CU(cudaEventRecord(e1, h->stream));
-            CU(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CU(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = L;
-            }
+    for (int prec = 0; prec < (h->mixed ? 2 : 1); ++prec) {
+        const std::string key = tune_key(h) + (prec ? " fp32" : " fp64");
+        int code = 0;
+        if (!cache_lookup(cache_path, key, &code)) {
+            int err = MFWQ_OK;
+            code = prec ? tune_xstage<float>(h, true, &err) : tune_xstage<double>(h, false, &err);
+            if (err != MFWQ_OK) return fail(err, "autotune: a timing launch failed");
+            cache_store(cache_path, key, code);
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
-        cache_store(cache_path, key, best);
+        int L = code % 10, mode = code / 10;
+        if (L > h->max_xlines) L = h->max_xlines;
+        if (prec) {
+            h->xlines32 = L;
+            h->xmode32 = mode;
+        } else {
+            h->xlines = L;
+            h->xmode = mode;
+        }
     }
-    h->xlines = best > h->max_xlines ? h->max_xlines : best;
-    if (xlines_out) *xlines_out = h->xlines;
+    if (xlines_out) *xlines_out = 10 * h->xmode + h->xlines;
     return MFWQ_OK;
 }
 

@@ -19,6 +19,8 @@
 // 1024 B between 8-row groups), K chunks of 128 bytes, two stages so that
 // the loads of chunk c+1 overlap the MMAs of chunk c.  Every wait on an
 // mbarrier is bounded; on timeout the kernel records an error and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -283,6 +285,213 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_fd_tc(TcArgs a) {
     }
 }
 
+// ---------------------------------------------------------------- TMA variant (TF32)
+// Operands arrive by cp.async.bulk.tensor (2D tiles of 32 FP32 x rows, 128-byte
+// swizzle) straight into the canonical SWIZZLE_128B K-major layout the MMA
+// reads (8-row x 128-byte atoms, SBO = 1024 B; the K step inside an atom moves
+// the descriptor start by 32 B).  One thread issues the copies and the MMAs;
+// "full" mbarriers count the copied bytes, "empty" ones are signalled by the
+// MMA commit that consumed a stage.  Row strides must be multiples of 16 bytes
+// (n_in % 4 == 0); coordinates start at multiples of 32 elements.
+constexpr int kTmaStages = 2;
+
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset: 8-row atoms
+    d |= (uint64_t)1 << 46;            // descriptor version
+    d |= (uint64_t)2 << 61;            // layout: 128-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(mbar)
+        : "memory");
+}
+
+struct TmaArgs {
+    float* Out;
+    int R, n_in, n_out, n_pad, tmem_cols;
+    const float* l1;
+    const float* l2;
+    const float* l3;
+    int n1;
+    int* err;
+    const int* skip;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_fd_tc_tma(const __grid_constant__ CUtensorMap mapA,
+                                                           const __grid_constant__ CUtensorMap mapB, TmaArgs a) {
+    if (a.skip && *a.skip) return;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned stages: [A 128 x 128 B][B n_pad x 128 B]
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int a_bytes = kTileM * kChunkBytes;
+    const int b_bytes = a.n_pad * kChunkBytes;
+    const int stage_bytes = a_bytes + b_bytes;  // multiple of 1024 (n_pad is a multiple of 16 -> 2048 B)
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kTmaStages * stage_bytes);
+    uint64_t* empty = full + kTmaStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(empty + kTmaStages);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(a.tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kTmaStages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t idesc = make_idesc(2u, kTileM, a.n_pad);
+    const int nchunks = (a.n_in + 31) / 32;
+    const int ntiles = (a.R + kTileM - 1) / kTileM;
+    const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int total = my_tiles * nchunks;  // chunks this CTA consumes, in order
+    bool ok = true;
+    // producer state (thread 0): next chunk to load
+    int loaded = 0;
+    auto issue = [&](int g) -> bool {  // load chunk g into stage g % S (thread 0)
+        const int s = g % kTmaStages, j = g / kTmaStages;
+        if (j >= 1 && !mbar_wait(smem_u32(&empty[s]), (uint32_t)((j - 1) & 1))) return false;
+        const int tile = blockIdx.x + (g / nchunks) * gridDim.x;
+        const int c = g % nchunks;
+        unsigned char* sa = smem + s * stage_bytes;
+        mbar_expect_tx(smem_u32(&full[s]), (uint32_t)stage_bytes);
+        tma_load_2d(smem_u32(sa), &mapA, c * 32, tile * kTileM, smem_u32(&full[s]));
+        tma_load_2d(smem_u32(sa + a_bytes), &mapB, c * 32, 0, smem_u32(&full[s]));
+        return true;
+    };
+    if (tid == 0)
+        for (; loaded < total && loaded < kTmaStages; ++loaded) ok = ok && issue(loaded);
+    int g = 0;
+    for (int ti = 0; ti < my_tiles; ++ti) {
+        const int tile = blockIdx.x + ti * gridDim.x;
+        const int row0 = tile * kTileM;
+        if (tid == 0 && ok) {
+            for (int c = 0; c < nchunks; ++c, ++g) {
+                const int s = g % kTmaStages, j = g / kTmaStages;
+                if (!mbar_wait(smem_u32(&full[s]), (uint32_t)(j & 1))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t abase = smem_u32(smem + s * stage_bytes);
+                const uint32_t bbase = abase + a_bytes;
+#pragma unroll
+                for (int kk = 0; kk < kChunkBytes / 32; ++kk)
+                    mma<0>(tmem, make_desc_sw128(abase + kk * 32), make_desc_sw128(bbase + kk * 32), idesc,
+                           (c > 0 || kk > 0) ? 1u : 0u);
+                mma_commit(smem_u32(&empty[s]));
+                if (loaded < total) {
+                    if (!issue(loaded)) {
+                        ok = false;
+                        break;
+                    }
+                    ++loaded;
+                }
+            }
+        }
+        // everyone: wait for the tile's last commit, then read TMEM
+        const int gl = (ti + 1) * nchunks - 1;
+        __syncthreads();
+        if (!mbar_wait(smem_u32(&empty[gl % kTmaStages]), (uint32_t)((gl / kTmaStages) & 1))) ok = false;
+        if (!__syncthreads_and(ok ? 1 : 0)) {
+            ok = false;
+            break;
+        }
+        tc_fence_after();
+        const int r = row0 + warp * 32 + lane;
+        const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+        float sum_ij = 0.f;
+        if (a.l3 && r < a.R) {
+            const int jj = r / a.n1, ii = r - jj * a.n1;
+            sum_ij = a.l1[ii] + a.l2[jj];
+        }
+        for (int c0 = 0; c0 < a.n_pad; c0 += 16) {
+            float v[16];
+            tmem_ld16(tbase + c0, v);
+            if (r < a.R) {
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int o = c0 + q;
+                    if (o < a.n_out) {
+                        float val = v[q];
+                        if (a.l3) val = val / (sum_ij + a.l3[o]);
+                        a.Out[(size_t)o * a.R + r] = val;
+                    }
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (!ok && tid == 0) atomicExch(a.err, 1);
+    // loads issued but never consumed (only after a failure) and the last commit must land before exit
+    if (tid == 0 && total > 0) {
+        const int gl = total - 1;
+        mbar_wait(smem_u32(&empty[gl % kTmaStages]), (uint32_t)((gl / kTmaStages) & 1));
+        for (int q = g; q < loaded; ++q) mbar_wait(smem_u32(&full[q % kTmaStages]), (uint32_t)((q / kTmaStages) & 1));
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(a.tmem_cols));
+    }
+}
+
+// The tensor-map encoder is a driver entry point; it is looked up through the
+// runtime so that the library does not link libcuda directly.
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+bool encode_map(CUtensorMap* m, const float* base, int cols, int rows, int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(float)};
+    cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                        CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int tma_smem_bytes(int n_pad) {
+    int b = kTmaStages * (kTileM * kChunkBytes + n_pad * kChunkBytes) + 1024 + 64;  // + alignment slack, barriers
+    if (n_pad > 128 && b < 80 * 1024) b = 80 * 1024;
+    return b;
+}
+
 int g_num_sms = 0;
 
 // Dynamic shared memory of one CTA.  With 256 TMEM columns per CTA at most two
@@ -316,6 +525,28 @@ int launch_pass(const float* A, const float* Bm, float* Out, int R, int n_in, in
     int grid = 2 * g_num_sms;
     if (grid > ntiles) grid = ntiles;
     if (grid < 1) grid = 1;
+    if (KIND == 0 && n_in % 4 == 0 && ((uintptr_t)A & 15) == 0 && ((uintptr_t)Bm & 15) == 0) {
+        CUtensorMap ma, mb;
+        if (encode_map(&ma, A, n_in, R, kTileM) && encode_map(&mb, Bm, n_in, n_out, a.n_pad)) {
+            TmaArgs t;
+            t.Out = Out;
+            t.R = R;
+            t.n_in = n_in;
+            t.n_out = n_out;
+            t.n_pad = a.n_pad;
+            t.tmem_cols = a.tmem_cols;
+            t.l1 = l1;
+            t.l2 = l2;
+            t.l3 = l3;
+            t.n1 = n1;
+            t.err = err;
+            t.skip = skip;
+            launch_begin(S_FD_TC, s);
+            k_fd_tc_tma<<<grid, kTcThreads, tma_smem_bytes(a.n_pad), s>>>(ma, mb, t);
+            launch_end(S_FD_TC, s);
+            return cudaGetLastError() == cudaSuccess ? MFWQ_OK : MFWQ_ECUDA;
+        }
+    }
     launch_begin(S_FD_TC, s);
     k_fd_tc<KIND><<<grid, kTcThreads, tc_smem_bytes(a.n_pad), s>>>(a);
     launch_end(S_FD_TC, s);
@@ -346,6 +577,8 @@ int configure_fd_tc(int max_n) {
     const int bytes = tc_smem_bytes(256);
     if (cudaFuncSetAttribute(k_fd_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return MFWQ_ECUDA;
     if (cudaFuncSetAttribute(k_fd_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) != cudaSuccess) return MFWQ_ECUDA;
+    if (cudaFuncSetAttribute(k_fd_tc_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, tma_smem_bytes(256)) != cudaSuccess)
+        return MFWQ_ECUDA;
     return MFWQ_OK;
 }
 

@@ -16,6 +16,7 @@ struct OpCtx {
     T* scratch;        // apply_scratch_elems() elements of T
     cudaStream_t stream;
     int xlines = 4;    // (q3, q2) lines per block of the forward x stage: 2, 4 or 8
+    int xmode = 0;     // forward x-stage work mapping: 0 per (line, item), 1 per item over all lines
 };
 
 // y = K~ x, y = K~^T x, g6 = dJ/dC (Algorithm 2 and its transpose).  A nonzero

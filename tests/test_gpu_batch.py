@@ -72,13 +72,32 @@ def test_batch_with_converged_patch_and_maxit(mf):
         op.close()
 
 
+@pytest.mark.parametrize("mode,lines", [(m, L) for m in (0, 1) for L in (2, 4, 8)])
+def test_every_xstage_variant_keeps_parity(mf, tmp_path, mode, lines):
+    """Each (mapping, lines) variant the autotuner may pick gives the oracle's apply."""
+    p, nel = 3, (7, 5, 9)
+    op = _patch(mf, p, nel, 4)
+    cache = str(tmp_path / "forced.jsonl")
+    key = "xstage p=%d n1=%d nq1=%d nq2=%d nq3=%d fp64" % (p, op.n[0], op.nq[0], op.nq[1], op.nq[2])
+    with open(cache, "w") as fh:
+        fh.write('{"key": "%s", "xstage": %d}\n' % (key, 10 * mode + lines))
+    assert op.autotune(cache) == 10 * mode + lines
+    tabs = [O.tables_1d(inputs.open_uniform_knots(p, nel[l]), p) for l in range(3)]
+    C6 = O.coefficient_grid(tabs, "ring", inputs.fourier_modes(4), 0.3)
+    x = inputs.uniform_vector(op.shape, 8)
+    ref = O.apply_alg2(tabs, O.full_coeff(C6), x)
+    y = op.apply(torch.from_numpy(x).to(DEV)).cpu().numpy()
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    op.close()
+
+
 def test_autotune_keeps_parity(mf, tmp_path):
     p, nel = 4, (9, 8, 10)
     op = _patch(mf, p, nel, 2)
     cache = str(tmp_path / "tune.jsonl")
     L = op.autotune(cache)
-    assert L in (2, 4, 8)
-    assert os.path.exists(cache) and '"xlines": %d' % L in open(cache).read()
+    assert L % 10 in (2, 4, 8) and L // 10 in (0, 1)
+    assert os.path.exists(cache) and '"xstage": %d' % L in open(cache).read()
     assert op.autotune(cache) == L  # cache hit
     tabs = [O.tables_1d(inputs.open_uniform_knots(p, nel[l]), p) for l in range(3)]
     C6 = O.coefficient_grid(tabs, "ring", inputs.fourier_modes(2), 0.3)
