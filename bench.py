@@ -240,13 +240,15 @@ def event_time(stream, fn, reps):
     return a.elapsed_time(b) / reps
 
 
-def make_op(mf, p, nel, mixed=False, fd="tf32", device=None, geometry="ring"):
+def make_op(mf, p, nel, mixed=False, fd="tf32", device=None, geometry="ring", tune=True):
     from paper_1712_08565_gb300 import inputs
     knots = [inputs.open_uniform_knots(p, nel)] * 3
     op = mf.Operator(p, knots, mixed=mixed, fd_precision=fd, device=device)
     C = op.eval_coeff(geometry)
     op.set_coeff(C)
     del C
+    if tune:  # x-stage tile shape, timed once per shape and cached
+        op.autotune(os.path.join(tempfile.gettempdir(), "mfwq_autotune.jsonl"))
     return op, knots
 
 
@@ -323,7 +325,7 @@ def batched(mf, device):
     lines = {}
     for i, (p, nel) in enumerate(specs):
         knots = [inputs.open_uniform_knots(p, nel[l]) for l in range(3)]
-        op = mf.Operator(p, knots, device=device)
+        op = mf.Operator(p, knots, mixed=True, fd_precision="tf32", device=device)
         op.set_coeff(op.eval_coeff("ring", inputs.fourier_modes(1000 + i), BATCH["kscale"]))
         L = op.autotune(tune)
         lines[L] = lines.get(L, 0) + 1
@@ -334,12 +336,20 @@ def batched(mf, device):
     N = sum(op.N for op in ops)
     b = mf.Batch(ops)
     us = [torch.empty_like(f) for f in fs]
-    b.solve(fs, us, rtol=BATCH["rtol"])  # warm-up
+    b.solve(fs, us, rtol=BATCH["rtol"], force_fp64=True)  # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    _, infos = b.solve(fs, us, rtol=BATCH["rtol"])
+    _, infos = b.solve(fs, us, rtol=BATCH["rtol"], force_fp64=True)
     torch.cuda.synchronize()
     tb = time.perf_counter() - t0
+    u64 = [u.clone() for u in us]
+    b.solve(fs, us, rtol=BATCH["rtol"])  # mixed, warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, minfos = b.solve(fs, us, rtol=BATCH["rtol"])
+    torch.cuda.synchronize()
+    tm = time.perf_counter() - t0
+    merr = max(float(torch.linalg.vector_norm(u - v) / torch.linalg.vector_norm(v)) for u, v in zip(us, u64))
     t0 = time.perf_counter()
     seq_iters = []
     for op, f, u in zip(ops, fs, us):
@@ -350,6 +360,9 @@ def batched(mf, device):
     applies = 2 * sum(i.iterations for i in infos)
     res = {"workload": BATCH["name"], "patches": len(ops), "N_total": N, "rtol": BATCH["rtol"],
            "setup_s": setup_s, "batched_s": tb, "sequential_s": ts, "speedup_vs_sequential": ts / tb,
+           "mixed_batched_s": tm, "mixed_all_converged": all(i.converged for i in minfos),
+           "mixed_max_rel_residual": max(i.rel_residual for i in minfos), "mixed_max_rel_err_vs_fp64": merr,
+           "mixed_speedup_vs_fp64_batched": tb / tm,
            "sweeps": max(i.outer_iterations for i in infos), "iterations_min_max": [min(i.iterations for i in infos), max(i.iterations for i in infos)],
            "all_converged": all(i.converged for i in infos),
            "apply_dof_per_s": sum(2 * i.iterations * op.N for i, op in zip(infos, ops)) / tb,

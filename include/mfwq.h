@@ -247,15 +247,19 @@ typedef struct mfwq_batch_s* mfwq_batch;
 int mfwq_batch_create(int count, const mfwq_handle* patches, mfwq_batch* out);
 void mfwq_batch_destroy(mfwq_batch b);
 
-/* Solves K~_i u_i = f_i for every patch with FP64 FD-preconditioned BiCGStab
- * (as mfwq_solve with force_fp64).  One BiCGStab iteration of all patches is
- * captured into a single CUDA graph (each patch on its own stream) and
- * launched once per sweep; every patch keeps its own device-resident scalars,
- * and the kernels of a converged patch return at once.  f_dev[i], u_dev[i]:
- * device vectors of patch i.  infos (count entries, may be NULL) receive each
- * patch's status, iterations and residual; outer_iterations holds the number
- * of sweeps.  Returns the first failing patch status (MFWQ_OK if all
- * converged).  Synchronous. */
+/* Solves K~_i u_i = f_i for every patch.  FP64 form (force_fp64, or any patch
+ * without mixed = 1): FD-preconditioned BiCGStab as mfwq_solve; one BiCGStab
+ * iteration of all patches is captured into a single CUDA graph (each patch
+ * on its own stream) and launched once per sweep; every patch keeps its own
+ * device-resident scalars, and the kernels of a converged patch return at
+ * once; outer_iterations holds the number of sweeps.  Mixed form (every patch
+ * mixed = 1): FP64 refinement steps in lockstep over the patches still above
+ * rtol, each inner FP32 solve of all of them one graph launch per sweep;
+ * iterations sums a patch's inner iterations, outer_iterations counts its
+ * refinement steps.  f_dev[i], u_dev[i]: device vectors of patch i.  infos
+ * (count entries, may be NULL) receive each patch's status, iterations and
+ * FP64 relative residual.  Returns the first failing patch status (MFWQ_OK if
+ * all converged).  Synchronous. */
 int mfwq_batch_solve(mfwq_batch b, const double* const* f_dev, double* const* u_dev, const mfwq_solve_opts* opts,
                      mfwq_solve_info* infos);
 

@@ -385,8 +385,12 @@ int solve_mixed(mfwq_handle h, const double* f, double* u, const mfwq_solve_opts
     int outer = 0, inner_total = 0, status = MFWQ_ENOCONV;
     double rel = 1.0;
     for (;;) {
-        ST(run_apply<double>(c64, u, w64, nullptr));
-        ST(axpby_into<double>(f, w64, r64, N, s));
+        if (outer == 0 && !o.use_initial_guess) {
+            CU(cudaMemcpyAsync(r64, f, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));  // u = 0: r = f
+        } else {
+            ST(run_apply<double>(c64, u, w64, nullptr));
+            ST(axpby_into<double>(f, w64, r64, N, s));
+        }
         ST(norm2_into(r64, N, h->part, h->dnorm, s));
         CU(cudaMemcpyAsync(h->hnorm, h->dnorm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CU(cudaStreamSynchronize(s));
@@ -802,6 +806,183 @@ extern "C" void mfwq_batch_destroy(mfwq_batch b) {
     free_batch(b);
 }
 
+namespace {
+// Captures one BiCGStab iteration of the listed patches (each on its own
+// stream, forked from and joined to the batch's origin stream) into a graph.
+template <typename T>
+int capture_sweep(mfwq_batch b, const std::vector<int>& list, const std::vector<LinOp<T>>& A, const std::vector<LinOp<T>>& P,
+                  const std::vector<const T*>& f, const std::vector<T*>& x, const std::vector<KrylovBufs<T>>& bufs,
+                  cudaGraphExec_t* exec) {
+    cudaGraph_t graph = nullptr;
+    *exec = nullptr;
+    CU(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+    int cst = MFWQ_OK;
+    if (cudaEventRecord(b->fork, b->origin) != cudaSuccess) cst = MFWQ_ECUDA;
+    for (int i : list) {
+        if (cst != MFWQ_OK) break;
+        mfwq_handle h = b->h[i];
+        if (cudaStreamWaitEvent(b->streams[i], b->fork, 0) != cudaSuccess) cst = MFWQ_ECUDA;
+        if (cst == MFWQ_OK)
+            cst = krylov_enqueue_iter<T>(A[i], P[i], f[i], x[i], bufs[i], &b->dsc[i], h->part, h->N, b->streams[i]);
+        if (cst == MFWQ_OK && cudaEventRecord(b->join[i], b->streams[i]) != cudaSuccess) cst = MFWQ_ECUDA;
+        if (cst == MFWQ_OK && cudaStreamWaitEvent(b->origin, b->join[i], 0) != cudaSuccess) cst = MFWQ_ECUDA;
+    }
+    cudaError_t ce = cudaStreamEndCapture(b->origin, &graph);
+    if (cst != MFWQ_OK || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(MFWQ_ECUDA, "capture of the batched iteration failed");
+    }
+    cudaError_t ie = cudaGraphInstantiate(exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        cudaGetLastError();
+        return fail(MFWQ_ECUDA, "cudaGraphInstantiate failed");
+    }
+    return MFWQ_OK;
+}
+
+// Runs sweeps of a captured iteration until every listed patch is done or
+// maxit sweeps ran; returns the number of sweeps.
+int run_sweeps(mfwq_batch b, const std::vector<int>& list, cudaGraphExec_t exec, int maxit, int* sweeps) {
+    const int count = (int)b->h.size();
+    *sweeps = 0;
+    for (int k = 0; k < maxit; ++k) {
+        CU(cudaGraphLaunch(exec, b->origin));
+        CU(cudaMemcpyAsync(b->hsc, b->dsc, sizeof(KScal) * count, cudaMemcpyDeviceToHost, b->origin));
+        CU(cudaStreamSynchronize(b->origin));
+        *sweeps = k + 1;
+        bool done = true;
+        for (int i : list)
+            if (!b->hsc[i].skip1) done = false;
+        if (done) break;
+    }
+    return MFWQ_OK;
+}
+
+// Mixed form: FP64 refinement steps in lockstep over the patches still above
+// rtol; each inner FP32 BiCGStab (FP32 operator, tensor-core FD) runs for all
+// of them together, one graph launch per sweep.
+int batch_solve_mixed(mfwq_batch b, const double* const* f_dev, double* const* u_dev, const mfwq_solve_opts& o,
+                      mfwq_solve_info* infos) {
+    const int count = (int)b->h.size();
+    for (int i = 0; i < count; ++i)
+        if (!b->h[i]->mixed) return fail(MFWQ_EINVAL, "every patch of a mixed batch solve needs mixed = 1");
+    const double inner_rtol = o.inner_rtol > 0 ? o.inner_rtol : 1e-4;
+    const int inner_maxit = o.inner_maxit > 0 ? o.inner_maxit : 200;
+    std::vector<LinOp<float>> A(count), P(count);
+    std::vector<const float*> r32(count);
+    std::vector<float*> d32(count);
+    std::vector<KrylovBufs<float>> bufs(count);
+    for (int i = 0; i < count; ++i) {
+        mfwq_handle h = b->h[i];
+        OpCtx<float> c = ctx32(h);
+        c.stream = b->streams[i];
+        DirD<float> d[3] = {h->d32[0], h->d32[1], h->d32[2]};
+        float* tmp = h->fd_tmp32;
+        int* err = h->derr;
+        const int prec = h->fd_prec;
+        cudaStream_t s = b->streams[i];
+        A[i] = [c](const float* in, float* out, const int* skip) { return run_apply<float>(c, in, out, skip); };
+        P[i] = [d, tmp, s, err, prec](const float* in, float* out, const int* skip) {
+            return run_fd_tc(d, prec, in, out, tmp, err, skip, s);
+        };
+        r32[i] = h->kv32 + 8 * h->N;
+        d32[i] = h->kv32 + 9 * h->N;
+        bufs[i] = bufs32(h);
+    }
+    std::vector<int> active(count), status(count, MFWQ_ENOCONV), outer(count, 0), inner(count, 0);
+    std::vector<double> rel(count, 1.0);
+    for (int i = 0; i < count; ++i) active[i] = i;
+    for (int k = 0;; ++k) {
+        // FP64 residuals (the first one is f when u starts at zero)
+        for (int i : active) {
+            mfwq_handle h = b->h[i];
+            cudaStream_t s = b->streams[i];
+            OpCtx<double> c = ctx64(h);
+            c.stream = s;
+            double* w64 = h->kv64;
+            double* r64 = h->kv64 + h->N;
+            if (k == 0 && !o.use_initial_guess) {
+                CU(cudaMemsetAsync(u_dev[i], 0, sizeof(double) * h->N, s));
+                CU(cudaMemcpyAsync(r64, f_dev[i], sizeof(double) * h->N, cudaMemcpyDeviceToDevice, s));
+            } else {
+                ST(run_apply<double>(c, u_dev[i], w64, nullptr));
+                ST(axpby_into<double>(f_dev[i], w64, r64, h->N, s));
+            }
+            ST(norm2_into(r64, h->N, h->part, h->dnorm, s));
+            if (k == 0) ST(norm2_into(f_dev[i], h->N, h->part, h->dnorm + 1, s));
+            CU(cudaMemcpyAsync(h->hnorm, h->dnorm, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        }
+        std::vector<int> next;
+        for (int i : active) {
+            mfwq_handle h = b->h[i];
+            CU(cudaStreamSynchronize(b->streams[i]));
+            const double r2 = h->hnorm[0], f2 = h->hnorm[1];
+            if (!std::isfinite(r2)) {
+                status[i] = MFWQ_ENAN;
+                continue;
+            }
+            rel[i] = f2 > 0 ? std::sqrt(r2 / f2) : 0.0;
+            if (f2 == 0.0 || rel[i] <= o.rtol) {
+                status[i] = MFWQ_OK;
+                continue;
+            }
+            if (outer[i] >= o.maxit) continue;
+            next.push_back(i);
+        }
+        active = next;
+        if (active.empty()) break;
+        // inner solves of the active patches
+        CU(cudaEventRecord(b->fork, b->origin));
+        for (int i : active) {
+            mfwq_handle h = b->h[i];
+            cudaStream_t s = b->streams[i];
+            CU(cudaStreamWaitEvent(s, b->fork, 0));
+            ST(to_f32_scaled(h->kv64 + h->N, h->dnorm, const_cast<float*>(r32[i]), h->N, s));
+            ST(krylov_enqueue_init<float>(A[i], r32[i], d32[i], false, inner_rtol, bufs[i], &b->dsc[i], h->part, h->N, s));
+            CU(cudaEventRecord(b->join[i], s));
+            CU(cudaStreamWaitEvent(b->origin, b->join[i], 0));
+        }
+        CU(cudaMemcpyAsync(b->hsc, b->dsc, sizeof(KScal) * count, cudaMemcpyDeviceToHost, b->origin));
+        CU(cudaStreamSynchronize(b->origin));
+        cudaGraphExec_t exec = nullptr;
+        ST(capture_sweep<float>(b, active, A, P, r32, d32, bufs, &exec));
+        int sweeps = 0;
+        int st = run_sweeps(b, active, exec, inner_maxit, &sweeps);
+        cudaGraphExecDestroy(exec);
+        if (st != MFWQ_OK) return st;
+        for (int i : active) {
+            mfwq_handle h = b->h[i];
+            inner[i] += b->hsc[i].iters;
+            if (b->hsc[i].status == MFWQ_ENAN) {
+                status[i] = MFWQ_ENAN;
+                continue;
+            }
+            ST(add_f32_scaled(u_dev[i], d32[i], h->dnorm, h->N, b->streams[i]));
+            ++outer[i];
+        }
+        std::vector<int> keep;
+        for (int i : active)
+            if (status[i] != MFWQ_ENAN) keep.push_back(i);
+        active = keep;
+        if (active.empty()) break;
+    }
+    int worst = MFWQ_OK;
+    for (int i = 0; i < count; ++i) {
+        CU(cudaStreamSynchronize(b->streams[i]));
+        if (infos) {
+            infos[i].status = status[i];
+            infos[i].iterations = inner[i];
+            infos[i].outer_iterations = outer[i];
+            infos[i].rel_residual = rel[i];
+        }
+        if (status[i] != MFWQ_OK && worst == MFWQ_OK) worst = status[i];
+    }
+    return worst;
+}
+}  // namespace
+
 extern "C" int mfwq_batch_solve(mfwq_batch b, const double* const* f_dev, double* const* u_dev, const mfwq_solve_opts* opts,
                                 mfwq_solve_info* infos) {
     if (!b || !f_dev || !u_dev) return fail(MFWQ_EINVAL, "bad argument");
@@ -811,6 +992,11 @@ extern "C" int mfwq_batch_solve(mfwq_batch b, const double* const* f_dev, double
     if (!(o.rtol > 0) || o.maxit < 0) return fail(MFWQ_EINVAL, "rtol must be > 0 and maxit >= 0");
     for (int i = 0; i < count; ++i)
         if (!f_dev[i] || !u_dev[i] || f_dev[i] == u_dev[i]) return fail(MFWQ_EINVAL, "bad patch vectors");
+    if (!o.force_fp64) {
+        bool all_mixed = true;
+        for (int i = 0; i < count; ++i) all_mixed = all_mixed && b->h[i]->mixed;
+        if (all_mixed) return batch_solve_mixed(b, f_dev, u_dev, o, infos);
+    }
     std::vector<PatchOps> ops;
     for (int i = 0; i < count; ++i) ops.push_back(patch_ops(b->h[i], b->streams[i]));
     // initial residuals, every patch on its own stream

@@ -460,7 +460,10 @@ class Batch:
         except Exception:
             pass
 
-    def solve(self, fs, us=None, rtol=1e-8, maxit=500, check=False):
+    def solve(self, fs, us=None, rtol=1e-8, maxit=500, force_fp64=False, inner_rtol=0.0, inner_maxit=0, x0=False,
+              check=False):
+        """Solve every patch; FP64 (force_fp64 or any non-mixed patch) or the
+        mixed refinement (all patches mixed).  With x0, us holds the initial guesses."""
         import torch
         n = len(self.ops)
         us = us if us is not None else [torch.empty_like(f) for f in fs]
@@ -469,6 +472,10 @@ class Batch:
         o = SolveOpts()
         o.rtol = rtol
         o.maxit = maxit
+        o.force_fp64 = 1 if force_fp64 else 0
+        o.inner_rtol = inner_rtol
+        o.inner_maxit = inner_maxit
+        o.use_initial_guess = 1 if x0 else 0
         infos = (SolveInfoC * n)()
         st = lib().mfwq_batch_solve(self._h, fp, up, ctypes.byref(o), infos)
         if st not in (MFWQ_OK, -6, -5, -8) or (check and st != MFWQ_OK):

@@ -23,9 +23,9 @@ def mf():
     return mfwq
 
 
-def _patch(mf, p, nel, seed):
+def _patch(mf, p, nel, seed, mixed=False):
     knots = [inputs.open_uniform_knots(p, nel[l]) for l in range(3)]
-    op = mf.Operator(p, knots, device=DEV)
+    op = mf.Operator(p, knots, mixed=mixed, device=DEV)
     modes = inputs.fourier_modes(seed)
     op.set_coeff(op.eval_coeff("ring", modes, 0.3))
     return op
@@ -55,6 +55,29 @@ def test_batch_equals_separate_solves(mf):
         fn = f.cpu().numpy().ravel()
         res = np.linalg.norm(fn - K @ u.cpu().numpy().ravel()) / np.linalg.norm(fn)
         assert res <= 2e-8
+        op.close()
+
+
+def test_batch_mixed_equals_separate_mixed_solves(mf):
+    """Mixed form of the batch: FP64 refinement steps in lockstep, inner FP32
+    solves of all active patches one graph launch per sweep; each patch ends
+    where its own mixed solve ends, at an FP64 residual below 1e-8."""
+    specs = [(3, (6, 9, 7)), (5, (5, 4, 8)), (2, (12, 6, 5)), (4, (4, 7, 6))]
+    ops = [_patch(mf, p, nel, 10 + i, mixed=True) for i, (p, nel) in enumerate(specs)]
+    fs = [op.load_vector("ring", "sines") for op in ops]
+    ref = [op.solve(f, rtol=1e-8, inner_rtol=1e-4) for op, f in zip(ops, fs)]
+    b = mf.Batch(ops)
+    us, infos = b.solve(fs, rtol=1e-8, inner_rtol=1e-4)
+    for (u0, i0), u, i in zip(ref, us, infos):
+        assert i.converged and i0.converged and i.rel_residual <= 1e-8
+        assert i.outer_iterations == i0.outer_iterations and i.iterations == i0.iterations
+        assert torch.equal(u, u0)
+    u64, i64 = b.solve(fs, rtol=1e-8, force_fp64=True)
+    for u, u2, i in zip(us, u64, i64):
+        assert i.converged
+        assert float(torch.linalg.vector_norm(u - u2) / torch.linalg.vector_norm(u2)) <= 1e-6
+    b.close()
+    for op in ops:
         op.close()
 
 
