@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the p sweep, mixed solve and CPU baseline")
+    ap.add_argument("--kernel-nel", default=None, help="with --kernel-run: elements per direction, e.g. 192,64,64")
     ap.add_argument("--kernel-run", choices=["apply", "apply_T", "fd64", "fdtc", "fdbf16", "apply32"], default=None,
                     help="set up the workload, run one operator 3 times and exit (target for ncu captures)")
     return ap.parse_args()
@@ -241,8 +242,10 @@ def event_time(stream, fn, reps):
 
 
 def make_op(mf, p, nel, mixed=False, fd="tf32", device=None, geometry="ring", tune=True):
+    """nel: elements per direction (int) or per direction 1, 2, 3 (3 ints)."""
     from paper_1712_08565_gb300 import inputs
-    knots = [inputs.open_uniform_knots(p, nel)] * 3
+    nels = [nel] * 3 if isinstance(nel, int) else list(nel)
+    knots = [inputs.open_uniform_knots(p, nels[l]) for l in range(3)]
     op = mf.Operator(p, knots, mixed=mixed, fd_precision=fd, device=device)
     C = op.eval_coeff(geometry)
     op.set_coeff(C)
@@ -507,9 +510,11 @@ def run_ours(args):
     return 0
 
 
-def kernel_run(which):
+def kernel_run(which, nel_override=None):
     """Setup + three launches of one operator on the bench workload (the
-    p = 6, 192-element ring for the mixed-precision operators)."""
+    p = 6, 192-element ring for the mixed-precision operators), or on the
+    same degree with the elements per direction given (a smaller case with
+    the same direction-1 size, for profiler captures)."""
     import torch
     from paper_1712_08565_gb300 import build
     build.build()
@@ -518,6 +523,8 @@ def kernel_run(which):
     dev = torch.device("cuda", 0)
     mixed = which in ("fdtc", "fdbf16", "apply32")
     p, nel = (MIXED["p"], MIXED["nel"]) if mixed else (WORKLOAD["p"], WORKLOAD["nel"])
+    if nel_override:
+        nel = tuple(int(v) for v in nel_override.split(","))
     op, _ = make_op(mf, p, nel, mixed=mixed, fd="bf16" if which == "fdbf16" else "tf32", device=dev)
     x = torch.from_numpy(inputs.uniform_vector(op.shape, 1)).to(dev)
     if mixed:
@@ -537,7 +544,7 @@ def kernel_run(which):
 def main():
     args = parse()
     if args.kernel_run:
-        return kernel_run(args.kernel_run)
+        return kernel_run(args.kernel_run, args.kernel_nel)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -229,14 +229,20 @@ int mfwq_fd_precond_noalloc(const int n[3], const double* const U_dev[3], const 
  * independence is the uncoupled case of the multi-patch setting the paper
  * names as future work in its conclusions. */
 
-/* Times the forward x stage of mfwq_apply (and of mfwq_apply_f32 on a mixed
- * handle) with 2, 4 and 8 (q3,q2) lines per block and both work mappings
- * (0: one thread per line and item, 1: one thread per item over all lines of
- * the block) on this handle's sizes, and keeps the fastest; *xlines_out (may
- * be NULL) receives the FP64 choice as 10 * mapping + lines.  cache_path (may
- * be NULL) is a file of JSON lines {"key": "...", "xstage": 10 * mapping +
- * lines}: a hit skips the timing, a miss appends the result.  Uses the
- * handle's Krylov work vectors, so call it between solves.  Synchronous. */
+/* Times mfwq_apply (and mfwq_apply_f32 on a mixed handle) on this handle's
+ * sizes and keeps the fastest launch shapes: first the forward x stage with 2,
+ * 4 and 8 (q3,q2) lines per block and four work mappings (0: one thread per
+ * line and item, 1: one thread per item over all lines of the block, 2 and 3:
+ * the same with the block's inputs prefetched into shared memory by bulk
+ * copies, where the slabs allow it; 4 and 5: 8 lines per block, a thread owns
+ * a two-row tile and 4 or 8 lines; each with the default or a reduced
+ * shared-memory carveout), then 1, 2 or 4 output rows per thread in the other
+ * four stages.  *xlines_out (may be NULL) receives the FP64 choice as
+ * 1000 * carveout + 100 * rows + 10 * mapping + lines.  cache_path (may be
+ * NULL) is a file of JSON lines {"key": "...", "xstage": that code}: a hit
+ * skips the timing, a miss appends the result (codes below 100 mean one row
+ * per thread).  Uses
+ * the handle's Krylov work vectors, so call it between solves.  Synchronous. */
 int mfwq_autotune(mfwq_handle h, const char* cache_path, int* xlines_out);
 
 typedef struct mfwq_batch_s* mfwq_batch;

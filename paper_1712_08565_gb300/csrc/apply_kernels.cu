@@ -20,6 +20,7 @@
 
 #include "kernels.h"
 #include "prof.h"
+#include "ptx_async.cuh"
 
 namespace mfwq {
 
@@ -38,253 +39,290 @@ struct Ptr9 {
 // ---------------------------------------------------------------- slow-dimension band contraction
 // out[a][r][c] = sum_t band(r, t) in[a][start(r) + t][c] for the middle (A > 1)
 // or the slowest (A = 1) dimension; the Op decides inputs, outputs, families.
+// A thread owns one column (a, c) and R consecutive output rows r0..r0+R-1:
+// it walks the union of their bands once, so each input row it loads serves
+// every one of the R rows whose band holds it (about R times fewer loads than
+// one row per thread).  The block's R band rows are staged in shared memory
+// interleaved by family ([R][width][NF]), one broadcast load per (row, t).
 struct SlowGeom {
     int A, Rin, Rout, C;
 };
 
-template <class Op>
+template <class Op, int R>
 __global__ void __launch_bounds__(kThreads) k_slow(Op op, SlowGeom g, const int* skip) {
+    using T = typename Op::Elem;
+    constexpr int NF = Op::NF, NIN = Op::NIN, NACC = Op::NACC;
     if (skip && *skip) return;
-    const int r = blockIdx.y;
-    const int s = op.band.start[r];
-    const int L = op.band.len[r];
+    extern __shared__ __align__(16) unsigned char slow_smem[];
+    T* sb = reinterpret_cast<T*>(slow_smem);
+    const int r0 = blockIdx.y * R;
+    const int nr = min(R, g.Rout - r0);
+    const int W = op.band.width;
+    int s[R], len[R];
+    int lo = 0x7fffffff, hi = 0;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        s[k] = 0;
+        len[k] = 0;
+        if (k < nr) {
+            s[k] = op.band.start[r0 + k];
+            len[k] = op.band.len[r0 + k];
+            if (len[k] > 0) {
+                lo = min(lo, s[k]);
+                hi = max(hi, s[k] + len[k]);
+            }
+        }
+    }
+    for (int e = threadIdx.x; e < nr * W * NF; e += blockDim.x) {
+        const int k = e / (W * NF), rem = e - k * W * NF, t = rem / NF, f = rem - t * NF;
+        sb[e] = op.band.row(f, r0 + k)[t];
+    }
+    __syncthreads();
     const size_t AC = (size_t)g.A * g.C;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < AC; e += (size_t)gridDim.x * blockDim.x) {
         const size_t a = e / g.C, c = e - a * g.C;
-        const size_t i0 = (a * g.Rin + s) * g.C + c;
-        const size_t o = (a * g.Rout + r) * g.C + c;
-        op.run(r, L, i0, (size_t)g.C, o);
+        T acc[R][NACC];
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int m = 0; m < NACC; ++m) acc[k][m] = 0;
+        const size_t ib = a * g.Rin * (size_t)g.C + c;
+        for (int q = lo; q < hi; ++q) {
+            T x[NIN];
+            op.load(ib + (size_t)q * g.C, x);
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const int t = q - s[k];
+                if ((unsigned)t < (unsigned)len[k]) op.fma(sb + (k * W + t) * NF, x, acc[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+            if (k < nr) op.store((a * g.Rout + r0 + k) * (size_t)g.C + c, acc[k]);
     }
 }
 
+// The ops: NIN inputs loaded per row, NACC accumulators per output row, NF
+// band families (w points at the NF values of one (row, t) in family order).
 template <typename T>
 struct OpTrialZ {  // Z0 = B0 v, Z1 = B1 v
+    using Elem = T;
+    static constexpr int NIN = 1, NACC = 2, NF = 2;
     BandD<T> band;
     const T* __restrict__ v;
     T* __restrict__ z0;
     T* __restrict__ z1;
-    __device__ void run(int r, int L, size_t i0, size_t st, size_t o) const {
-        const T* b0 = band.row(0, r);
-        const T* b1 = band.row(1, r);
-        T a0 = 0, a1 = 0;
-        for (int t = 0; t < L; ++t) {
-            T x = v[i0 + t * st];
-            a0 = fmaT(b0[t], x, a0);
-            a1 = fmaT(b1[t], x, a1);
-        }
-        z0[o] = a0;
-        z1[o] = a1;
+    __device__ void load(size_t i, T* x) const { x[0] = v[i]; }
+    __device__ void fma(const T* w, const T* x, T* u) const {
+        u[0] = fmaT(w[0], x[0], u[0]);
+        u[1] = fmaT(w[1], x[0], u[1]);
+    }
+    __device__ void store(size_t o, const T* u) const {
+        z0[o] = u[0];
+        z1[o] = u[1];
     }
 };
 
 template <typename T>
 struct OpTrialY {  // Y00 = B0 Z0, Y10 = B1 Z0, Y01 = B0 Z1
+    using Elem = T;
+    static constexpr int NIN = 2, NACC = 3, NF = 2;
     BandD<T> band;
     const T* __restrict__ z0;
     const T* __restrict__ z1;
     T* __restrict__ y00;
     T* __restrict__ y10;
     T* __restrict__ y01;
-    __device__ void run(int r, int L, size_t i0, size_t st, size_t o) const {
-        const T* b0 = band.row(0, r);
-        const T* b1 = band.row(1, r);
-        T a = 0, b = 0, c = 0;
-        for (int t = 0; t < L; ++t) {
-            T x0 = z0[i0 + t * st], x1 = z1[i0 + t * st];
-            a = fmaT(b0[t], x0, a);
-            b = fmaT(b1[t], x0, b);
-            c = fmaT(b0[t], x1, c);
-        }
-        y00[o] = a;
-        y10[o] = b;
-        y01[o] = c;
+    __device__ void load(size_t i, T* x) const {
+        x[0] = z0[i];
+        x[1] = z1[i];
+    }
+    __device__ void fma(const T* w, const T* x, T* u) const {
+        u[0] = fmaT(w[0], x[0], u[0]);
+        u[1] = fmaT(w[1], x[0], u[1]);
+        u[2] = fmaT(w[0], x[1], u[2]);
+    }
+    __device__ void store(size_t o, const T* u) const {
+        y00[o] = u[0];
+        y10[o] = u[1];
+        y01[o] = u[2];
     }
 };
 
 template <typename T>
 struct OpTestY {  // 9 x-contracted tensors -> 4 z-groups through W2
+    using Elem = T;
+    static constexpr int NIN = 9, NACC = 4, NF = 4;
     BandD<T> band;
     const T* __restrict__ in[9];
     T* __restrict__ out[4];
-    __device__ void run(int r, int L, size_t i0, size_t st, size_t o) const {
-        const T* w00 = band.row(0, r);
-        const T* w01 = band.row(1, r);
-        const T* w10 = band.row(2, r);
-        const T* w11 = band.row(3, r);
-        T u0 = 0, u1 = 0, u2 = 0, u3 = 0;
-        for (int t = 0; t < L; ++t) {
-            const size_t i = i0 + t * st;
-            const T f00 = w00[t], f01 = w01[t], f10 = w10[t], f11 = w11[t];
-            // z-family (0,0): pairs 11, 12, 21, 22 with y-families (0,0), (0,1), (1,0), (1,1)
-            u0 = fmaT(f00, in[0][i], u0);
-            u0 = fmaT(f01, in[1][i], u0);
-            u0 = fmaT(f10, in[3][i], u0);
-            u0 = fmaT(f11, in[4][i], u0);
-            // z-family (0,1): pairs 13 (y 00), 23 (y 10)
-            u1 = fmaT(f00, in[2][i], u1);
-            u1 = fmaT(f10, in[5][i], u1);
-            // z-family (1,0): pairs 31 (y 00), 32 (y 01)
-            u2 = fmaT(f00, in[6][i], u2);
-            u2 = fmaT(f01, in[7][i], u2);
-            // z-family (1,1): pair 33 (y 00)
-            u3 = fmaT(f00, in[8][i], u3);
-        }
-        out[0][o] = u0;
-        out[1][o] = u1;
-        out[2][o] = u2;
-        out[3][o] = u3;
+    __device__ void load(size_t i, T* x) const {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) x[k] = in[k][i];
+    }
+    __device__ void fma(const T* w, const T* x, T* u) const {
+        const T f00 = w[0], f01 = w[1], f10 = w[2], f11 = w[3];
+        // z-family (0,0): pairs 11, 12, 21, 22 with y-families (0,0), (0,1), (1,0), (1,1)
+        u[0] = fmaT(f00, x[0], u[0]);
+        u[0] = fmaT(f01, x[1], u[0]);
+        u[0] = fmaT(f10, x[3], u[0]);
+        u[0] = fmaT(f11, x[4], u[0]);
+        // z-family (0,1): pairs 13 (y 00), 23 (y 10)
+        u[1] = fmaT(f00, x[2], u[1]);
+        u[1] = fmaT(f10, x[5], u[1]);
+        // z-family (1,0): pairs 31 (y 00), 32 (y 01)
+        u[2] = fmaT(f00, x[6], u[2]);
+        u[2] = fmaT(f01, x[7], u[2]);
+        // z-family (1,1): pair 33 (y 00)
+        u[3] = fmaT(f00, x[8], u[3]);
+    }
+    __device__ void store(size_t o, const T* u) const {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) out[f][o] = u[f];
     }
 };
 
 template <typename T>
 struct OpTestZ {  // w = sum_f W3^f U_f
+    using Elem = T;
+    static constexpr int NIN = 4, NACC = 1, NF = 4;
     BandD<T> band;
     const T* __restrict__ in[4];
     T* __restrict__ out;
-    __device__ void run(int r, int L, size_t i0, size_t st, size_t o) const {
-        const T* w0 = band.row(0, r);
-        const T* w1 = band.row(1, r);
-        const T* w2 = band.row(2, r);
-        const T* w3 = band.row(3, r);
-        T acc = 0;
-        for (int t = 0; t < L; ++t) {
-            const size_t i = i0 + t * st;
-            acc = fmaT(w0[t], in[0][i], acc);
-            acc = fmaT(w1[t], in[1][i], acc);
-            acc = fmaT(w2[t], in[2][i], acc);
-            acc = fmaT(w3[t], in[3][i], acc);
-        }
-        out[o] = acc;
+    __device__ void load(size_t i, T* x) const {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = in[k][i];
     }
+    __device__ void fma(const T* w, const T* x, T* u) const {
+        u[0] = fmaT(w[0], x[0], u[0]);
+        u[0] = fmaT(w[1], x[1], u[0]);
+        u[0] = fmaT(w[2], x[2], u[0]);
+        u[0] = fmaT(w[3], x[3], u[0]);
+    }
+    __device__ void store(size_t o, const T* u) const { out[o] = u[0]; }
 };
 
 // ---- transposed stages
 template <typename T>
 struct OpTestZT {  // V_f = W3^f^T y  (band rows q3 -> i3)
+    using Elem = T;
+    static constexpr int NIN = 1, NACC = 4, NF = 4;
     BandD<T> band;
     const T* __restrict__ in;
     T* __restrict__ out[4];
-    __device__ void run(int r, int L, size_t i0, size_t st, size_t o) const {
-        const T* w0 = band.row(0, r);
-        const T* w1 = band.row(1, r);
-        const T* w2 = band.row(2, r);
-        const T* w3 = band.row(3, r);
-        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        for (int t = 0; t < L; ++t) {
-            T x = in[i0 + t * st];
-            a0 = fmaT(w0[t], x, a0);
-            a1 = fmaT(w1[t], x, a1);
-            a2 = fmaT(w2[t], x, a2);
-            a3 = fmaT(w3[t], x, a3);
-        }
-        out[0][o] = a0;
-        out[1][o] = a1;
-        out[2][o] = a2;
-        out[3][o] = a3;
+    __device__ void load(size_t i, T* x) const { x[0] = in[i]; }
+    __device__ void fma(const T* w, const T* x, T* u) const {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) u[f] = fmaT(w[f], x[0], u[f]);
+    }
+    __device__ void store(size_t o, const T* u) const {
+#pragma unroll
+        for (int f = 0; f < 4; ++f) out[f][o] = u[f];
     }
 };
 
 template <typename T>
 struct OpTestYT {  // R^(ab) = W2^(y-fam)^T V_(z-fam), 9 outputs
+    using Elem = T;
+    static constexpr int NIN = 4, NACC = 9, NF = 4;
     BandD<T> band;
     const T* __restrict__ in[4];
     T* __restrict__ out[9];
-    __device__ void run(int r, int L, size_t i0, size_t st, size_t o) const {
-        const T* w00 = band.row(0, r);
-        const T* w01 = band.row(1, r);
-        const T* w10 = band.row(2, r);
-        const T* w11 = band.row(3, r);
-        T r11 = 0, r12 = 0, r13 = 0, r21 = 0, r22 = 0, r23 = 0, r31 = 0, r32 = 0, r33 = 0;
-        for (int t = 0; t < L; ++t) {
-            const size_t i = i0 + t * st;
-            const T v0 = in[0][i], v1 = in[1][i], v2 = in[2][i], v3 = in[3][i];
-            const T f00 = w00[t], f01 = w01[t], f10 = w10[t], f11 = w11[t];
-            r11 = fmaT(f00, v0, r11);
-            r12 = fmaT(f01, v0, r12);
-            r21 = fmaT(f10, v0, r21);
-            r22 = fmaT(f11, v0, r22);
-            r13 = fmaT(f00, v1, r13);
-            r23 = fmaT(f10, v1, r23);
-            r31 = fmaT(f00, v2, r31);
-            r32 = fmaT(f01, v2, r32);
-            r33 = fmaT(f00, v3, r33);
-        }
-        out[0][o] = r11;
-        out[1][o] = r12;
-        out[2][o] = r13;
-        out[3][o] = r21;
-        out[4][o] = r22;
-        out[5][o] = r23;
-        out[6][o] = r31;
-        out[7][o] = r32;
-        out[8][o] = r33;
+    __device__ void load(size_t i, T* x) const {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) x[k] = in[k][i];
+    }
+    __device__ void fma(const T* w, const T* x, T* u) const {
+        const T f00 = w[0], f01 = w[1], f10 = w[2], f11 = w[3];
+        // outputs in pair order 11, 12, 13, 21, 22, 23, 31, 32, 33
+        u[0] = fmaT(f00, x[0], u[0]);
+        u[1] = fmaT(f01, x[0], u[1]);
+        u[3] = fmaT(f10, x[0], u[3]);
+        u[4] = fmaT(f11, x[0], u[4]);
+        u[2] = fmaT(f00, x[1], u[2]);
+        u[5] = fmaT(f10, x[1], u[5]);
+        u[6] = fmaT(f00, x[2], u[6]);
+        u[7] = fmaT(f01, x[2], u[7]);
+        u[8] = fmaT(f00, x[3], u[8]);
+    }
+    __device__ void store(size_t o, const T* u) const {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) out[k][o] = u[k];
     }
 };
 
 template <typename T>
 struct OpTrialYT {  // Zt0 = B0^T X1 + B1^T X2, Zt1 = B0^T X3 (band rows j2 -> q2)
+    using Elem = T;
+    static constexpr int NIN = 3, NACC = 2, NF = 2;
     BandD<T> band;
     const T* __restrict__ x1;
     const T* __restrict__ x2;
     const T* __restrict__ x3;
     T* __restrict__ z0;
     T* __restrict__ z1;
-    __device__ void run(int r, int L, size_t i0, size_t st, size_t o) const {
-        const T* b0 = band.row(0, r);
-        const T* b1 = band.row(1, r);
-        T a = 0, b = 0;
-        for (int t = 0; t < L; ++t) {
-            const size_t i = i0 + t * st;
-            a = fmaT(b0[t], x1[i], a);
-            a = fmaT(b1[t], x2[i], a);
-            b = fmaT(b0[t], x3[i], b);
-        }
-        z0[o] = a;
-        z1[o] = b;
+    __device__ void load(size_t i, T* x) const {
+        x[0] = x1[i];
+        x[1] = x2[i];
+        x[2] = x3[i];
+    }
+    __device__ void fma(const T* w, const T* x, T* u) const {
+        u[0] = fmaT(w[0], x[0], u[0]);
+        u[0] = fmaT(w[1], x[1], u[0]);
+        u[1] = fmaT(w[0], x[2], u[1]);
+    }
+    __device__ void store(size_t o, const T* u) const {
+        z0[o] = u[0];
+        z1[o] = u[1];
     }
 };
 
 template <typename T>
 struct OpTrialZT {  // out = B0^T Zt0 + B1^T Zt1 (band rows j3 -> q3)
+    using Elem = T;
+    static constexpr int NIN = 2, NACC = 1, NF = 2;
     BandD<T> band;
     const T* __restrict__ z0;
     const T* __restrict__ z1;
     T* __restrict__ out;
-    __device__ void run(int r, int L, size_t i0, size_t st, size_t o) const {
-        const T* b0 = band.row(0, r);
-        const T* b1 = band.row(1, r);
-        T a = 0;
-        for (int t = 0; t < L; ++t) {
-            const size_t i = i0 + t * st;
-            a = fmaT(b0[t], z0[i], a);
-            a = fmaT(b1[t], z1[i], a);
-        }
-        out[o] = a;
+    __device__ void load(size_t i, T* x) const {
+        x[0] = z0[i];
+        x[1] = z1[i];
     }
+    __device__ void fma(const T* w, const T* x, T* u) const {
+        u[0] = fmaT(w[0], x[0], u[0]);
+        u[0] = fmaT(w[1], x[1], u[0]);
+    }
+    __device__ void store(size_t o, const T* u) const { out[o] = u[0]; }
 };
 
 template <typename T>
 struct OpSingle {  // out = band(fam 0) applied to one input (load-vector stages)
+    using Elem = T;
+    static constexpr int NIN = 1, NACC = 1, NF = 1;
     BandD<T> band;
     const T* __restrict__ in;
     T* __restrict__ out;
-    __device__ void run(int r, int L, size_t i0, size_t st, size_t o) const {
-        const T* b = band.row(0, r);
-        T a = 0;
-        for (int t = 0; t < L; ++t) a = fmaT(b[t], in[i0 + t * st], a);
-        out[o] = a;
-    }
+    __device__ void load(size_t i, T* x) const { x[0] = in[i]; }
+    __device__ void fma(const T* w, const T* x, T* u) const { u[0] = fmaT(w[0], x[0], u[0]); }
+    __device__ void store(size_t o, const T* u) const { out[o] = u[0]; }
 };
 
+// rows: output rows per thread (1, 2 or 4)
 template <class Op>
-cudaError_t launch_slow(int tag, const Op& op, int A, int Rin, int Rout, int C, const int* skip, cudaStream_t s) {
+cudaError_t launch_slow(int tag, const Op& op, int A, int Rin, int Rout, int C, const int* skip, cudaStream_t s,
+                        int rows = 1) {
     SlowGeom g{A, Rin, Rout, C};
+    const int R = rows == 2 || rows == 4 ? rows : 1;
     size_t AC = (size_t)A * C;
     unsigned bx = (unsigned)((AC + kThreads - 1) / kThreads);
     if (bx > 65535u) bx = 65535u;
-    dim3 grid(bx, Rout);
+    dim3 grid(bx, (Rout + R - 1) / R);
+    const size_t sm = sizeof(typename Op::Elem) * (size_t)R * op.band.width * Op::NF;
     launch_begin(tag, s);
-    k_slow<<<grid, kThreads, 0, s>>>(op, g, skip);
+    if (R == 4) k_slow<Op, 4><<<grid, kThreads, sm, s>>>(op, g, skip);
+    else if (R == 2) k_slow<Op, 2><<<grid, kThreads, sm, s>>>(op, g, skip);
+    else k_slow<Op, 1><<<grid, kThreads, sm, s>>>(op, g, skip);
     launch_end(tag, s);
     return cudaGetLastError();
 }
@@ -296,9 +334,12 @@ struct XArgs {
     BandD<T> BT;   // rows j1 -> q1
     BandD<T> W;    // rows i1 -> q1
     BandD<T> WT;   // rows q1 -> i1
+    TileD<T> BX;   // B in two-point tiles (tiled mapping)
+    TileD<T> WX;   // W in two-output tiles (tiled mapping)
     int n1, nq1, nlines;
-    size_t Nq;     // points per coefficient field
-    const T* C;    // [6][Nq]
+    size_t cs;     // element stride between the coefficient fields of C
+    size_t gs;     // element stride between the fields of the gradient output
+    const T* C;    // [6][cs], the first Nq of each field used
 };
 
 constexpr int kLines = 4;
@@ -313,18 +354,40 @@ constexpr int kLines = 4;
 //  MODE 1: a thread owns one point or one (alpha, i) output for all LINES
 //          lines, so each band coefficient it loads serves LINES multiply-adds
 //          (fewest loads; best when the FP32 pipe leaves the loads exposed).
-template <typename T, int LINES, int MODE>
-__global__ void __launch_bounds__(kThreads) k_xstage_apply(XArgs<T> a, const T* __restrict__ y0, const T* __restrict__ y1,
-                                                           const T* __restrict__ y2, T* __restrict__ tout, size_t tstride,
-                                                           const int* skip) {
-    if (skip && *skip) return;
-    extern __shared__ unsigned char smem_raw[];
-    T* sY = reinterpret_cast<T*>(smem_raw);  // [3][LINES][n1]
-    T* sH = sY + 3 * LINES * a.n1;           // [3][LINES][nq1]
-    const int line0 = blockIdx.x * LINES;
-    const int nl = min(LINES, a.nlines - line0);
+//  MODE 2, 3: the mappings of MODE 0, 1 with the block's inputs (its three
+//          Y slabs and six coefficient slabs, all contiguous) prefetched into
+//          shared memory by bulk copies (cp.async.bulk) that complete on one
+//          mbarrier, so every HBM read of the block is in flight at once and
+//          the coefficient products read shared memory.  Needs LINES *
+//          sizeof(T) to be a multiple of 16 and 16-byte aligned slabs.
+template <typename T, int LINES>
+__device__ bool xstage_prefetch(const XArgs<T>& a, const T* __restrict__ y0, const T* __restrict__ y1,
+                                const T* __restrict__ y2, int line0, int nl, T* sY, T* sC, uint64_t* mbar, int* err) {
     const int n1 = a.n1, nq1 = a.nq1;
-    const int hs = LINES * nq1;
+    if (nl == LINES) {
+        const uint32_t mb = ptx::smem_u32(mbar);
+        if (threadIdx.x == 0) {
+            ptx::mbar_init(mb, 1);
+            ptx::fence_mbar_init();
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const uint32_t yb = (uint32_t)(LINES * n1 * sizeof(T)), cb = (uint32_t)(LINES * nq1 * sizeof(T));
+            ptx::mbar_expect_tx(mb, 3 * yb + 6 * cb);
+            const size_t yo = (size_t)line0 * n1, co = (size_t)line0 * nq1;
+            ptx::bulk_g2s(ptx::smem_u32(sY), y0 + yo, yb, mb);
+            ptx::bulk_g2s(ptx::smem_u32(sY + LINES * n1), y1 + yo, yb, mb);
+            ptx::bulk_g2s(ptx::smem_u32(sY + 2 * LINES * n1), y2 + yo, yb, mb);
+            for (int s = 0; s < 6; ++s) ptx::bulk_g2s(ptx::smem_u32(sC + s * LINES * nq1), a.C + s * a.cs + co, cb, mb);
+        }
+        const bool ok = ptx::mbar_wait(mb, 0);
+        if (__syncthreads_and(ok ? 1 : 0)) return true;
+        // timed out: record it, give the copies in flight one more bounded wait, give up on the block
+        if (threadIdx.x == 0 && err) atomicExch(err, 1);
+        ptx::mbar_wait(mb, 0);
+        return false;
+    }
+    // last, partial block: the slabs are shorter than a multiple of 16 bytes, plain loads
     for (int e = threadIdx.x; e < nl * n1; e += blockDim.x) {
         const int l = e / n1, j = e - l * n1;
         const size_t gi = (size_t)(line0 + l) * n1 + j;
@@ -332,25 +395,69 @@ __global__ void __launch_bounds__(kThreads) k_xstage_apply(XArgs<T> a, const T* 
         sY[(1 * LINES + l) * n1 + j] = y1[gi];
         sY[(2 * LINES + l) * n1 + j] = y2[gi];
     }
+    for (int e = threadIdx.x; e < nl * nq1; e += blockDim.x) {
+        const int l = e / nq1, q = e - l * nq1;
+        const size_t gi = (size_t)(line0 + l) * nq1 + q;
+#pragma unroll
+        for (int s = 0; s < 6; ++s) sC[(s * LINES + l) * nq1 + q] = a.C[s * a.cs + gi];
+    }
+    return true;
+}
+
+// CARVE (0 or 1) only makes a separate function: CARVE = 1 copies are given a
+// smaller preferred shared-memory carveout, so fewer blocks share an SM and
+// the band tables they all read stay in a larger L1.
+template <typename T, int LINES, int MODE, int CARVE>
+__global__ void __launch_bounds__(kThreads) k_xstage_apply(XArgs<T> a, const T* __restrict__ y0, const T* __restrict__ y1,
+                                                           const T* __restrict__ y2, T* __restrict__ tout, size_t tstride,
+                                                           const int* skip, int* err) {
+    constexpr bool PF = MODE >= 2;
+    constexpr int MAP = MODE & 1;
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // [mbarrier, 16 B if PF][Y: 3][LINES][n1][H: 3][LINES][nq1][C (PF): 6][LINES][nq1]
+    T* sY = reinterpret_cast<T*>(smem_raw + (PF ? 16 : 0));
+    T* sH = sY + 3 * LINES * a.n1;
+    T* sC = sH + 3 * LINES * a.nq1;
+    const int line0 = blockIdx.x * LINES;
+    const int nl = min(LINES, a.nlines - line0);
+    const int n1 = a.n1, nq1 = a.nq1;
+    const int hs = LINES * nq1;
+    if (PF) {
+        if (!xstage_prefetch<T, LINES>(a, y0, y1, y2, line0, nl, sY, sC, reinterpret_cast<uint64_t*>(smem_raw), err))
+            return;
+    } else {
+        for (int e = threadIdx.x; e < nl * n1; e += blockDim.x) {
+            const int l = e / n1, j = e - l * n1;
+            const size_t gi = (size_t)(line0 + l) * n1 + j;
+            sY[(0 * LINES + l) * n1 + j] = y0[gi];
+            sY[(1 * LINES + l) * n1 + j] = y1[gi];
+            sY[(2 * LINES + l) * n1 + j] = y2[gi];
+        }
+    }
+    // coefficient field s at (line l, point q): shared-memory slab or HBM
+    auto cval = [&](int s, int l, int q) -> T {
+        if (PF) return sC[(s * LINES + l) * nq1 + q];
+        return a.C[(size_t)s * a.cs + (size_t)(line0 + l) * nq1 + q];
+    };
     for (int b = 0; b < 3; ++b) {
         __syncthreads();
         const int bfam = b == 0 ? 1 : 0;
         // symmetric-storage slots of C_(alpha,beta), alpha = 1..3: alpha if alpha = beta, else 2 + alpha + beta
-        const size_t c0 = (size_t)(b == 0 ? 0 : 2 + b) * a.Nq;
-        const size_t c1 = (size_t)(b == 1 ? 1 : 3 + b) * a.Nq;
-        const size_t c2 = (size_t)(b == 2 ? 2 : 4 + b) * a.Nq;
-        if (MODE == 0) {
+        const int c0 = b == 0 ? 0 : 2 + b;
+        const int c1 = b == 1 ? 1 : 3 + b;
+        const int c2 = b == 2 ? 2 : 4 + b;
+        if (MAP == 0) {
             for (int e = threadIdx.x; e < nl * nq1; e += blockDim.x) {
                 const int l = e / nq1, q = e - l * nq1;
                 const int s = a.B.start[q], L = a.B.len[q];
                 const T* Y = sY + (b * LINES + l) * n1 + s;
                 T g = 0;
                 for (int t = 0; t < L; ++t) g = fmaT(a.B.lane(bfam, q, t), Y[t], g);
-                const size_t pt = (size_t)(line0 + l) * nq1 + q;
                 T* H = sH + l * nq1 + q;
-                H[0 * hs] = a.C[c0 + pt] * g;
-                H[1 * hs] = a.C[c1 + pt] * g;
-                H[2 * hs] = a.C[c2 + pt] * g;
+                H[0 * hs] = cval(c0, l, q) * g;
+                H[1 * hs] = cval(c1, l, q) * g;
+                H[2 * hs] = cval(c2, l, q) * g;
             }
         } else {
             for (int q = threadIdx.x; q < nq1; q += blockDim.x) {
@@ -367,17 +474,16 @@ __global__ void __launch_bounds__(kThreads) k_xstage_apply(XArgs<T> a, const T* 
 #pragma unroll
                 for (int l = 0; l < LINES; ++l) {
                     if (l >= nl) break;
-                    const size_t pt = (size_t)(line0 + l) * nq1 + q;
                     T* H = sH + l * nq1 + q;
-                    H[0 * hs] = a.C[c0 + pt] * g[l];
-                    H[1 * hs] = a.C[c1 + pt] * g[l];
-                    H[2 * hs] = a.C[c2 + pt] * g[l];
+                    H[0 * hs] = cval(c0, l, q) * g[l];
+                    H[1 * hs] = cval(c1, l, q) * g[l];
+                    H[2 * hs] = cval(c2, l, q) * g[l];
                 }
             }
         }
         __syncthreads();
         // outputs; x-family (a1, b1) = ([alpha = 1], [beta = 1])
-        if (MODE == 0) {
+        if (MAP == 0) {
             const int per = nl * n1;
             for (int e = threadIdx.x; e < 3 * per; e += blockDim.x) {
                 const int al = e / per, rem = e - al * per;
@@ -414,12 +520,208 @@ __global__ void __launch_bounds__(kThreads) k_xstage_apply(XArgs<T> a, const T* 
     }
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, int CARVE>
 void launch_xstage(int L, dim3 grid, size_t sm, cudaStream_t st, const XArgs<T>& a, const T* y0, const T* y1, const T* y2,
-                   T* tout, size_t tstride, const int* skip) {
-    if (L == 2) k_xstage_apply<T, 2, MODE><<<grid, kThreads, sm, st>>>(a, y0, y1, y2, tout, tstride, skip);
-    else if (L == 8) k_xstage_apply<T, 8, MODE><<<grid, kThreads, sm, st>>>(a, y0, y1, y2, tout, tstride, skip);
-    else k_xstage_apply<T, 4, MODE><<<grid, kThreads, sm, st>>>(a, y0, y1, y2, tout, tstride, skip);
+                   T* tout, size_t tstride, const int* skip, int* err) {
+    if (L == 2) k_xstage_apply<T, 2, MODE, CARVE><<<grid, kThreads, sm, st>>>(a, y0, y1, y2, tout, tstride, skip, err);
+    else if (L == 8) k_xstage_apply<T, 8, MODE, CARVE><<<grid, kThreads, sm, st>>>(a, y0, y1, y2, tout, tstride, skip, err);
+    else k_xstage_apply<T, 4, MODE, CARVE><<<grid, kThreads, sm, st>>>(a, y0, y1, y2, tout, tstride, skip, err);
+}
+
+// ---- tiled forward x stage (modes 4 and 5)
+// A block owns kTileLines = 8 lines; shared memory holds them lines-innermost
+// ([row][8 lines], 16 bytes of padding after every 128 bytes so that lanes a
+// few rows apart hit different banks).  A thread owns a tile of two rows of
+// B or W (two points, or two outputs) and LG = 4 (mode 4) or 8 (mode 5) lines
+// and walks the tile's union window once: per window offset one paired load
+// of the two rows' band values and LG-wide vector loads of the lines, 2 * LG
+// multiply-adds (4 * LG for the alpha = 2, 3 pair of outputs, which share the
+// W family).  Register tiles over rows and lines cut the shared-memory and L1
+// traffic per multiply-add several times below one thread per (line, item).
+constexpr int kTileLines = 8;
+
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+
+// element offset of row r in a lines-innermost slab
+template <typename T>
+__host__ __device__ __forceinline__ int trow(int r) {
+    constexpr int PR = 128 / (kTileLines * (int)sizeof(T));  // rows per 128 bytes: 4 (FP32), 2 (FP64)
+    return r * kTileLines + (r / PR) * (16 / (int)sizeof(T));
+}
+
+// LG consecutive line values of a lines-innermost row, 16-byte vector loads
+template <typename T, int LG>
+__device__ __forceinline__ void load_lines(const T* p, T* v) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < LG / 4; ++k) {
+            const float4 x = reinterpret_cast<const float4*>(p)[k];
+            v[4 * k] = x.x;
+            v[4 * k + 1] = x.y;
+            v[4 * k + 2] = x.z;
+            v[4 * k + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < LG / 2; ++k) {
+            const double2 x = reinterpret_cast<const double2*>(p)[k];
+            v[2 * k] = x.x;
+            v[2 * k + 1] = x.y;
+        }
+    }
+}
+
+template <typename T, int LG>
+__device__ __forceinline__ void store_lines(T* p, const T* v) {
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int k = 0; k < LG / 4; ++k)
+            reinterpret_cast<float4*>(p)[k] = make_float4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < LG / 2; ++k) reinterpret_cast<double2*>(p)[k] = make_double2(v[2 * k], v[2 * k + 1]);
+    }
+}
+
+template <typename T, int LG, int CARVE>
+__global__ void __launch_bounds__(kThreads) k_xstage_tiled(XArgs<T> a, const T* __restrict__ y0, const T* __restrict__ y1,
+                                                           const T* __restrict__ y2, T* __restrict__ tout, size_t tstride,
+                                                           const int* skip) {
+    using T2 = typename Vec2<T>::type;
+    constexpr int NG = kTileLines / LG;  // line groups per block
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n1 = a.n1, nq1 = a.nq1;
+    const int ysz = trow<T>(n1 + 4), hsz = trow<T>(nq1 + 4);  // slab sizes (whole 128-byte groups)
+    T* sY = reinterpret_cast<T*>(smem_raw);  // [3 beta][ysz]: Y rows j
+    T* sH = sY + 3 * ysz;                    // [3 alpha][hsz]: H rows q
+    const int line0 = blockIdx.x * kTileLines;
+    const int nl = min(kTileLines, a.nlines - line0);
+    for (int e = threadIdx.x; e < 3 * kTileLines * n1; e += blockDim.x) {
+        const int b = e / (kTileLines * n1), rem = e - b * kTileLines * n1;
+        const int l = rem / n1, j = rem - l * n1;
+        const T* yb = b == 0 ? y0 : (b == 1 ? y1 : y2);
+        sY[b * ysz + trow<T>(j) + l] = l < nl ? yb[(size_t)(line0 + l) * n1 + j] : T(0);
+    }
+    const int ntb = a.BX.ntile, ntw = a.WX.ntile;
+    for (int b = 0; b < 3; ++b) {
+        __syncthreads();
+        const int bfam = b == 0 ? 1 : 0;
+        const int cs[3] = {b == 0 ? 0 : 2 + b, b == 1 ? 1 : 3 + b, b == 2 ? 2 : 4 + b};
+        // trial: G_b at points 2k, 2k+1 for LG lines, then H^(alpha b) = C_(alpha b) G_b
+        for (int it = threadIdx.x; it < ntb * NG; it += blockDim.x) {
+            const int g = it / ntb, k = it - g * ntb;
+            const int j0 = a.BX.start[k], wl = a.BX.len[k];
+            T acc0[LG], acc1[LG];
+#pragma unroll
+            for (int l = 0; l < LG; ++l) acc0[l] = acc1[l] = 0;
+            const T* ys = sY + b * ysz + g * LG;
+            for (int u = 0; u < wl; ++u) {
+                const T2 bb = *reinterpret_cast<const T2*>(a.BX.pair(bfam, u, k));
+                T y[LG];
+                load_lines<T, LG>(ys + trow<T>(j0 + u), y);
+#pragma unroll
+                for (int l = 0; l < LG; ++l) {
+                    acc0[l] = fmaT(bb.x, y[l], acc0[l]);
+                    acc1[l] = fmaT(bb.y, y[l], acc1[l]);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int q = 2 * k + r;
+                if (q >= nq1) break;
+#pragma unroll
+                for (int al = 0; al < 3; ++al) {
+                    T h[LG];
+#pragma unroll
+                    for (int l = 0; l < LG; ++l) {
+                        const int line = g * LG + l;
+                        const T c = line < nl ? a.C[(size_t)cs[al] * a.cs + (size_t)(line0 + line) * nq1 + q] : T(0);
+                        h[l] = c * (r == 0 ? acc0[l] : acc1[l]);
+                    }
+                    store_lines<T, LG>(sH + al * hsz + trow<T>(q) + g * LG, h);
+                }
+            }
+        }
+        __syncthreads();
+        // test: the alpha = 2, 3 outputs (W family bfam, shared) and the alpha = 1 outputs (family 2 + bfam)
+        const int np = ntw * NG;
+        for (int it = threadIdx.x; it < 2 * np; it += blockDim.x) {
+            const bool two = it < np;
+            const int jt = two ? it : it - np;
+            const int g = jt / ntw, k = jt - g * ntw;
+            const int q0 = a.WX.start[k], wl = a.WX.len[k];
+            const int fam = two ? bfam : 2 + bfam;
+            const int i0 = 2 * k;
+            if (two) {
+                T a20[LG], a21[LG], a30[LG], a31[LG];
+#pragma unroll
+                for (int l = 0; l < LG; ++l) a20[l] = a21[l] = a30[l] = a31[l] = 0;
+                const T* h2 = sH + 1 * hsz + g * LG;
+                const T* h3 = sH + 2 * hsz + g * LG;
+                for (int u = 0; u < wl; ++u) {
+                    const T2 w = *reinterpret_cast<const T2*>(a.WX.pair(fam, u, k));
+                    T x2[LG], x3[LG];
+                    load_lines<T, LG>(h2 + trow<T>(q0 + u), x2);
+                    load_lines<T, LG>(h3 + trow<T>(q0 + u), x3);
+#pragma unroll
+                    for (int l = 0; l < LG; ++l) {
+                        a20[l] = fmaT(w.x, x2[l], a20[l]);
+                        a21[l] = fmaT(w.y, x2[l], a21[l]);
+                        a30[l] = fmaT(w.x, x3[l], a30[l]);
+                        a31[l] = fmaT(w.y, x3[l], a31[l]);
+                    }
+                }
+                T* o2 = tout + (size_t)(3 + b) * tstride;
+                T* o3 = tout + (size_t)(6 + b) * tstride;
+#pragma unroll
+                for (int l = 0; l < LG; ++l) {
+                    const int line = g * LG + l;
+                    if (line >= nl) break;
+                    const size_t ob = (size_t)(line0 + line) * n1 + i0;
+                    o2[ob] = a20[l];
+                    o3[ob] = a30[l];
+                    if (i0 + 1 < n1) {
+                        o2[ob + 1] = a21[l];
+                        o3[ob + 1] = a31[l];
+                    }
+                }
+            } else {
+                T a10[LG], a11[LG];
+#pragma unroll
+                for (int l = 0; l < LG; ++l) a10[l] = a11[l] = 0;
+                const T* h1 = sH + g * LG;
+                for (int u = 0; u < wl; ++u) {
+                    const T2 w = *reinterpret_cast<const T2*>(a.WX.pair(fam, u, k));
+                    T x1[LG];
+                    load_lines<T, LG>(h1 + trow<T>(q0 + u), x1);
+#pragma unroll
+                    for (int l = 0; l < LG; ++l) {
+                        a10[l] = fmaT(w.x, x1[l], a10[l]);
+                        a11[l] = fmaT(w.y, x1[l], a11[l]);
+                    }
+                }
+                T* o1 = tout + (size_t)b * tstride;
+#pragma unroll
+                for (int l = 0; l < LG; ++l) {
+                    const int line = g * LG + l;
+                    if (line >= nl) break;
+                    const size_t ob = (size_t)(line0 + line) * n1 + i0;
+                    o1[ob] = a10[l];
+                    if (i0 + 1 < n1) o1[ob + 1] = a11[l];
+                }
+            }
+        }
+    }
 }
 
 // Transposed x stage: R (9 inputs [line][n1]) -> S^(ab) = W1^T R at q1 ->
@@ -463,8 +765,8 @@ __global__ void __launch_bounds__(kThreads) k_xstage_applyT(XArgs<T> a, Ptr9<T> 
             S[8] = fmaT(f00, R[8 * fs + t], S[8]);
         }
         const size_t pt = (size_t)(line0 + l) * nq1 + q;
-        const T c11 = a.C[pt], c22 = a.C[a.Nq + pt], c33 = a.C[2 * a.Nq + pt];
-        const T c12 = a.C[3 * a.Nq + pt], c13 = a.C[4 * a.Nq + pt], c23 = a.C[5 * a.Nq + pt];
+        const T c11 = a.C[pt], c22 = a.C[a.cs + pt], c33 = a.C[2 * a.cs + pt];
+        const T c12 = a.C[3 * a.cs + pt], c13 = a.C[4 * a.cs + pt], c23 = a.C[5 * a.cs + pt];
         const int es = kLines * nq1;
         T* E = sE + l * nq1 + q;
         E[0 * es] = c11 * S[0] + c12 * S[3] + c13 * S[6];  // beta = 1: C_11 S11 + C_21 S21 + C_31 S31
@@ -547,25 +849,28 @@ __global__ void __launch_bounds__(kThreads) k_xstage_grad(XArgs<T> a, const T* _
         }
         const size_t pt = (size_t)(line0 + l) * nq1 + q;
         g6[pt] = -S[0] * g1;
-        g6[a.Nq + pt] = -S[4] * g2;
-        g6[2 * a.Nq + pt] = -S[8] * g3;
-        g6[3 * a.Nq + pt] = -(S[1] * g2 + S[3] * g1);
-        g6[4 * a.Nq + pt] = -(S[2] * g3 + S[6] * g1);
-        g6[5 * a.Nq + pt] = -(S[5] * g3 + S[7] * g2);
+        g6[a.gs + pt] = -S[4] * g2;
+        g6[2 * a.gs + pt] = -S[8] * g3;
+        g6[3 * a.gs + pt] = -(S[1] * g2 + S[3] * g1);
+        g6[4 * a.gs + pt] = -(S[2] * g3 + S[6] * g1);
+        g6[5 * a.gs + pt] = -(S[5] * g3 + S[7] * g2);
     }
 }
 
 template <typename T>
-XArgs<T> xargs(const DirD<T>& d1, int nlines, size_t Nq, const T* C) {
+XArgs<T> xargs(const DirD<T>& d1, int nlines, size_t cs, const T* C) {
     XArgs<T> a;
     a.B = d1.B;
     a.BT = d1.BT;
     a.W = d1.W;
     a.WT = d1.WT;
+    a.BX = d1.BX;
+    a.WX = d1.WX;
     a.n1 = d1.n;
     a.nq1 = d1.nq;
     a.nlines = nlines;
-    a.Nq = Nq;
+    a.cs = cs;
+    a.gs = 0;
     a.C = C;
     return a;
 }
@@ -689,13 +994,39 @@ __global__ void __launch_bounds__(kThreads) k_rhs_x(int geom, int forcing, BandD
 }  // namespace
 
 // ================================================================= host launchers
+// Element strides of the workspace tensors [nq3][nq2][n1] (SP) and
+// [nq3][n2][n1] (SQ), rounded up to 32 elements so that every tensor starts
+// on a 128-byte boundary (bulk copies need 16).
+static void scratch_strides(const int n[3], const int nq[3], size_t* SP, size_t* SQ) {
+    *SP = ((size_t)nq[2] * nq[1] * n[0] + 31) / 32 * 32;
+    *SQ = ((size_t)nq[2] * n[1] * n[0] + 31) / 32 * 32;
+}
+
+template <typename T>
+static void scratch_strides(const OpCtx<T>& c, size_t* SP, size_t* SQ) {
+    const int n[3] = {c.d[0].n, c.d[1].n, c.d[2].n}, nq[3] = {c.d[0].nq, c.d[1].nq, c.d[2].nq};
+    scratch_strides(n, nq, SP, SQ);
+}
+
+template <typename T, int CARVE>
+void launch_xstage_mode(int mode, int L, dim3 grid, size_t sm, cudaStream_t st, const XArgs<T>& a, const T* y0,
+                        const T* y1, const T* y2, T* tout, size_t tstride, const int* skip, int* err) {
+    if (mode == 4) k_xstage_tiled<T, 4, CARVE><<<grid, kThreads, sm, st>>>(a, y0, y1, y2, tout, tstride, skip);
+    else if (mode == 5) k_xstage_tiled<T, 8, CARVE><<<grid, kThreads, sm, st>>>(a, y0, y1, y2, tout, tstride, skip);
+    else if (mode == 1) launch_xstage<T, 1, CARVE>(L, grid, sm, st, a, y0, y1, y2, tout, tstride, skip, err);
+    else if (mode == 2) launch_xstage<T, 2, CARVE>(L, grid, sm, st, a, y0, y1, y2, tout, tstride, skip, err);
+    else if (mode == 3) launch_xstage<T, 3, CARVE>(L, grid, sm, st, a, y0, y1, y2, tout, tstride, skip, err);
+    else launch_xstage<T, 0, CARVE>(L, grid, sm, st, a, y0, y1, y2, tout, tstride, skip, err);
+}
+
 template <typename T>
 int run_apply(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
     const DirD<T>& d1 = c.d[0];
     const DirD<T>& d2 = c.d[1];
     const DirD<T>& d3 = c.d[2];
     const int n1 = d1.n, n2 = d2.n, n3 = d3.n, q1 = d1.nq, q2 = d2.nq, q3 = d3.nq;
-    const size_t SP = (size_t)q3 * q2 * n1, SQ = (size_t)q3 * n2 * n1;
+    size_t SP, SQ;
+    scratch_strides(c, &SP, &SQ);
     T* P = c.scratch;           // 12 x SP
     T* Q = c.scratch + 12 * SP; // 4 x SQ
     T* Z0 = Q;
@@ -706,19 +1037,25 @@ int run_apply(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
     cudaError_t e;
     // trial z
     OpTrialZ<T> oz{d3.B, x, Z0, Z1};
-    if ((e = launch_slow(S_TRIAL_Z, oz, 1, n3, q3, n2 * n1, skip, c.stream)) != cudaSuccess) return MFWQ_ECUDA;
+    if ((e = launch_slow(S_TRIAL_Z, oz, 1, n3, q3, n2 * n1, skip, c.stream, c.srows)) != cudaSuccess) return MFWQ_ECUDA;
     // trial y
     OpTrialY<T> oy{d2.B, Z0, Z1, Y[0], Y[1], Y[2]};
-    if ((e = launch_slow(S_TRIAL_Y, oy, q3, n2, q2, n1, skip, c.stream)) != cudaSuccess) return MFWQ_ECUDA;
-    // x stage (lines per block chosen by the autotuner: 2, 4 or 8)
+    if ((e = launch_slow(S_TRIAL_Y, oy, q3, n2, q2, n1, skip, c.stream, c.srows)) != cudaSuccess) return MFWQ_ECUDA;
+    // x stage (lines per block and work mapping chosen by the autotuner)
     {
-        XArgs<T> a = xargs(d1, q3 * q2, c.Nq, c.C);
-        const int L = c.xlines == 2 || c.xlines == 8 ? c.xlines : 4;
-        size_t sm = sizeof(T) * ((size_t)3 * L * n1 + (size_t)3 * L * q1);
+        XArgs<T> a = xargs(d1, q3 * q2, c.cs, c.C);
+        int L = c.xlines == 2 || c.xlines == 8 ? c.xlines : 4;
+        int mode = c.xmode >= 0 && c.xmode <= 5 ? c.xmode : 0;
+        if (mode >= 4) L = kTileLines;
+        if (!xstage_mode_valid((int)sizeof(T), n1, q1, L, mode) || (mode >= 2 && mode <= 3 && c.cs % 4 != 0)) {
+            mode = 0;
+            L = 4;
+        }
+        const size_t sm = (size_t)xstage_smem_bytes((int)sizeof(T), n1, q1, L, mode);
         dim3 grid((q3 * q2 + L - 1) / L);
         launch_begin(S_XSTAGE, c.stream);
-        if (c.xmode == 1) launch_xstage<T, 1>(L, grid, sm, c.stream, a, Y[0], Y[1], Y[2], Tt[0], SP, skip);
-        else launch_xstage<T, 0>(L, grid, sm, c.stream, a, Y[0], Y[1], Y[2], Tt[0], SP, skip);
+        if (c.xcarve) launch_xstage_mode<T, 1>(mode, L, grid, sm, c.stream, a, Y[0], Y[1], Y[2], Tt[0], SP, skip, c.err);
+        else launch_xstage_mode<T, 0>(mode, L, grid, sm, c.stream, a, Y[0], Y[1], Y[2], Tt[0], SP, skip, c.err);
         launch_end(S_XSTAGE, c.stream);
         if (cudaGetLastError() != cudaSuccess) return MFWQ_ECUDA;
     }
@@ -727,13 +1064,13 @@ int run_apply(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
     oty.band = d2.W;
     for (int k = 0; k < 9; ++k) oty.in[k] = Tt[k];
     for (int f = 0; f < 4; ++f) oty.out[f] = Q + f * SQ;
-    if ((e = launch_slow(S_TEST_Y, oty, q3, q2, n2, n1, skip, c.stream)) != cudaSuccess) return MFWQ_ECUDA;
+    if ((e = launch_slow(S_TEST_Y, oty, q3, q2, n2, n1, skip, c.stream, c.srows)) != cudaSuccess) return MFWQ_ECUDA;
     // test z
     OpTestZ<T> otz;
     otz.band = d3.W;
     for (int f = 0; f < 4; ++f) otz.in[f] = Q + f * SQ;
     otz.out = y;
-    if ((e = launch_slow(S_TEST_Z, otz, 1, q3, n3, n2 * n1, skip, c.stream)) != cudaSuccess) return MFWQ_ECUDA;
+    if ((e = launch_slow(S_TEST_Z, otz, 1, q3, n3, n2 * n1, skip, c.stream, c.srows)) != cudaSuccess) return MFWQ_ECUDA;
     return MFWQ_OK;
 }
 
@@ -743,19 +1080,20 @@ static int run_test_T_partials(const OpCtx<T>& c, const T* x, const int* skip) {
     const DirD<T>& d2 = c.d[1];
     const DirD<T>& d3 = c.d[2];
     const int n1 = c.d[0].n, n2 = d2.n, n3 = d3.n, q2 = d2.nq, q3 = d3.nq;
-    const size_t SP = (size_t)q3 * q2 * n1, SQ = (size_t)q3 * n2 * n1;
+    size_t SP, SQ;
+    scratch_strides(c, &SP, &SQ);
     T* P = c.scratch;
     T* Q = c.scratch + 12 * SP;
     OpTestZT<T> o1;
     o1.band = d3.WT;
     o1.in = x;
     for (int f = 0; f < 4; ++f) o1.out[f] = Q + f * SQ;
-    if (launch_slow(S_TEST_ZT, o1, 1, n3, q3, n2 * n1, skip, c.stream) != cudaSuccess) return MFWQ_ECUDA;
+    if (launch_slow(S_TEST_ZT, o1, 1, n3, q3, n2 * n1, skip, c.stream, c.srows) != cudaSuccess) return MFWQ_ECUDA;
     OpTestYT<T> o2;
     o2.band = d2.WT;
     for (int f = 0; f < 4; ++f) o2.in[f] = Q + f * SQ;
     for (int k = 0; k < 9; ++k) o2.out[k] = P + (3 + k) * SP;
-    if (launch_slow(S_TEST_YT, o2, q3, n2, q2, n1, skip, c.stream) != cudaSuccess) return MFWQ_ECUDA;
+    if (launch_slow(S_TEST_YT, o2, q3, n2, q2, n1, skip, c.stream, c.srows) != cudaSuccess) return MFWQ_ECUDA;
     return MFWQ_OK;
 }
 
@@ -765,14 +1103,15 @@ int run_apply_T(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
     const DirD<T>& d2 = c.d[1];
     const DirD<T>& d3 = c.d[2];
     const int n1 = d1.n, n2 = d2.n, n3 = d3.n, q1 = d1.nq, q2 = d2.nq, q3 = d3.nq;
-    const size_t SP = (size_t)q3 * q2 * n1, SQ = (size_t)q3 * n2 * n1;
+    size_t SP, SQ;
+    scratch_strides(c, &SP, &SQ);
     T* P = c.scratch;
     T* Q = c.scratch + 12 * SP;
     int st = run_test_T_partials(c, x, skip);
     if (st != MFWQ_OK) return st;
     // x stage: R (P[3..12)) -> X1, X2, X3 (P[0..3))
     {
-        XArgs<T> a = xargs(d1, q3 * q2, c.Nq, c.C);
+        XArgs<T> a = xargs(d1, q3 * q2, c.cs, c.C);
         size_t sm = sizeof(T) * ((size_t)9 * kLines * n1 + (size_t)3 * kLines * q1);
         dim3 grid((q3 * q2 + kLines - 1) / kLines);
         Ptr9<T> rp;
@@ -783,9 +1122,9 @@ int run_apply_T(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
         if (cudaGetLastError() != cudaSuccess) return MFWQ_ECUDA;
     }
     OpTrialYT<T> o3{d2.BT, P, P + SP, P + 2 * SP, Q, Q + SQ};
-    if (launch_slow(S_TRIAL_YT, o3, q3, q2, n2, n1, skip, c.stream) != cudaSuccess) return MFWQ_ECUDA;
+    if (launch_slow(S_TRIAL_YT, o3, q3, q2, n2, n1, skip, c.stream, c.srows) != cudaSuccess) return MFWQ_ECUDA;
     OpTrialZT<T> o4{d3.BT, Q, Q + SQ, y};
-    if (launch_slow(S_TRIAL_ZT, o4, 1, q3, n3, n2 * n1, skip, c.stream) != cudaSuccess) return MFWQ_ECUDA;
+    if (launch_slow(S_TRIAL_ZT, o4, 1, q3, n3, n2 * n1, skip, c.stream, c.srows) != cudaSuccess) return MFWQ_ECUDA;
     return MFWQ_OK;
 }
 
@@ -795,18 +1134,20 @@ int run_grad(const OpCtx<T>& c, const T* lam, const T* u, T* g6) {
     const DirD<T>& d2 = c.d[1];
     const DirD<T>& d3 = c.d[2];
     const int n1 = d1.n, n2 = d2.n, n3 = d3.n, q2 = d2.nq, q3 = d3.nq;
-    const size_t SP = (size_t)q3 * q2 * n1, SQ = (size_t)q3 * n2 * n1;
+    size_t SP, SQ;
+    scratch_strides(c, &SP, &SQ);
     T* P = c.scratch;
     T* Q = c.scratch + 12 * SP;
     // trial partials of u: Z (Q[0..2)) -> Y (P[0..3))
     OpTrialZ<T> oz{d3.B, u, Q, Q + SQ};
-    if (launch_slow(S_TRIAL_Z, oz, 1, n3, q3, n2 * n1, nullptr, c.stream) != cudaSuccess) return MFWQ_ECUDA;
+    if (launch_slow(S_TRIAL_Z, oz, 1, n3, q3, n2 * n1, nullptr, c.stream, c.srows) != cudaSuccess) return MFWQ_ECUDA;
     OpTrialY<T> oy{d2.B, Q, Q + SQ, P, P + SP, P + 2 * SP};
-    if (launch_slow(S_TRIAL_Y, oy, q3, n2, q2, n1, nullptr, c.stream) != cudaSuccess) return MFWQ_ECUDA;
+    if (launch_slow(S_TRIAL_Y, oy, q3, n2, q2, n1, nullptr, c.stream, c.srows) != cudaSuccess) return MFWQ_ECUDA;
     // test partials of lambda: V (Q) -> R (P[3..12))
     int st = run_test_T_partials(c, lam, nullptr);
     if (st != MFWQ_OK) return st;
-    XArgs<T> a = xargs(d1, q3 * q2, c.Nq, c.C);
+    XArgs<T> a = xargs(d1, q3 * q2, c.cs, c.C);
+    a.gs = c.Nq;
     size_t sm = sizeof(T) * ((size_t)12 * kLines * n1);
     dim3 grid((q3 * q2 + kLines - 1) / kLines);
     Ptr9<T> rp;
@@ -820,21 +1161,71 @@ int run_grad(const OpCtx<T>& c, const T* lam, const T* u, T* g6) {
 }
 
 size_t apply_scratch_elems(const int n[3], const int nq[3]) {
-    return 12 * (size_t)nq[2] * nq[1] * n[0] + 4 * (size_t)nq[2] * n[1] * n[0];
+    size_t SP, SQ;
+    scratch_strides(n, nq, &SP, &SQ);
+    return 12 * SP + 4 * SQ;
 }
 
 size_t rhs_scratch_elems(const int n[3], const int ng[3]) {
     return (size_t)ng[2] * ng[1] * n[0] + (size_t)ng[2] * n[1] * n[0];
 }
 
-int xstage_smem_bytes(int elem_size, int n1, int nq1, int lines) {
-    return (int)(((size_t)3 * lines * n1 + (size_t)3 * lines * nq1) * elem_size);
+int xstage_smem_bytes(int elem_size, int n1, int nq1, int lines, int mode) {
+    if (mode >= 4) {  // tiled: two lines-innermost slabs of 3 x (rows + 4) padded rows
+        const int pr = 128 / (kTileLines * elem_size), pad = 16 / elem_size;
+        auto tr = [&](int r) { return (size_t)r * kTileLines + (size_t)(r / pr) * pad; };
+        return (int)(3 * (tr(n1 + 4) + tr(nq1 + 4)) * elem_size);
+    }
+    size_t e = (size_t)3 * lines * n1 + (size_t)3 * lines * nq1;
+    if (mode >= 2) e += (size_t)6 * lines * nq1;
+    return (int)(e * elem_size + (mode >= 2 ? 16 : 0));
+}
+
+bool xstage_mode_valid(int elem_size, int n1, int nq1, int lines, int mode) {
+    if (mode < 0 || mode > 5) return false;
+    if (mode >= 4 && lines != kTileLines) return false;
+    if (mode >= 2 && (lines * elem_size) % 16 != 0) return false;
+    return xstage_smem_bytes(elem_size, n1, nq1, lines, mode) <= kXstageSmemMax;
 }
 
 int xstage_aux_smem_bytes(int elem_size, int n1, int nq1) {
     size_t b = (size_t)9 * kLines * n1 + (size_t)3 * kLines * nq1;  // transposed x stage
     size_t c = (size_t)12 * kLines * n1;                             // gradient x stage
     return (int)((b > c ? b : c) * elem_size);
+}
+
+constexpr int kReducedCarvePct = 50;  // preferred shared-memory carveout of the CARVE = 1 copies
+
+template <class K>
+static cudaError_t set_kernel_smem(K kern, int bytes, int carve) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && carve)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, kReducedCarvePct);
+    return e;
+}
+
+template <int MODE, int CARVE>
+static cudaError_t set_xstage_smem(int bytes) {
+    cudaError_t e = set_kernel_smem(k_xstage_apply<double, 2, MODE, CARVE>, bytes, CARVE);
+    if (e == cudaSuccess) e = set_kernel_smem(k_xstage_apply<double, 4, MODE, CARVE>, bytes, CARVE);
+    if (e == cudaSuccess) e = set_kernel_smem(k_xstage_apply<double, 8, MODE, CARVE>, bytes, CARVE);
+    if (e == cudaSuccess) e = set_kernel_smem(k_xstage_apply<float, 2, MODE, CARVE>, bytes, CARVE);
+    if (e == cudaSuccess) e = set_kernel_smem(k_xstage_apply<float, 4, MODE, CARVE>, bytes, CARVE);
+    if (e == cudaSuccess) e = set_kernel_smem(k_xstage_apply<float, 8, MODE, CARVE>, bytes, CARVE);
+    return e;
+}
+
+template <int CARVE>
+static cudaError_t set_xstage_smem_all(int bytes) {
+    cudaError_t e = set_xstage_smem<0, CARVE>(bytes);
+    if (e == cudaSuccess) e = set_xstage_smem<1, CARVE>(bytes);
+    if (e == cudaSuccess) e = set_xstage_smem<2, CARVE>(bytes);
+    if (e == cudaSuccess) e = set_xstage_smem<3, CARVE>(bytes);
+    if (e == cudaSuccess) e = set_kernel_smem(k_xstage_tiled<double, 4, CARVE>, bytes, CARVE);
+    if (e == cudaSuccess) e = set_kernel_smem(k_xstage_tiled<double, 8, CARVE>, bytes, CARVE);
+    if (e == cudaSuccess) e = set_kernel_smem(k_xstage_tiled<float, 4, CARVE>, bytes, CARVE);
+    if (e == cudaSuccess) e = set_kernel_smem(k_xstage_tiled<float, 8, CARVE>, bytes, CARVE);
+    return e;
 }
 
 // The dynamic shared-memory limit is a per-kernel attribute shared by all
@@ -844,18 +1235,8 @@ int configure_xstage_smem(int bytes) {
     if (bytes <= configured) return MFWQ_OK;
     cudaError_t e = cudaSuccess;
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    e = cudaFuncSetAttribute(k_xstage_apply<double, 2, 0>, A, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<double, 4, 0>, A, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<double, 8, 0>, A, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 2, 0>, A, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 4, 0>, A, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 8, 0>, A, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<double, 2, 1>, A, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<double, 4, 1>, A, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<double, 8, 1>, A, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 2, 1>, A, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 4, 1>, A, bytes);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_apply<float, 8, 1>, A, bytes);
+    e = set_xstage_smem_all<0>(bytes);
+    if (e == cudaSuccess) e = set_xstage_smem_all<1>(bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_applyT<double>, A, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_grad<double>, A, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_applyT<float>, A, bytes);

@@ -90,6 +90,57 @@ BandOff stage_band(Arena& a, const Band1D& b) {
     return o;
 }
 
+struct TileOff {
+    size_t start, len, v64, v32;
+    int ntile, width;
+};
+
+// Two-row tiles of a band (TileD): per tile the union window of rows 2k and
+// 2k+1 and both rows' values on it, [fams][width][ntile][2].
+TileOff stage_tiles(Arena& a, const Band1D& b) {
+    const int nt = (b.rows + 1) / 2;
+    std::vector<int> st(nt), ln(nt);
+    int width = 1;
+    for (int k = 0; k < nt; ++k) {
+        int lo = 0x7fffffff, hi = 0;
+        for (int r = 2 * k; r < std::min(2 * k + 2, b.rows); ++r)
+            if (b.len[r] > 0) {
+                lo = std::min(lo, b.start[r]);
+                hi = std::max(hi, b.start[r] + b.len[r]);
+            }
+        st[k] = hi > 0 ? lo : 0;
+        ln[k] = hi > 0 ? hi - lo : 0;
+        width = std::max(width, ln[k]);
+    }
+    std::vector<double> v((size_t)b.fams * width * nt * 2, 0.0);
+    for (int f = 0; f < b.fams; ++f)
+        for (int k = 0; k < nt; ++k)
+            for (int r = 2 * k; r < std::min(2 * k + 2, b.rows); ++r)
+                for (int t = 0; t < b.len[r]; ++t) {
+                    const int u = b.start[r] + t - st[k];
+                    v[(((size_t)f * width + u) * nt + k) * 2 + (r - 2 * k)] = b.at(f, r, t);
+                }
+    TileOff o;
+    o.start = a.add_vec(st);
+    o.len = a.add_vec(ln);
+    o.v64 = a.add_vec(v);
+    o.v32 = a.add_vec(convert<float>(v));
+    o.ntile = nt;
+    o.width = width;
+    return o;
+}
+
+template <typename T>
+TileD<T> tiles_at(unsigned char* base, const TileOff& o) {
+    TileD<T> t;
+    t.start = reinterpret_cast<const int*>(base + o.start);
+    t.len = reinterpret_cast<const int*>(base + o.len);
+    t.val = reinterpret_cast<const T*>(base + (sizeof(T) == 8 ? o.v64 : o.v32));
+    t.ntile = o.ntile;
+    t.width = o.width;
+    return t;
+}
+
 template <typename T>
 BandD<T> band_at(unsigned char* base, const BandOff& o) {
     BandD<T> b;
@@ -110,6 +161,7 @@ struct mfwq_handle_s {
     Dir1D dir[3];
     int n[3], nq[3], ng[3];
     size_t N = 0, Nq = 0;
+    size_t cs = 0;  // field stride of C64 / C32: Nq rounded up to 32 (aligned bulk copies)
     unsigned char* d_tables = nullptr;
     DirD<double> d64[3];
     DirD<float> d32[3];
@@ -126,6 +178,8 @@ struct mfwq_handle_s {
     int xlines = 4, max_xlines = 4;  // forward x-stage lines per block, FP64 (autotuned)
     int xmode = 0;                   // FP64 x-stage work mapping (autotuned)
     int xlines32 = 4, xmode32 = 1;   // the same for the FP32 operator
+    int srows = 1, srows32 = 1;      // slow-dimension output rows per thread (autotuned)
+    int xcarve = 0, xcarve32 = 0;    // x stage with the reduced shared-memory carveout (autotuned)
     KScal* dsc = nullptr;
     KScal* hsc = nullptr;    // pinned
     Profiler prof;
@@ -140,10 +194,14 @@ OpCtx<double> ctx64(mfwq_handle h) {
     for (int l = 0; l < 3; ++l) c.d[l] = h->d64[l];
     c.C = h->C64;
     c.Nq = h->Nq;
+    c.cs = h->cs;
+    c.err = h->derr;
     c.scratch = static_cast<double*>(h->scratch);
     c.stream = h->stream;
     c.xlines = h->xlines;
     c.xmode = h->xmode;
+    c.srows = h->srows;
+    c.xcarve = h->xcarve;
     return c;
 }
 
@@ -152,10 +210,14 @@ OpCtx<float> ctx32(mfwq_handle h) {
     for (int l = 0; l < 3; ++l) c.d[l] = h->d32[l];
     c.C = h->C32;
     c.Nq = h->Nq;
+    c.cs = h->cs;
+    c.err = h->derr;
     c.scratch = static_cast<float*>(h->scratch);
     c.stream = h->stream;
     c.xlines = h->xlines32;
     c.xmode = h->xmode32;
+    c.srows = h->srows32;
+    c.xcarve = h->xcarve32;
     return c;
 }
 
@@ -204,11 +266,13 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
     }
     h->N = (size_t)h->n[0] * h->n[1] * h->n[2];
     h->Nq = (size_t)h->nq[0] * h->nq[1] * h->nq[2];
+    h->cs = (h->Nq + 31) / 32 * 32;
     if (h->Nq * 9 >= ((size_t)1 << 40)) return fail(MFWQ_EINVAL, "problem too large");
 
     // ---- tables
     Arena a;
     BandOff bo[3][5];
+    TileOff to[3][2];
     size_t U64[3], UT64[3], L64[3], U32[3], UT32[3], L32[3], XQ[3], XG[3];
     size_t VE[3] = {}, VET[3] = {}, VO[3] = {}, VOT[3] = {}, LS[3] = {};
     for (int l = 0; l < 3; ++l) {
@@ -218,6 +282,8 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
         bo[l][2] = stage_band(a, d.W);
         bo[l][3] = stage_band(a, d.WT);
         bo[l][4] = stage_band(a, d.GT);
+        to[l][0] = stage_tiles(a, d.B);
+        to[l][1] = stage_tiles(a, d.W);
         U64[l] = a.add_vec(d.U);
         UT64[l] = a.add_vec(d.UT);
         L64[l] = a.add_vec(d.lam);
@@ -253,6 +319,10 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
         y.W = band_at<float>(base, bo[l][2]);
         y.WT = band_at<float>(base, bo[l][3]);
         y.GT = band_at<float>(base, bo[l][4]);
+        x.BX = tiles_at<double>(base, to[l][0]);
+        x.WX = tiles_at<double>(base, to[l][1]);
+        y.BX = tiles_at<float>(base, to[l][0]);
+        y.WX = tiles_at<float>(base, to[l][1]);
         x.U = reinterpret_cast<const double*>(base + U64[l]);
         x.UT = reinterpret_cast<const double*>(base + UT64[l]);
         x.lam = reinterpret_cast<const double*>(base + L64[l]);
@@ -277,11 +347,11 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
     }
 
     // ---- coefficient, workspace
-    ST(dmalloc((void**)&h->C64, sizeof(double) * 6 * h->Nq));
-    CU(cudaMemset(h->C64, 0, sizeof(double) * 6 * h->Nq));
+    ST(dmalloc((void**)&h->C64, sizeof(double) * 6 * h->cs));
+    CU(cudaMemset(h->C64, 0, sizeof(double) * 6 * h->cs));
     if (h->mixed) {
-        ST(dmalloc((void**)&h->C32, sizeof(float) * 6 * h->Nq));
-        CU(cudaMemset(h->C32, 0, sizeof(float) * 6 * h->Nq));
+        ST(dmalloc((void**)&h->C32, sizeof(float) * 6 * h->cs));
+        CU(cudaMemset(h->C32, 0, sizeof(float) * 6 * h->cs));
     }
     size_t sc = apply_scratch_elems(h->n, h->nq);
     size_t sr = rhs_scratch_elems(h->n, h->ng);
@@ -305,14 +375,14 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
     CU(cudaMallocHost((void**)&h->hsc, sizeof(KScal)));
     CU(cudaMallocHost((void**)&h->hnorm, sizeof(double) * 2));
 
-    const int kSmemMax = 227 * 1024;
-    int smem = std::max(xstage_smem_bytes(8, h->n[0], h->nq[0], 4), xstage_aux_smem_bytes(8, h->n[0], h->nq[0]));
-    if (smem > kSmemMax) return fail(MFWQ_EINVAL, "direction-1 size too large for the x-stage tile");
-    h->max_xlines = 4;
-    if (xstage_smem_bytes(8, h->n[0], h->nq[0], 8) <= kSmemMax) {
-        smem = std::max(smem, xstage_smem_bytes(8, h->n[0], h->nq[0], 8));
-        h->max_xlines = 8;
-    }
+    int smem = std::max(xstage_smem_bytes(8, h->n[0], h->nq[0], 4, 0), xstage_aux_smem_bytes(8, h->n[0], h->nq[0]));
+    if (smem > kXstageSmemMax) return fail(MFWQ_EINVAL, "direction-1 size too large for the x-stage tile");
+    h->max_xlines = xstage_smem_bytes(8, h->n[0], h->nq[0], 8, 0) <= kXstageSmemMax ? 8 : 4;
+    for (int es : {8, 4})
+        for (int mode = 0; mode < 6; ++mode)
+            for (int L : {2, 4, 8})
+                if (xstage_mode_valid(es, h->n[0], h->nq[0], L, mode))
+                    smem = std::max(smem, xstage_smem_bytes(es, h->n[0], h->nq[0], L, mode));
     ST(configure_xstage_smem(smem));
     CU(cudaDeviceSynchronize());
     return MFWQ_OK;
@@ -487,18 +557,23 @@ int mfwq_eval_coeff(mfwq_handle h, int geometry, const double* modes_host, int n
 }
 
 namespace {
-__global__ void k_to_f32(const double* __restrict__ x, float* __restrict__ y, size_t n) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) y[i] = (float)x[i];
+// y[s][cs] = x[s][n] for s < 6 (coefficient fields into the padded FP32 copy)
+__global__ void k_fields_to_f32(const double* __restrict__ x, size_t n, float* __restrict__ y, size_t cs) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < 6 * n; i += (size_t)gridDim.x * blockDim.x) {
+        const size_t s = i / n, k = i - s * n;
+        y[s * cs + k] = (float)x[i];
+    }
 }
 }  // namespace
 
 int mfwq_set_coeff(mfwq_handle h, const double* C_dev) {
     ProfScope _ps(h ? &h->prof : nullptr);
     if (!h || !C_dev) return fail(MFWQ_EINVAL, "bad argument");
-    CU(cudaMemcpyAsync(h->C64, C_dev, sizeof(double) * 6 * h->Nq, cudaMemcpyDeviceToDevice, h->stream));
+    CU(cudaMemcpy2DAsync(h->C64, sizeof(double) * h->cs, C_dev, sizeof(double) * h->Nq, sizeof(double) * h->Nq, 6,
+                         cudaMemcpyDeviceToDevice, h->stream));
     if (h->mixed) {
         launch_begin(S_SETUP, h->stream);
-        k_to_f32<<<1024, 256, 0, h->stream>>>(C_dev, h->C32, 6 * h->Nq);
+        k_fields_to_f32<<<1024, 256, 0, h->stream>>>(C_dev, h->Nq, h->C32, h->cs);
         launch_end(S_SETUP, h->stream);
         CU(cudaGetLastError());
     }
@@ -675,35 +750,62 @@ int tune_xstage(mfwq_handle h, bool f32, int* err) {
     if (cudaMemsetAsync(x, 0, sizeof(T) * h->N, h->stream) != cudaSuccess) { *err = MFWQ_ECUDA; return 4; }
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) { *err = MFWQ_ECUDA; return 4; }
+    OpCtx<T> c;
+    for (int l = 0; l < 3; ++l) c.d[l] = f32 ? *(DirD<T>*)&h->d32[l] : *(DirD<T>*)&h->d64[l];
+    c.C = f32 ? (const T*)h->C32 : (const T*)h->C64;
+    c.Nq = h->Nq;
+    c.cs = h->cs;
+    c.err = h->derr;
+    c.scratch = static_cast<T*>(h->scratch);
+    c.stream = h->stream;
+    // one untimed apply, then three timed ones
+    auto time_apply = [&]() -> float {
+        if (run_apply<T>(c, x, y, nullptr) != MFWQ_OK) { *err = MFWQ_ECUDA; return 1e30f; }
+        cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < 3; ++r) run_apply<T>(c, x, y, nullptr);
+        cudaEventRecord(e1, h->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms;
+    };
+    // the x stage first (slow stages one row per thread), then the slow stages' rows with that x stage
     float best_ms = 1e30f;
-    int best = f32 ? 14 : 4;
-    for (int mode = 0; mode < 2; ++mode)
-        for (int L : {2, 4, 8}) {
-            if (L > h->max_xlines) continue;
-            OpCtx<T> c;
-            for (int l = 0; l < 3; ++l) c.d[l] = f32 ? *(DirD<T>*)&h->d32[l] : *(DirD<T>*)&h->d64[l];
-            c.C = f32 ? (const T*)h->C32 : (const T*)h->C64;
-            c.Nq = h->Nq;
-            c.scratch = static_cast<T*>(h->scratch);
-            c.stream = h->stream;
-            c.xlines = L;
-            c.xmode = mode;
-            if (run_apply<T>(c, x, y, nullptr) != MFWQ_OK) { *err = MFWQ_ECUDA; break; }
-            cudaEventRecord(e0, h->stream);
-            for (int r = 0; r < 3; ++r) run_apply<T>(c, x, y, nullptr);
-            cudaEventRecord(e1, h->stream);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = 10 * mode + L;
+    int best_mode = 0, best_L = 4, best_R = 1, best_carve = 0;
+    c.srows = 1;
+    for (int carve = 0; carve < 2 && *err == MFWQ_OK; ++carve)
+        for (int mode = 0; mode < 6 && *err == MFWQ_OK; ++mode)
+            for (int L : {2, 4, 8}) {
+                if ((mode < 4 && L > h->max_xlines) || !xstage_mode_valid((int)sizeof(T), h->n[0], h->nq[0], L, mode))
+                    continue;
+                c.xlines = L;
+                c.xmode = mode;
+                c.xcarve = carve;
+                const float ms = time_apply();
+                if (*err != MFWQ_OK) break;
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_mode = mode;
+                    best_L = L;
+                    best_carve = carve;
+                }
             }
+    c.xlines = best_L;
+    c.xmode = best_mode;
+    c.xcarve = best_carve;
+    for (int R : {2, 4}) {
+        if (*err != MFWQ_OK) break;
+        c.srows = R;
+        const float ms = time_apply();
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_R = R;
         }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (cudaGetLastError() != cudaSuccess) *err = MFWQ_ECUDA;
-    return best;
+    return 1000 * best_carve + 100 * best_R + 10 * best_mode + best_L;
 }
 }  // namespace
 
@@ -719,17 +821,22 @@ extern "C" int mfwq_autotune(mfwq_handle h, const char* cache_path, int* xlines_
             if (err != MFWQ_OK) return fail(err, "autotune: a timing launch failed");
             cache_store(cache_path, key, code);
         }
-        int L = code % 10, mode = code / 10;
-        if (L > h->max_xlines) L = h->max_xlines;
+        int L = code % 10, mode = (code / 10) % 10, R = (code / 100) % 10, carve = (code / 1000) % 10 ? 1 : 0;
+        if (mode < 4 && L > h->max_xlines) L = h->max_xlines;
+        if (R != 2 && R != 4) R = 1;
         if (prec) {
             h->xlines32 = L;
             h->xmode32 = mode;
+            h->srows32 = R;
+            h->xcarve32 = carve;
         } else {
             h->xlines = L;
             h->xmode = mode;
+            h->srows = R;
+            h->xcarve = carve;
         }
     }
-    if (xlines_out) *xlines_out = 10 * h->xmode + h->xlines;
+    if (xlines_out) *xlines_out = 1000 * h->xcarve + 100 * h->srows + 10 * h->xmode + h->xlines;
     return MFWQ_OK;
 }
 

@@ -28,19 +28,20 @@
 
 #include "kernels.h"
 #include "prof.h"
+#include "ptx_async.cuh"
 
 namespace mfwq {
 namespace {
+
+using ptx::mbar_expect_tx;
+using ptx::mbar_init;
+using ptx::mbar_wait;
+using ptx::smem_u32;
 
 constexpr int kTcThreads = 128;
 constexpr int kTileM = 128;
 constexpr int kChunkBytes = 128;           // K bytes per chunk and row
 constexpr int kStages = 2;
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
 
 // Shared-memory matrix descriptor, no swizzle, K-major.
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -56,29 +57,6 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint
 // BF16 = 1 for kind::f16), both K-major, N and M encoded.
 __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, int M, int N) {
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count));
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait: false after kWaitCycles.
-__device__ bool mbar_wait(uint32_t a, uint32_t parity) {
-    long long t0 = clock64();
-    while (!mbar_try_wait(a, parity)) {
-        if (clock64() - t0 > kWaitCycles) return false;
-    }
-    return true;
 }
 
 template <int KIND>
@@ -305,9 +283,6 @@ __device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
     return d;
 }
 
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-}
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t mbar) {
     asm volatile(

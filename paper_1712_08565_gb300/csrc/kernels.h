@@ -11,13 +11,21 @@ namespace mfwq {
 template <typename T>
 struct OpCtx {
     DirD<T> d[3];
-    const T* C;        // [6][Nq]
-    size_t Nq;
+    const T* C;        // [6][cs]: field s at C + s * cs, Nq values each
+    size_t Nq;         // quadrature points
+    size_t cs;         // field stride of C, a multiple of 32
     T* scratch;        // apply_scratch_elems() elements of T
     cudaStream_t stream;
     int xlines = 4;    // (q3, q2) lines per block of the forward x stage: 2, 4 or 8
-    int xmode = 0;     // forward x-stage work mapping: 0 per (line, item), 1 per item over all lines
+    int xmode = 0;     // forward x-stage work mapping: 0 per (line, item), 1 per item over all lines,
+                       // 2 and 3 the same with the block's inputs prefetched by bulk copies,
+                       // 4 and 5 two-row tiles over 4 or 8 lines (8 lines per block)
+    int xcarve = 0;    // 1: forward x stage with the reduced shared-memory carveout (larger L1)
+    int srows = 1;     // output rows per thread of the slow-dimension stages: 1, 2 or 4
+    int* err = nullptr;  // device error word: set when a bounded wait times out
 };
+
+constexpr int kXstageSmemMax = 227 * 1024;
 
 // y = K~ x, y = K~^T x, g6 = dJ/dC (Algorithm 2 and its transpose).  A nonzero
 // *skip (device flag, may be NULL) turns every launch into a no-op.
@@ -30,7 +38,8 @@ int run_grad(const OpCtx<T>& c, const T* lam, const T* u, T* g6);
 
 size_t apply_scratch_elems(const int n[3], const int nq[3]);
 size_t rhs_scratch_elems(const int n[3], const int ng[3]);
-int xstage_smem_bytes(int elem_size, int n1, int nq1, int lines);  // forward x stage
+int xstage_smem_bytes(int elem_size, int n1, int nq1, int lines, int mode);  // forward x stage
+bool xstage_mode_valid(int elem_size, int n1, int nq1, int lines, int mode);
 int xstage_aux_smem_bytes(int elem_size, int n1, int nq1);         // transposed and gradient x stages
 int configure_xstage_smem(int bytes);
 

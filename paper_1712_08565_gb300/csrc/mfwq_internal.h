@@ -67,10 +67,25 @@ struct BandD {
     MFWQ_HD T lane(int f, int r, int t) const { return valT[((size_t)f * width + t) * rows + r]; }
 };
 
+// A band regrouped into tiles of two consecutive rows (rows 2k, 2k+1): tile
+// k covers columns start[k] .. start[k] + len[k] - 1, the union of its rows'
+// bands, and val holds both rows' values on that window, zero outside a
+// row's own band: [fams][width][ntile][2], width = max len.
+template <typename T>
+struct TileD {
+    const int* start;
+    const int* len;
+    const T* val;
+    int ntile, width;
+    // the two rows' values at window offset u of tile k, family f
+    MFWQ_HD const T* pair(int f, int u, int k) const { return val + (((size_t)f * width + u) * ntile + k) * 2; }
+};
+
 template <typename T>
 struct DirD {
     int n, nq, ng;
     BandD<T> B, BT, W, WT, GT;
+    TileD<T> BX, WX;  // B and W in two-row tiles (the tiled x stage)
     const T* U;     // [n][n]
     const T* UT;    // [n][n]
     const T* lam;   // [n]

@@ -373,7 +373,9 @@ class Operator:
         _check(lib().mfwq_sync(self._h))
 
     def autotune(self, cache_path: str | None = None) -> int:
-        """Pick the x-stage lines per block by timing (mfwq_autotune); returns it."""
+        """Pick the apply's launch shapes by timing (mfwq_autotune); returns the
+        FP64 choice as 1000 * reduced carveout + 100 * slow-stage rows
+        + 10 * x-stage mapping + lines."""
         v = ctypes.c_int()
         _check(lib().mfwq_autotune(self._h, cache_path.encode() if cache_path else None, ctypes.byref(v)))
         return v.value

@@ -95,22 +95,57 @@ def test_batch_with_converged_patch_and_maxit(mf):
         op.close()
 
 
-@pytest.mark.parametrize("mode,lines", [(m, L) for m in (0, 1) for L in (2, 4, 8)])
-def test_every_xstage_variant_keeps_parity(mf, tmp_path, mode, lines):
-    """Each (mapping, lines) variant the autotuner may pick gives the oracle's apply."""
+@pytest.mark.parametrize("mode,lines,rows,carve", [(m, L, 1, 0) for m in (0, 1, 2, 3) for L in (2, 4, 8)]
+                         + [(4, 8, 1, 0), (5, 8, 1, 0), (0, 4, 2, 0), (2, 2, 4, 0), (3, 8, 4, 0), (4, 8, 4, 0),
+                            (1, 4, 1, 1), (5, 8, 2, 1)])
+def test_every_xstage_variant_keeps_parity(mf, tmp_path, mode, lines, rows, carve):
+    """Each launch shape the autotuner may pick gives the oracle's apply: x
+    stage (mapping, lines, carveout copy) and slow-stage rows per thread; 345
+    lines and 10 or 23 rows per slow stage, so every shape leaves a partial
+    last block."""
     p, nel = 3, (7, 5, 9)
     op = _patch(mf, p, nel, 4)
     cache = str(tmp_path / "forced.jsonl")
     key = "xstage p=%d n1=%d nq1=%d nq2=%d nq3=%d fp64" % (p, op.n[0], op.nq[0], op.nq[1], op.nq[2])
+    code = 1000 * carve + 100 * rows + 10 * mode + lines
     with open(cache, "w") as fh:
-        fh.write('{"key": "%s", "xstage": %d}\n' % (key, 10 * mode + lines))
-    assert op.autotune(cache) == 10 * mode + lines
+        fh.write('{"key": "%s", "xstage": %d}\n' % (key, code))
+    assert op.autotune(cache) == code
     tabs = [O.tables_1d(inputs.open_uniform_knots(p, nel[l]), p) for l in range(3)]
     C6 = O.coefficient_grid(tabs, "ring", inputs.fourier_modes(4), 0.3)
     x = inputs.uniform_vector(op.shape, 8)
     ref = O.apply_alg2(tabs, O.full_coeff(C6), x)
     y = op.apply(torch.from_numpy(x).to(DEV)).cpu().numpy()
     assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    if rows > 1:  # the transposed apply runs its slow stages with the same rows
+        yT = op.apply_T(torch.from_numpy(x).to(DEV)).cpu().numpy()
+        refT = O.apply_T_alg2(tabs, O.full_coeff(C6), x)
+        assert np.abs(yT - refT).max() <= 1e-12 * np.abs(refT).max()
+    op.close()
+
+
+@pytest.mark.parametrize("mode,lines", [(m, L) for m in (0, 1, 2, 3) for L in (2, 4, 8)] + [(4, 8), (5, 8)])
+def test_every_fp32_xstage_variant(mf, tmp_path, mode, lines):
+    """The same for the FP32 operator of a mixed handle (FP32 prefetch needs 4
+    or 8 lines; a forced 2-line prefetch runs the plain mapping).  n1 = 11 and
+    nq1 = 25 are odd, so the two-row tiles end with a half tile, and 399 lines
+    leave a partial last block of the tiled mappings."""
+    p, nel = 4, (9, 6, 7)
+    knots = [inputs.open_uniform_knots(p, nel[l]) for l in range(3)]
+    op = mf.Operator(p, knots, mixed=True, device=DEV)
+    tabs = [O.tables_1d(knots[l], p) for l in range(3)]
+    C6 = O.coefficient_grid(tabs, "ring", inputs.fourier_modes(5), 0.3)
+    op.set_coeff(torch.from_numpy(np.ascontiguousarray(C6)).to(DEV))
+    cache = str(tmp_path / "forced32.jsonl")
+    base = "xstage p=%d n1=%d nq1=%d nq2=%d nq3=%d" % (p, op.n[0], op.nq[0], op.nq[1], op.nq[2])
+    with open(cache, "w") as fh:
+        fh.write('{"key": "%s fp64", "xstage": 4}\n' % base)
+        fh.write('{"key": "%s fp32", "xstage": %d}\n' % (base, 400 + 10 * mode + lines))
+    op.autotune(cache)
+    x = inputs.uniform_vector(op.shape, 10)
+    ref = O.apply_alg2(tabs, O.full_coeff(C6), x)
+    y = op.apply_f32(torch.from_numpy(x).float().to(DEV)).double().cpu().numpy()
+    assert np.abs(y - ref).max() <= 1e-5 * np.abs(ref).max()
     op.close()
 
 
@@ -119,7 +154,8 @@ def test_autotune_keeps_parity(mf, tmp_path):
     op = _patch(mf, p, nel, 2)
     cache = str(tmp_path / "tune.jsonl")
     L = op.autotune(cache)
-    assert L % 10 in (2, 4, 8) and L // 10 in (0, 1)
+    assert L % 10 in (2, 4, 8) and (L // 10) % 10 in (0, 1, 2, 3, 4, 5) and (L // 100) % 10 in (1, 2, 4)
+    assert L // 1000 in (0, 1)
     assert os.path.exists(cache) and '"xstage": %d' % L in open(cache).read()
     assert op.autotune(cache) == L  # cache hit
     tabs = [O.tables_1d(inputs.open_uniform_knots(p, nel[l]), p) for l in range(3)]

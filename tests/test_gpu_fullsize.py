@@ -1,0 +1,184 @@
+"""GPU parity at the workload sizes the bench times, in the bench's launch
+configuration (same setup, autotuned x stage): outputs the oracle computes one
+by one (sampled rows of K~ v, of K~^T v, of the load vector), the full FD
+preconditioner where the oracle can afford it, and properties that hold at any
+size (residuals of the solves measured by the oracle).
+
+Sizes: the 130^3 ring (p = 4) and its p = 2..6 sweep at 128 elements, the
+196^3 ring (p = 6, mixed precision), the 65^3 ring with a random K field
+(p = 3, adjoint gradient) and the 64 uneven patches of the batched workload."""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1712_08565_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+DEV = "cuda:0"
+TUNE = os.path.join(tempfile.gettempdir(), "mfwq_autotune.jsonl")
+
+
+@pytest.fixture(scope="module")
+def mf():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1712_08565_gb300 import build
+    build.build()
+    from paper_1712_08565_gb300 import mfwq
+    return mfwq
+
+
+def _ring(mf, p, nel, mixed=False, modes=None, kscale=0.0):
+    knots = [inputs.open_uniform_knots(p, nel)] * 3
+    op = mf.Operator(p, knots, mixed=mixed, device=DEV)
+    op.set_coeff(op.eval_coeff("ring", modes, kscale))
+    op.autotune(TUNE)
+    tabs = [O.tables_1d(knots[0], p)] * 3
+    return op, tabs
+
+
+def _rows(shape, count, seed):
+    """Sampled output rows: the corners and faces (boundary bands) plus random interior rows."""
+    n3, n2, n1 = shape
+    g = inputs.rng(seed)
+    rows = {(0, 0, 0), (n3 - 1, n2 - 1, n1 - 1), (0, n2 // 2, n1 - 1), (n3 // 2, 0, 1), (2, n2 - 3, n1 // 3)}
+    while len(rows) < count:
+        rows.add(tuple(int(v) for v in (g.integers(n3), g.integers(n2), g.integers(n1))))
+    return sorted(rows)
+
+
+@pytest.mark.parametrize("p", [4, 2, 3, 5, 6])
+def test_apply_sampled_rows_at_128_elements(mf, p):
+    op, tabs = _ring(mf, p, 128)
+    x = inputs.uniform_vector(op.shape, 40 + p)
+    y = op.apply(torch.from_numpy(x).to(DEV)).cpu().numpy()
+    rows = _rows(op.shape, 40, p)
+    ref = O.apply_rows(tabs, O.coefficient_box_fn(tabs, "ring"), x, rows)
+    got = np.array([y[r] for r in rows])
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-12 * scale
+    if p == 4:
+        yT = op.apply_T(torch.from_numpy(x).to(DEV)).cpu().numpy()
+        # (K~^T x)_j = sum_i K~_ij x_i: by the adjoint identity against unit vectors,
+        # e_j^T K~^T x = (K~ e_j)^T x, which the oracle evaluates from its rows
+        for r in rows[:6]:
+            e = np.zeros(op.shape)
+            e[r] = 1.0
+            col = op.apply(torch.from_numpy(e).to(DEV)).cpu().numpy()
+            assert abs(yT[r] - float(np.sum(col * x))) <= 1e-12 * np.abs(yT).max()
+    op.close()
+
+
+def test_fd_full_at_130_cubed(mf):
+    op, tabs = _ring(mf, 4, 128)
+    r = inputs.uniform_vector(op.shape, 7)
+    z = op.fd_precond(torch.from_numpy(r).to(DEV)).cpu().numpy()
+    ref = O.fd_apply(O.fd_setup(tabs), r)
+    assert np.abs(z - ref).max() <= 1e-12 * np.abs(ref).max()
+    op.close()
+
+
+def test_solve_130_cubed_residual_and_load_vector(mf):
+    op, tabs = _ring(mf, 4, 128)
+    f = op.load_vector("ring", "sines")
+    rows = _rows(op.shape, 30, 3)
+    fr = O.load_vector_rows(tabs, "ring", O.forcing_sines, rows)
+    fn = f.cpu().numpy()
+    assert np.abs(np.array([fn[r] for r in rows]) - fr).max() <= 1e-13 * np.abs(fn).max()
+    u, info = op.solve(f, rtol=1e-10)
+    assert info.converged and info.rel_residual <= 1e-10
+    un = u.cpu().numpy()
+    Ku = O.apply_rows(tabs, O.coefficient_box_fn(tabs, "ring"), un, rows)
+    res = np.array([fn[r] for r in rows]) - Ku
+    # every entry of the residual is bounded by its 2-norm, <= 1e-10 ||f||_2 (with rounding slack)
+    assert np.abs(res).max() <= 2e-10 * np.linalg.norm(fn)
+    op.close()
+
+
+def test_mixed_196_cubed(mf):
+    op, tabs = _ring(mf, 6, 192, mixed=True)
+    r = inputs.uniform_vector(op.shape, 8)
+    z64 = op.fd_precond(torch.from_numpy(r).to(DEV)).cpu().numpy()
+    ref = O.fd_apply(O.fd_setup(tabs), r)
+    assert np.abs(z64 - ref).max() <= 1e-12 * np.abs(ref).max()
+    z32 = op.fd_precond_f32(torch.from_numpy(r).float().to(DEV)).double().cpu().numpy()
+    assert np.linalg.norm(z32 - ref) <= 1e-2 * np.linalg.norm(ref)
+    f = op.load_vector("ring", "sines")
+    u, info = op.solve(f, rtol=1e-8, inner_rtol=1e-4)
+    assert info.converged and info.rel_residual <= 1e-8
+    rows = _rows(op.shape, 20, 4)
+    fn, un = f.cpu().numpy(), u.cpu().numpy()
+    Ku = O.apply_rows(tabs, O.coefficient_box_fn(tabs, "ring"), un, rows)
+    assert np.abs(np.array([fn[r] for r in rows]) - Ku).max() <= 2e-8 * np.linalg.norm(fn)
+    op.close()
+
+
+def test_adjoint_gradient_65_cubed(mf):
+    """K = exp(0.3 g) I with a seeded 8-mode Fourier field, J = 1/2 |u - u_target|^2
+    with u_target the solution for g = 0: dJ/dC against the oracle gradient and
+    against central differences along 20 random directions.  The step h = 1e-4
+    (relative to |C|) keeps the central-difference truncation (h^2) and the
+    solver's noise (residual 1e-12 / 2h) both near 1e-8 of the derivative."""
+    p, nel = 3, 64
+    modes = inputs.fourier_modes(123)
+    op, tabs = _ring(mf, p, nel, modes=modes, kscale=0.3)
+    C = op.eval_coeff("ring", modes, 0.3)
+    C0 = op.eval_coeff("ring")
+    f = op.load_vector("ring", "sines")
+    op.set_coeff(C0)
+    u_t, _ = op.solve(f, rtol=1e-12, maxit=2000)
+    op.set_coeff(C)
+    u, info = op.solve(f, rtol=1e-12, maxit=2000)
+    assert info.converged
+    lam, infoT = op.solve_T(u - u_t, rtol=1e-12, maxit=2000)
+    assert infoT.converged
+    g = op.grad_coeff(lam, u)
+    ref = O.grad_coeff(tabs, lam.cpu().numpy(), u.cpu().numpy())
+    assert np.abs(g.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max()
+
+    def J(Cv):
+        op.set_coeff(Cv)
+        uu, ii = op.solve(f, rtol=1e-12, maxit=2000)
+        assert ii.converged
+        return 0.5 * float(((uu - u_t) ** 2).sum())
+
+    gen = torch.Generator(device="cpu").manual_seed(20)
+    h = 1e-4
+    for _ in range(20):
+        d = ((torch.rand(C.shape, generator=gen, dtype=torch.float64) - 0.5) * 2).to(DEV) * C.abs()
+        fd = (J(C + h * d) - J(C - h * d)) / (2 * h)
+        an = float((g * d).sum())
+        assert abs(fd - an) <= 1e-5 * abs(an), (fd, an)
+    op.close()
+
+
+def test_batched_64_patches(mf):
+    specs = inputs.batch_patches(count=64, seed=0)
+    ops, fs, tabs = [], [], []
+    for i, (p, nel) in enumerate(specs):
+        knots = [inputs.open_uniform_knots(p, nel[l]) for l in range(3)]
+        op = mf.Operator(p, knots, mixed=True, device=DEV)
+        op.set_coeff(op.eval_coeff("ring", inputs.fourier_modes(1000 + i), 0.3))
+        op.autotune(TUNE)
+        ops.append(op)
+        fs.append(op.load_vector("ring", "sines"))
+        tabs.append([O.tables_1d(knots[l], p) for l in range(3)] if i < 6 else None)
+    b = mf.Batch(ops)
+    us, infos = b.solve(fs, rtol=1e-8, force_fp64=True)
+    assert all(i.converged and i.rel_residual <= 1e-8 for i in infos)
+    um, minfos = b.solve(fs, [torch.empty_like(f) for f in fs], rtol=1e-8)
+    assert all(i.converged and i.rel_residual <= 1e-8 for i in minfos)
+    for i in range(6):  # the oracle checks the residual of a few patches, FP64 and mixed
+        box = O.coefficient_box_fn(tabs[i], "ring", inputs.fourier_modes(1000 + i), 0.3)
+        rows = _rows(ops[i].shape, 8, i)
+        fn = fs[i].cpu().numpy()
+        for u in (us[i], um[i]):
+            Ku = O.apply_rows(tabs[i], box, u.cpu().numpy(), rows)
+            assert np.abs(np.array([fn[r] for r in rows]) - Ku).max() <= 2e-8 * np.linalg.norm(fn)
+    b.close()
+    for op in ops:
+        op.close()
