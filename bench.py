@@ -160,6 +160,49 @@ def stage_flops(mf, p, knots):
     }, n, nq
 
 
+def csrc_digest() -> str:
+    """sha256 over the library's CUDA/C++ sources (names and contents): the
+    identity of the kernels a profile's counters were taken on."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1712_08565_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from the ncu summaries
+    under profiles/ (lines '<!-- traffic kernel="..." workload="..."
+    bytes_per_launch=B csrc_sha256=H -->'), or None when no summary was taken
+    on the current sources."""
+    import re
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    digest = csrc_digest()
+    pat = re.compile(r'<!-- traffic kernel="([^"]+)" workload="([^"]+)" bytes_per_launch=(\d+) csrc_sha256=([0-9a-f]+) -->')
+    for name in sorted(os.listdir(d)):
+        if not name.endswith(".md"):
+            continue
+        with open(os.path.join(d, name)) as fh:
+            for m in pat.finditer(fh.read()):
+                if m.group(1) == kernel and m.group(2) == workload and m.group(4) == digest:
+                    return int(m.group(3))
+    return None
+
+
+def xstage_kernel_name(code: int, elem: str) -> str:
+    """Kernel that runs the forward x stage for an autotune code."""
+    L, mode, carve = code % 10, (code // 10) % 10, (code // 1000) % 10
+    if mode >= 4:
+        return "k_xstage_tiled<%s, %d, %d>" % (elem, 4 if mode == 4 else 8, carve)
+    return "k_xstage_apply<%s, %d, %d, %d>" % (elem, L, mode, carve)
+
+
 def fp64_peak_tflops(sm_mhz=None):
     mhz = SM_MAX_MHZ_NOMINAL if sm_mhz is None else sm_mhz
     return NUM_SMS * mhz * 1e6 * FP64_FLOP_PER_CLK_SM / 1e12
@@ -250,8 +293,9 @@ def make_op(mf, p, nel, mixed=False, fd="tf32", device=None, geometry="ring", tu
     C = op.eval_coeff(geometry)
     op.set_coeff(C)
     del C
-    if tune:  # x-stage tile shape, timed once per shape and cached
-        op.autotune(os.path.join(tempfile.gettempdir(), "mfwq_autotune.jsonl"))
+    op.tune_code = None
+    if tune:  # launch shapes, timed once per patch shape and cached
+        op.tune_code = op.autotune(os.path.join(tempfile.gettempdir(), "mfwq_autotune.jsonl"))
     return op, knots
 
 
@@ -443,8 +487,9 @@ def run_ours(args):
     dom_ms = stages[dom][0] / stages[dom][1]
     achieved = flops[dom] / (dom_ms * 1e-3) / 1e12
     peak = fp64_peak_tflops()
-    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+    dom_kernel = xstage_kernel_name(op.tune_code, "double") if dom == "xstage" and op.tune_code else dom
+    roofline = {"bound": "alu", "kernel": dom, "kernel_function": dom_kernel, "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": achieved / peak, "traffic": profiled_traffic(dom_kernel, WORKLOAD["name"]),
                 "peak_source": "FP64 pipe: 152 SMs x 2070 MHz x 4 flop/clk (1.25 TFLOP/s nominal); not in MEASURED_PEAKS.json",
                 "algorithmic_flops_per_launch": flops[dom], "ms_per_launch": dom_ms}
 
