@@ -12,6 +12,9 @@ efficient isogeometric k-method"):
 * Section 2.2  -- weighted quadrature: Eq. (exactness1d), Eq. (weights-support),
                   the point rule, Eq. (stiffness_sum), Eq. (Kwq), Eq. (exactness_K).
 * Section 2.3  -- Kronecker products, Eq. (ordering), Eq. (sum-factorization).
+* Eq. (M), (Mwq), (exactness_M) -- the mass (reaction) term c = alpha det J and
+                  its WQ approximation M~_ij = sum_q w_iq c(x_q) b_j(x_q).
+* Section 3.1  -- the factorisation M~ = W D B, Algorithm 1.
 * Section 3.2  -- the factorisation K~ = sum_ab W^(ab) D^(ab) B^(b), Algorithm 2.
 * Section 4    -- ring domain, Eq. (exact-solution), BiCGStab + FD preconditioner.
 
@@ -33,6 +36,12 @@ Readings of passages the paper leaves open (each is listed in the design doc):
 * R7  BiCGStab: right preconditioning, x0 given (default 0), r^_0 = r_0,
       convergence tested on the half step s and on the full step r.
 * R8  Load vector: tensor Gauss with p_l+1 points per span in direction l, c = |det J|.
+* R14 Mass weights: the 1D family W^(00) of the stiffness (exactness for
+      int b_i b_j, Eq. (exactness1d)) in every direction, so the mass term
+      uses the same weights as the (alpha != l, beta != l) stiffness factors.
+* R15 FD with a reaction term: P_sigma = P + sigma M3(x)M2(x)M1, whose inverse
+      is U diag(1/(l1+l2+l3+sigma)) U^T with the same U (sigma >= 0 chosen by
+      the caller; the paper gives no preconditioner for alpha > 0).
 
 Parity unpinned (no value in the paper or in mathematics fixes them):
 boundary-row weight values beyond their exactness residual, BiCGStab
@@ -577,6 +586,75 @@ def apply_rows(tabs, coef_box, V, rows):
 
 
 # ---------------------------------------------------------------------------
+# Section 3.1: the WQ mass operator (reaction term alpha u of Eq. (poisson))
+# ---------------------------------------------------------------------------
+def mass_wq(tabs, c) -> sp.csr_matrix:
+    """Explicit M~ = W D B of Section 3.1: W = W3^(00) (x) W2^(00) (x) W1^(00)
+    (reading R14), D = diag(c(x_q)), B = B3 (x) B2 (x) B1 (values).  c holds
+    c = alpha det J at the quadrature points, direction 1 fastest."""
+    Wk = kron3(*[tabs[l].W[(0, 0)] for l in (2, 1, 0)])
+    Bk = kron3(*[tabs[l].B0 for l in (2, 1, 0)])
+    return (Wk @ sp.diags(np.ravel(c)) @ Bk).tocsr()
+
+
+def mass_wq_entries(tabs, c) -> np.ndarray:
+    """Dense M~ entry by entry from Eq. (Mwq): M~_ij = sum_q w_{i,q} c(x_q)
+    b_j(x_q), tensor weights w_{i,q} = prod_l w^(00)_{l,i_l,q_l}.  Tiny grids."""
+    n = [t.n for t in tabs]
+    nq = [t.nq for t in tabs]
+    N = n[0] * n[1] * n[2]
+    cg = np.reshape(c, (nq[2], nq[1], nq[0]))
+    M = np.zeros((N, N))
+    for i in range(N):
+        i3, rem = divmod(i, n[0] * n[1])
+        i2, i1 = divmod(rem, n[0])
+        w = np.einsum("c,b,a->cba", tabs[2].W[(0, 0)][i3], tabs[1].W[(0, 0)][i2], tabs[0].W[(0, 0)][i1])
+        for j in range(N):
+            j3, rem = divmod(j, n[0] * n[1])
+            j2, j1 = divmod(rem, n[0])
+            b = np.einsum("c,b,a->cba", tabs[2].B0[:, j3], tabs[1].B0[:, j2], tabs[0].B0[:, j1])
+            M[i, j] = np.sum(w * cg * b)
+    return M
+
+
+def apply_mass_alg1(tabs, c, V):
+    """w = M~ v by the three steps of Algorithm 1: v~ = B v, then the pointwise
+    product with c, then w = W v~~, each Kronecker product by Eq.
+    (sum-factorization).  V, result [i3][i2][i1]; c [q3][q2][q1]."""
+    vt = kron_action(tabs[2].B0, tabs[1].B0, tabs[0].B0, V)
+    return kron_action(tabs[2].W[(0, 0)], tabs[1].W[(0, 0)], tabs[0].W[(0, 0)], c * vt)
+
+
+def apply_mass_T(tabs, c, Y):
+    """M~^T y = B^T D W^T y."""
+    s = kron_action(tabs[2].W[(0, 0)].T, tabs[1].W[(0, 0)].T, tabs[0].W[(0, 0)].T, Y)
+    return kron_action(tabs[2].B0.T, tabs[1].B0.T, tabs[0].B0.T, c * s)
+
+
+def grad_mass_coeff(tabs, LAM, U):
+    """dJ/dc(q) = -(W^T lambda)_q (B u)_q: M~ is linear in every c(x_q)."""
+    S = kron_action(tabs[2].W[(0, 0)].T, tabs[1].W[(0, 0)].T, tabs[0].W[(0, 0)].T, LAM)
+    return -S * kron_action(tabs[2].B0, tabs[1].B0, tabs[0].B0, U)
+
+
+def mass_rows(tabs, c_box, V, rows):
+    """Selected entries (M~ v)_i, each from Eq. (Mwq) on the points where the
+    tensor weights of row i may be nonzero.  c_box(S3, S2, S1) returns c on
+    that point box, shape (|S3|, |S2|, |S1|)."""
+    out = np.empty(len(rows))
+    for r, (i3, i2, i1) in enumerate(rows):
+        ii = (i1, i2, i3)
+        S = [np.nonzero(tabs[l].W[(0, 0)][ii[l]] != 0)[0] for l in range(3)]
+        J = [np.nonzero(np.any(tabs[l].B0[S[l]] != 0, axis=0))[0] for l in range(3)]
+        vloc = V[np.ix_(J[2], J[1], J[0])]
+        B = [tabs[l].B0[np.ix_(S[l], J[l])] for l in range(3)]
+        g = np.einsum("ca,db,ef,abf->cde", B[2], B[1], B[0], vloc, optimize=True)
+        w = [tabs[l].W[(0, 0)][ii[l], S[l]] for l in range(3)]
+        out[r] = np.einsum("c,d,e,cde,cde->", w[2], w[1], w[0], c_box(S[2], S[1], S[0]), g, optimize=True)
+    return out
+
+
+# ---------------------------------------------------------------------------
 # Geometry and coefficient, Eq. (C) with reading R5
 # ---------------------------------------------------------------------------
 def ring_map(xi1, xi2, xi3):
@@ -642,6 +720,29 @@ def coefficient_box_fn(tabs, geometry, modes=None, scale=0.0):
     return box
 
 
+def mass_coefficient_points(geometry, xi1, xi2, xi3, alpha):
+    """c = alpha |det J| (Eq. (M)) at parametric points, alpha a constant."""
+    xi1, xi2, xi3 = np.broadcast_arrays(*(np.asarray(a, dtype=np.float64) for a in (xi1, xi2, xi3)))
+    if geometry == "cube":
+        return np.full(xi1.shape, float(alpha))
+    if geometry == "ring":
+        return alpha * np.abs(np.linalg.det(ring_jacobian(xi1, xi2, xi3)))
+    raise ValueError(geometry)
+
+
+def mass_coefficient_grid(tabs, geometry, alpha):
+    """c on the full grid of WQ points, shape (nq3, nq2, nq1)."""
+    X3, X2, X1 = np.meshgrid(tabs[2].xq, tabs[1].xq, tabs[0].xq, indexing="ij")
+    return mass_coefficient_points(geometry, X1, X2, X3, alpha)
+
+
+def mass_coefficient_box_fn(tabs, geometry, alpha):
+    def box(S3, S2, S1):
+        X3, X2, X1 = np.meshgrid(tabs[2].xq[S3], tabs[1].xq[S2], tabs[0].xq[S1], indexing="ij")
+        return mass_coefficient_points(geometry, X1, X2, X3, alpha)
+    return box
+
+
 # ---------------------------------------------------------------------------
 # Load vector (reading R8) and the manufactured solutions of Section 4
 # ---------------------------------------------------------------------------
@@ -682,6 +783,13 @@ def exact_forcing_ring(x1, x2, x3):
     gradS_dot_gradq = (2 * rho - 5) * 2 * (x1 * k * c1 * s2 * s3 + x2 * k * s1 * c2 * s3)
     lapq = 2 * 4 * rho + (2 * rho - 5) * 4
     return -(q * lapS + 2 * gradS_dot_gradq + S * lapq)
+
+
+def exact_forcing_ring_reaction(alpha):
+    """f = -Laplace u + alpha u for Eq. (exact-solution) (K = I, constant alpha)."""
+    def f(x1, x2, x3):
+        return exact_forcing_ring(x1, x2, x3) + alpha * exact_solution_ring(x1, x2, x3)
+    return f
 
 
 def _gauss_tables(tabs, k):
@@ -762,9 +870,11 @@ class FD:
     U: list
     K: list
     M: list
+    shift: float = 0.0
 
 
-def fd_setup(tabs) -> FD:
+def fd_setup(tabs, shift: float = 0.0) -> FD:
+    """FD factors (reading R6); shift sigma adds sigma M3(x)M2(x)M1 to P (reading R15)."""
     lam, U, K, M = [], [], [], []
     for t in tabs:
         Kl = galerkin_1d(t.knots, t.p, 1, 1)
@@ -774,12 +884,12 @@ def fd_setup(tabs) -> FD:
         U.append(V)
         K.append(Kl)
         M.append(Ml)
-    return FD(lam, U, K, M)
+    return FD(lam, U, K, M, float(shift))
 
 
 def fd_diag(fd):
-    """lambda1_i + lambda2_j + lambda3_k as a tensor [k][j][i]."""
-    return fd.lam[2][:, None, None] + fd.lam[1][None, :, None] + fd.lam[0][None, None, :]
+    """lambda1_i + lambda2_j + lambda3_k (+ sigma) as a tensor [k][j][i]."""
+    return fd.lam[2][:, None, None] + fd.lam[1][None, :, None] + fd.lam[0][None, None, :] + fd.shift
 
 
 def fd_apply(fd, R):
@@ -796,9 +906,12 @@ def fd_apply_explicit(fd, r):
 
 
 def fd_matrix(fd) -> sp.csr_matrix:
-    """P = M3(x)M2(x)K1 + M3(x)K2(x)M1 + K3(x)M2(x)M1."""
+    """P = M3(x)M2(x)K1 + M3(x)K2(x)M1 + K3(x)M2(x)M1 (+ sigma M3(x)M2(x)M1)."""
     K, M = fd.K, fd.M
-    return (kron3(M[2], M[1], K[0]) + kron3(M[2], K[1], M[0]) + kron3(K[2], M[1], M[0])).tocsr()
+    P = kron3(M[2], M[1], K[0]) + kron3(M[2], K[1], M[0]) + kron3(K[2], M[1], M[0])
+    if fd.shift:
+        P = P + fd.shift * kron3(M[2], M[1], M[0])
+    return P.tocsr()
 
 
 # ---------------------------------------------------------------------------
@@ -866,6 +979,7 @@ class Patch:
     tabs: list
     C6: np.ndarray          # (6, nq3, nq2, nq1)
     fd: FD
+    cmass: np.ndarray = None  # c = alpha det J at the WQ points (nq3, nq2, nq1), or None
 
     @property
     def n(self):
@@ -880,10 +994,16 @@ class Patch:
         return full_coeff(self.C6)
 
     def apply(self, V):
-        return apply_alg2(self.tabs, self.Cfull, V)
+        out = apply_alg2(self.tabs, self.Cfull, V)
+        if self.cmass is not None:
+            out = out + apply_mass_alg1(self.tabs, self.cmass, V)
+        return out
 
     def apply_T(self, Y):
-        return apply_T_alg2(self.tabs, self.Cfull, Y)
+        out = apply_T_alg2(self.tabs, self.Cfull, Y)
+        if self.cmass is not None:
+            out = out + apply_mass_T(self.tabs, self.cmass, Y)
+        return out
 
     def precond(self, R):
         return fd_apply(self.fd, R)

@@ -326,6 +326,104 @@ def test_gradient_euler_identity_and_central_differences():
         assert abs(fd - an) <= 1e-5 * abs(an)
 
 
+# ---------------------------------------------------------------- reaction (mass) term
+def test_constant_mass_equals_galerkin_mass():
+    """Eq. (Mwq) with constant c: each direction's W^(00) B^(0) reproduces the 1D
+    mass integrals (exactness), so M~ = c (G3 (x) G2 (x) G1) with G_l = int b_i b_j
+    (computed here with scipy's B-splines and an independent Gauss rule)."""
+    tabs = _mixed_tables()
+    nq = int(np.prod([t.nq for t in tabs]))
+    M = O.mass_wq(tabs, np.full(nq, 2.5)).toarray()
+    G = [_independent_galerkin(t.knots, t.p, 0, 0) for t in tabs]
+    Mg = 2.5 * np.kron(G[2], np.kron(G[1], G[0]))
+    assert np.abs(M - Mg).max() <= 1e-13 * np.abs(Mg).max()
+    assert np.abs(M - M.T).max() <= 1e-13 * np.abs(M).max()
+
+
+def test_mass_assembly_algorithm1_rows_and_transpose():
+    """Kronecker assembly of M~ == Eq. (Mwq) entry by entry (variable c on the
+    ring); Algorithm 1, the transpose and the row-sampled form == the matrix."""
+    tabs = _mixed_tables()
+    c = O.mass_coefficient_grid(tabs, "ring", 3.0)
+    M = O.mass_wq(tabs, c)
+    Mb = O.mass_wq_entries(tabs, c)
+    assert np.abs(M.toarray() - Mb).max() <= 1e-13 * np.abs(Mb).max()
+    assert np.abs(M.toarray() - M.toarray().T).max() > 1e-6 * np.abs(Mb).max()  # non-constant c: not symmetric
+    shape = (tabs[2].n, tabs[1].n, tabs[0].n)
+    V = inputs.uniform_vector(shape, 31)
+    ref = (M @ V.ravel()).reshape(shape)
+    assert np.abs(O.apply_mass_alg1(tabs, c, V) - ref).max() <= 1e-13 * np.abs(ref).max()
+    refT = (M.T @ V.ravel()).reshape(shape)
+    assert np.abs(O.apply_mass_T(tabs, c, V) - refT).max() <= 1e-13 * np.abs(refT).max()
+    rows = [(0, 0, 0), (shape[0] - 1, shape[1] - 1, shape[2] - 1), (1, 2, 1)]
+    got = O.mass_rows(tabs, O.mass_coefficient_box_fn(tabs, "ring", 3.0), V, rows)
+    assert np.abs(got - np.array([ref[r] for r in rows])).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_ring_mass_coefficient_integrates_to_the_volume():
+    """int c / alpha over the parameter cube = volume of the quarter ring shell,
+    pi/4 (2^2 - 1^2) = 3 pi/4 (c = alpha det J, Eq. (M))."""
+    xg, wg = O.gauss_rule(O.uniform_knots(2, 3), 3)
+    X3, X2, X1 = np.meshgrid(xg, xg, xg, indexing="ij")
+    c = O.mass_coefficient_points("ring", X1, X2, X3, 2.0)
+    vol = np.einsum("c,b,a,cba->", wg, wg, wg, c) / 2.0
+    assert abs(vol - 0.75 * np.pi) <= 1e-14
+
+
+def test_cube_reaction_operator_is_shifted_fd_matrix():
+    """Unit cube, K = I, constant alpha: K~ + M~ = P + alpha M3(x)M2(x)M1, the
+    FD with shift alpha is its exact inverse, and the preconditioned solve
+    converges in one iteration (reading R15)."""
+    tabs = O.uniform_tables(2, (5, 4, 6))
+    alpha = 7.0
+    C6 = O.coefficient_grid(tabs, "cube")
+    c = O.mass_coefficient_grid(tabs, "cube", alpha)
+    A = O.stiffness_wq(tabs, O.full_coeff(C6)) + O.mass_wq(tabs, c)
+    fd = O.fd_setup(tabs, shift=alpha)
+    P = O.fd_matrix(fd)
+    assert abs(A - P).max() <= 1e-13 * abs(P).max()
+    shape = (tabs[2].n, tabs[1].n, tabs[0].n)
+    R = inputs.uniform_vector(shape, 41)
+    Z = O.fd_apply(fd, R)
+    assert np.linalg.norm(P @ Z.ravel() - R.ravel()) <= 1e-12 * np.linalg.norm(R)
+    patch = O.Patch(tabs, C6, fd, c)
+    U, info = patch.solve(O.load_vector(tabs, "cube", O.forcing_sines), 1e-10)
+    assert info.converged and info.iterations == 1
+
+
+def test_reaction_gradient_euler_identity_and_central_differences():
+    """K~(C) + M~(c) is linear in (C, c) jointly: sum C dJ/dC + sum c dJ/dc =
+    -lambda^T f; dJ/dc matches central differences."""
+    tabs = O.uniform_tables(2, (4, 3, 5))
+    C6 = O.coefficient_grid(tabs, "ring", inputs.fourier_modes(5), 0.3)
+    c = O.mass_coefficient_grid(tabs, "ring", 4.0)
+    F = O.load_vector(tabs, "ring", O.forcing_sines)
+    shape = F.shape
+
+    def solve(cc, rhs, transpose=False):
+        A = (O.stiffness_wq(tabs, O.full_coeff(C6)) + O.mass_wq(tabs, cc)).tocsc()
+        return spla.spsolve(A.T.tocsc() if transpose else A, rhs.ravel()).reshape(shape)
+
+    u_t = solve(0.0 * c, F)
+    u = solve(c, F)
+    lam = solve(c, u - u_t, transpose=True)
+    gC, gc = O.grad_coeff(tabs, lam, u), O.grad_mass_coeff(tabs, lam, u)
+    lf = np.dot(lam.ravel(), F.ravel())
+    assert abs(np.sum(C6 * gC) + np.sum(c * gc) + lf) <= 1e-10 * abs(lf)
+
+    def J(cc):
+        d = solve(cc, F) - u_t
+        return 0.5 * np.dot(d.ravel(), d.ravel())
+
+    gr = inputs.rng(9)
+    h = 1e-6
+    for _ in range(3):
+        d = gr.uniform(-1, 1, size=c.shape) * c
+        fdv = (J(c + h * d) - J(c - h * d)) / (2 * h)
+        an = np.sum(gc * d)
+        assert abs(fdv - an) <= 1e-5 * abs(an)
+
+
 # ---------------------------------------------------------------- Table 1
 def _table1():
     rows = {}
