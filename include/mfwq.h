@@ -126,6 +126,27 @@ int mfwq_eval_coeff(mfwq_handle h, int geometry, const double* modes_host, int n
  * caller's buffer may be reused afterwards.  Asynchronous. */
 int mfwq_set_coeff(mfwq_handle h, const double* C_dev);
 
+/* ---- reaction (mass) term: alpha u in Eq. (poisson) ----------------------
+ * The discrete operator becomes K~ + M~ with the WQ mass matrix of Eq. (Mwq),
+ * M~_ij = sum_q w_iq c(x_q) b_j(x_q), c = alpha det J (Eq. (M)), applied
+ * matrix-free as M~ = W D B (Algorithm 1, Section 3.1) inside every apply,
+ * transposed apply and solve of the handle (FP64 and, on a mixed handle,
+ * FP32).  The weights are the (0,0) family of the stiffness weights in every
+ * direction. */
+
+/* c_dev[nq3][nq2][nq1] = alpha |det J| at the WQ points for the given
+ * geometry and a constant alpha.  Asynchronous. */
+int mfwq_eval_mass_coeff(mfwq_handle h, int geometry, double alpha, double* c_dev);
+
+/* Copies c_dev[Nq] (c at the WQ points, any real values) into the handle and
+ * turns the reaction term on; c_dev = NULL turns it off and frees the copy.
+ * fd_shift (finite, >= 0) is added to every eigenvalue sum of the FD
+ * preconditioner, which then inverts P + fd_shift M3 (x) M2 (x) M1 exactly
+ * (same eigenvectors); a constant alpha on a cube-like patch suggests
+ * fd_shift = alpha.  The paper gives no preconditioner for alpha > 0.
+ * MFWQ_EINVAL on a negative or non-finite shift.  Asynchronous. */
+int mfwq_set_mass_coeff(mfwq_handle h, const double* c_dev, double fd_shift);
+
 /* Load vector f_i = int |det J| b_i (f o F) dxi (Eq. (linearsystem)) by
  * tensor Gauss quadrature with p+1 points per span.  Asynchronous. */
 int mfwq_load_vector(mfwq_handle h, int geometry, int forcing, double* f_dev);
@@ -195,6 +216,11 @@ int mfwq_solve_host(mfwq_handle h, const double* f_host, double* u_host,
  * orderings.  gC_dev: [6][nq3][nq2][nq1].  The quadrature-point gradients
  * B^(b) u are recomputed, not stored.  Asynchronous. */
 int mfwq_grad_coeff(mfwq_handle h, const double* lambda_dev, const double* u_dev, double* gC_dev);
+
+/* Gradient of J with respect to the reaction coefficient c at the WQ points:
+ * dJ/dc(q) = -(W^T lambda)_q (B u)_q with the mass factors of Algorithm 1.
+ * gc_dev: [nq3][nq2][nq1].  Works whether or not the term is on.  Asynchronous. */
+int mfwq_grad_mass_coeff(mfwq_handle h, const double* lambda_dev, const double* u_dev, double* gc_dev);
 
 /* Waits for the handle's stream and reports any failure seen since the last call. */
 int mfwq_sync(mfwq_handle h);
@@ -274,7 +300,8 @@ int mfwq_batch_solve(mfwq_batch b, const double* const* f_dev, double* const* u_
  * xstage, test_y, test_z (the five stages of the apply), test_zT, test_yT,
  * xstage_T, trial_yT, trial_zT (the transpose), xstage_grad, fd_dim1,
  * fd_dim23, fd_tc (FD mode products), krylov (BiCGStab vector and scalar
- * kernels), setup, fd_fold (even/odd folding of the FP64 FD). */
+ * kernels), setup, fd_fold (even/odd folding of the FP64 FD), mass (the
+ * reaction-term passes). */
 #define MFWQ_NSTAGES 24
 typedef struct {
     double ms[MFWQ_NSTAGES];           /* summed device time per stage (CUDA events) */

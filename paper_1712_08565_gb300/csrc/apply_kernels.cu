@@ -857,6 +857,108 @@ __global__ void __launch_bounds__(kThreads) k_xstage_grad(XArgs<T> a, const T* _
     }
 }
 
+// ---- reaction (mass) term, Algorithm 1 folded into the stiffness pipeline
+// M~ = W^(00) D_c B^(0) has the value family (0) in every trial direction and
+// the weight family (0,0) in every test direction.  The trial z and y stages
+// already hold Y00 = (B0_3 (x) B0_2) v, and T^(11) = W1^(11) (...) has the test
+// families (0,0) in y and z, so the mass term is one more x-direction pass per
+// line that adds W1^(00) (c (B0_1 Y00)) to T^(11) before the y and z test
+// stages.  The transposed and gradient passes mirror it on R^(11) =
+// (W3^(00)T (x) W2^(00)T) y, whose B0^T trial stages follow in y and z.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_mass_x(XArgs<T> a, const T* __restrict__ y00, const T* __restrict__ cm,
+                                                     T* __restrict__ t11, const int* skip) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sY = reinterpret_cast<T*>(smem_raw);  // [kLines][n1]
+    T* sH = sY + kLines * a.n1;              // [kLines][nq1]
+    const int line0 = blockIdx.x * kLines;
+    const int nl = min(kLines, a.nlines - line0);
+    const int n1 = a.n1, nq1 = a.nq1;
+    for (int e = threadIdx.x; e < nl * n1; e += blockDim.x) sY[e] = y00[(size_t)line0 * n1 + e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < nl * nq1; e += blockDim.x) {
+        const int l = e / nq1, q = e - l * nq1;
+        const int s = a.B.start[q], L = a.B.len[q];
+        const T* Y = sY + l * n1 + s;
+        T g = 0;
+        for (int t = 0; t < L; ++t) g = fmaT(a.B.lane(0, q, t), Y[t], g);
+        sH[e] = cm[(size_t)line0 * nq1 + e] * g;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nl * n1; e += blockDim.x) {
+        const int l = e / n1, i = e - l * n1;
+        const int s = a.W.start[i], L = a.W.len[i];
+        const T* H = sH + l * nq1 + s;
+        T acc = 0;
+        for (int t = 0; t < L; ++t) acc = fmaT(a.W.lane(0, i, t), H[t], acc);
+        t11[(size_t)line0 * n1 + e] += acc;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_mass_xT(XArgs<T> a, const T* __restrict__ r11, const T* __restrict__ cm,
+                                                      T* __restrict__ x1, const int* skip) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sR = reinterpret_cast<T*>(smem_raw);  // [kLines][n1]
+    T* sE = sR + kLines * a.n1;              // [kLines][nq1]
+    const int line0 = blockIdx.x * kLines;
+    const int nl = min(kLines, a.nlines - line0);
+    const int n1 = a.n1, nq1 = a.nq1;
+    for (int e = threadIdx.x; e < nl * n1; e += blockDim.x) sR[e] = r11[(size_t)line0 * n1 + e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < nl * nq1; e += blockDim.x) {
+        const int l = e / nq1, q = e - l * nq1;
+        const int s = a.WT.start[q], L = a.WT.len[q];
+        const T* R = sR + l * n1 + s;
+        T acc = 0;
+        for (int t = 0; t < L; ++t) acc = fmaT(a.WT.lane(0, q, t), R[t], acc);
+        sE[e] = cm[(size_t)line0 * nq1 + e] * acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nl * n1; e += blockDim.x) {
+        const int l = e / n1, j = e - l * n1;
+        const int s = a.BT.start[j], L = a.BT.len[j];
+        const T* E = sE + l * nq1 + s;
+        T acc = 0;
+        for (int t = 0; t < L; ++t) acc = fmaT(a.BT.lane(0, j, t), E[t], acc);
+        x1[(size_t)line0 * n1 + e] += acc;
+    }
+}
+
+// dJ/dc(q) = -(W^(00)T lambda)_q (B^(0) u)_q from Y00 (of u) and R^(11) (of lambda)
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_mass_grad(XArgs<T> a, const T* __restrict__ y00,
+                                                        const T* __restrict__ r11, T* __restrict__ gc) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sY = reinterpret_cast<T*>(smem_raw);  // [kLines][n1]
+    T* sR = sY + kLines * a.n1;              // [kLines][n1]
+    const int line0 = blockIdx.x * kLines;
+    const int nl = min(kLines, a.nlines - line0);
+    const int n1 = a.n1, nq1 = a.nq1;
+    for (int e = threadIdx.x; e < nl * n1; e += blockDim.x) {
+        sY[e] = y00[(size_t)line0 * n1 + e];
+        sR[e] = r11[(size_t)line0 * n1 + e];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nl * nq1; e += blockDim.x) {
+        const int l = e / nq1, q = e - l * nq1;
+        T g = 0, S = 0;
+        {
+            const int s = a.B.start[q], L = a.B.len[q];
+            const T* Y = sY + l * n1 + s;
+            for (int t = 0; t < L; ++t) g = fmaT(a.B.lane(0, q, t), Y[t], g);
+        }
+        {
+            const int s = a.WT.start[q], L = a.WT.len[q];
+            const T* R = sR + l * n1 + s;
+            for (int t = 0; t < L; ++t) S = fmaT(a.WT.lane(0, q, t), R[t], S);
+        }
+        gc[(size_t)line0 * nq1 + e] = -S * g;
+    }
+}
+
 template <typename T>
 XArgs<T> xargs(const DirD<T>& d1, int nlines, size_t cs, const T* C) {
     XArgs<T> a;
@@ -944,6 +1046,23 @@ __global__ void k_eval_coeff(int geom, Modes md, const double* __restrict__ xq1,
             const int i = pr[s][0], j = pr[s][1];
             C[s * Nq + p] = f * (A[i][0] * A[j][0] + A[i][1] * A[j][1] + A[i][2] * A[j][2]);
         }
+    }
+}
+
+// c = alpha |det J| at every WQ point (the reaction coefficient of Eq. (M))
+__global__ void k_eval_mass(int geom, double alpha, const double* __restrict__ xq1, const double* __restrict__ xq2,
+                            const double* __restrict__ xq3, int nq1, int nq2, int nq3, double* __restrict__ c) {
+    const size_t Nq = (size_t)nq1 * nq2 * nq3;
+    for (size_t p = (size_t)blockIdx.x * blockDim.x + threadIdx.x; p < Nq; p += (size_t)gridDim.x * blockDim.x) {
+        const int q1 = (int)(p % nq1);
+        const int q2 = (int)((p / nq1) % nq2);
+        const int q3 = (int)(p / ((size_t)nq1 * nq2));
+        double X[3], J[3][3];
+        geometry_at(geom, xq1[q1], xq2[q2], xq3[q3], X, J);
+        const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                           J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+        c[p] = alpha * fabs(det);
     }
 }
 
@@ -1059,6 +1178,14 @@ int run_apply(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
         launch_end(S_XSTAGE, c.stream);
         if (cudaGetLastError() != cudaSuccess) return MFWQ_ECUDA;
     }
+    if (c.cm) {  // reaction term into T^(11)
+        XArgs<T> a = xargs(d1, q3 * q2, c.cs, c.C);
+        launch_begin(S_MASS, c.stream);
+        k_mass_x<T><<<(q3 * q2 + kLines - 1) / kLines, kThreads, mass_smem_bytes((int)sizeof(T), n1, q1), c.stream>>>(
+            a, Y[0], c.cm, Tt[0], skip);
+        launch_end(S_MASS, c.stream);
+        if (cudaGetLastError() != cudaSuccess) return MFWQ_ECUDA;
+    }
     // test y: 9 -> 4 (U reuses Q)
     OpTestY<T> oty;
     oty.band = d2.W;
@@ -1120,6 +1247,13 @@ int run_apply_T(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
         k_xstage_applyT<T><<<grid, kThreads, sm, c.stream>>>(a, rp, P, P + SP, P + 2 * SP, skip);
         launch_end(S_XSTAGE_T, c.stream);
         if (cudaGetLastError() != cudaSuccess) return MFWQ_ECUDA;
+        if (c.cm) {  // reaction term: X1 += B1^(0)T (c W1^(00)T R^(11))
+            launch_begin(S_MASS, c.stream);
+            k_mass_xT<T><<<grid, kThreads, mass_smem_bytes((int)sizeof(T), n1, q1), c.stream>>>(a, P + 3 * SP, c.cm,
+                                                                                              P, skip);
+            launch_end(S_MASS, c.stream);
+            if (cudaGetLastError() != cudaSuccess) return MFWQ_ECUDA;
+        }
     }
     OpTrialYT<T> o3{d2.BT, P, P + SP, P + 2 * SP, Q, Q + SQ};
     if (launch_slow(S_TRIAL_YT, o3, q3, q2, n2, n1, skip, c.stream, c.srows) != cudaSuccess) return MFWQ_ECUDA;
@@ -1159,6 +1293,33 @@ int run_grad(const OpCtx<T>& c, const T* lam, const T* u, T* g6) {
     (void)n3;
     return MFWQ_OK;
 }
+
+template <typename T>
+int run_grad_mass(const OpCtx<T>& c, const T* lam, const T* u, T* gc) {
+    const DirD<T>& d1 = c.d[0];
+    const DirD<T>& d2 = c.d[1];
+    const DirD<T>& d3 = c.d[2];
+    const int n1 = d1.n, n2 = d2.n, n3 = d3.n, q1 = d1.nq, q2 = d2.nq, q3 = d3.nq;
+    size_t SP, SQ;
+    scratch_strides(c, &SP, &SQ);
+    T* P = c.scratch;
+    T* Q = c.scratch + 12 * SP;
+    OpTrialZ<T> oz{d3.B, u, Q, Q + SQ};
+    if (launch_slow(S_TRIAL_Z, oz, 1, n3, q3, n2 * n1, nullptr, c.stream, c.srows) != cudaSuccess) return MFWQ_ECUDA;
+    OpTrialY<T> oy{d2.B, Q, Q + SQ, P, P + SP, P + 2 * SP};
+    if (launch_slow(S_TRIAL_Y, oy, q3, n2, q2, n1, nullptr, c.stream, c.srows) != cudaSuccess) return MFWQ_ECUDA;
+    int st = run_test_T_partials(c, lam, nullptr);
+    if (st != MFWQ_OK) return st;
+    XArgs<T> a = xargs(d1, q3 * q2, c.cs, c.C);
+    launch_begin(S_MASS, c.stream);
+    k_mass_grad<T><<<(q3 * q2 + kLines - 1) / kLines, kThreads, sizeof(T) * 2 * kLines * (size_t)n1, c.stream>>>(
+        a, P, P + 3 * SP, gc);
+    launch_end(S_MASS, c.stream);
+    (void)q1;
+    return cudaGetLastError() == cudaSuccess ? MFWQ_OK : MFWQ_ECUDA;
+}
+
+int mass_smem_bytes(int elem_size, int n1, int nq1) { return (int)((size_t)kLines * (n1 + nq1) * elem_size); }
 
 size_t apply_scratch_elems(const int n[3], const int nq[3]) {
     size_t SP, SQ;
@@ -1240,6 +1401,11 @@ int configure_xstage_smem(int bytes) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_applyT<double>, A, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_grad<double>, A, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_applyT<float>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mass_x<double>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mass_x<float>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mass_xT<double>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mass_xT<float>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mass_grad<double>, A, bytes);
     if (e == cudaSuccess) configured = bytes;
     return e == cudaSuccess ? MFWQ_OK : MFWQ_ECUDA;
 }
@@ -1256,6 +1422,16 @@ int run_eval_coeff(const int nq[3], const double* const xq[3], int geom, const d
     if (blocks > 65535u * 8u) blocks = 65535u * 8u;
     launch_begin(S_SETUP, s);
     k_eval_coeff<<<blocks, 256, 0, s>>>(geom, md, xq[0], xq[1], xq[2], nq[0], nq[1], nq[2], C);
+    launch_end(S_SETUP, s);
+    return cudaGetLastError() == cudaSuccess ? MFWQ_OK : MFWQ_ECUDA;
+}
+
+int run_eval_mass(const int nq[3], const double* const xq[3], int geom, double alpha, double* c, cudaStream_t s) {
+    const size_t Nq = (size_t)nq[0] * nq[1] * nq[2];
+    unsigned blocks = (unsigned)((Nq + 255) / 256);
+    if (blocks > 65535u * 8u) blocks = 65535u * 8u;
+    launch_begin(S_SETUP, s);
+    k_eval_mass<<<blocks, 256, 0, s>>>(geom, alpha, xq[0], xq[1], xq[2], nq[0], nq[1], nq[2], c);
     launch_end(S_SETUP, s);
     return cudaGetLastError() == cudaSuccess ? MFWQ_OK : MFWQ_ECUDA;
 }
@@ -1280,5 +1456,6 @@ template int run_apply<double>(const OpCtx<double>&, const double*, double*, con
 template int run_apply<float>(const OpCtx<float>&, const float*, float*, const int*);
 template int run_apply_T<double>(const OpCtx<double>&, const double*, double*, const int*);
 template int run_grad<double>(const OpCtx<double>&, const double*, const double*, double*);
+template int run_grad_mass<double>(const OpCtx<double>&, const double*, const double*, double*);
 
 }  // namespace mfwq

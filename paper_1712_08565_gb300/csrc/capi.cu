@@ -167,6 +167,9 @@ struct mfwq_handle_s {
     DirD<float> d32[3];
     double* C64 = nullptr;
     float* C32 = nullptr;
+    double* Cm64 = nullptr;  // reaction coefficient (null: no reaction term)
+    float* Cm32 = nullptr;
+    double fd_shift = 0.0;
     void* scratch = nullptr;
     double* fd_tmp64 = nullptr;
     float* fd_tmp32 = nullptr;
@@ -202,6 +205,7 @@ OpCtx<double> ctx64(mfwq_handle h) {
     c.xmode = h->xmode;
     c.srows = h->srows;
     c.xcarve = h->xcarve;
+    c.cm = h->Cm64;
     return c;
 }
 
@@ -218,6 +222,7 @@ OpCtx<float> ctx32(mfwq_handle h) {
     c.xmode = h->xmode32;
     c.srows = h->srows32;
     c.xcarve = h->xcarve32;
+    c.cm = h->Cm32;
     return c;
 }
 
@@ -226,6 +231,8 @@ void free_handle(mfwq_handle h) {
     cudaFree(h->d_tables);
     cudaFree(h->C64);
     cudaFree(h->C32);
+    cudaFree(h->Cm64);
+    cudaFree(h->Cm32);
     cudaFree(h->scratch);
     cudaFree(h->fd_tmp64);
     cudaFree(h->fd_tmp32);
@@ -557,9 +564,9 @@ int mfwq_eval_coeff(mfwq_handle h, int geometry, const double* modes_host, int n
 }
 
 namespace {
-// y[s][cs] = x[s][n] for s < 6 (coefficient fields into the padded FP32 copy)
-__global__ void k_fields_to_f32(const double* __restrict__ x, size_t n, float* __restrict__ y, size_t cs) {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < 6 * n; i += (size_t)gridDim.x * blockDim.x) {
+// y[s][cs] = x[s][n] for s < nf (coefficient fields into a padded FP32 copy)
+__global__ void k_fields_to_f32(const double* __restrict__ x, size_t n, float* __restrict__ y, size_t cs, int nf) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nf * n; i += (size_t)gridDim.x * blockDim.x) {
         const size_t s = i / n, k = i - s * n;
         y[s * cs + k] = (float)x[i];
     }
@@ -573,11 +580,76 @@ int mfwq_set_coeff(mfwq_handle h, const double* C_dev) {
                          cudaMemcpyDeviceToDevice, h->stream));
     if (h->mixed) {
         launch_begin(S_SETUP, h->stream);
-        k_fields_to_f32<<<1024, 256, 0, h->stream>>>(C_dev, h->Nq, h->C32, h->cs);
+        k_fields_to_f32<<<1024, 256, 0, h->stream>>>(C_dev, h->Nq, h->C32, h->cs, 6);
         launch_end(S_SETUP, h->stream);
         CU(cudaGetLastError());
     }
     return MFWQ_OK;
+}
+
+int mfwq_eval_mass_coeff(mfwq_handle h, int geometry, double alpha, double* c_dev) {
+    ProfScope _ps(h ? &h->prof : nullptr);
+    if (!h || !c_dev || !std::isfinite(alpha)) return fail(MFWQ_EINVAL, "bad argument");
+    if (geometry != MFWQ_GEOM_CUBE && geometry != MFWQ_GEOM_RING) return fail(MFWQ_EINVAL, "unknown geometry");
+    const double* xq[3] = {h->d64[0].xq, h->d64[1].xq, h->d64[2].xq};
+    return run_eval_mass(h->nq, xq, geometry, alpha, c_dev, h->stream);
+}
+
+namespace {
+// lambda_3 + shift into the device eigenvalue tables of direction 3 (all FD forms)
+int upload_fd_shift(mfwq_handle h, double shift) {
+    const Dir1D& d = h->dir[2];
+    std::vector<double> l64(d.lam.size());
+    std::vector<float> l32(d.lam.size());
+    for (size_t k = 0; k < d.lam.size(); ++k) {
+        l64[k] = d.lam[k] + shift;
+        l32[k] = (float)l64[k];
+    }
+    CU(cudaMemcpy(const_cast<double*>(h->d64[2].lam), l64.data(), sizeof(double) * l64.size(), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(const_cast<float*>(h->d32[2].lam), l32.data(), sizeof(float) * l32.size(), cudaMemcpyHostToDevice));
+    if (d.sym && h->d64[2].lam_split) {
+        std::vector<double> ls(d.lam_split.size());
+        for (size_t k = 0; k < ls.size(); ++k) ls[k] = d.lam_split[k] + shift;
+        CU(cudaMemcpy(const_cast<double*>(h->d64[2].lam_split), ls.data(), sizeof(double) * ls.size(),
+                      cudaMemcpyHostToDevice));
+    }
+    return MFWQ_OK;
+}
+}  // namespace
+
+int mfwq_set_mass_coeff(mfwq_handle h, const double* c_dev, double fd_shift) {
+    ProfScope _ps(h ? &h->prof : nullptr);
+    if (!h) return fail(MFWQ_EINVAL, "NULL handle");
+    if (!std::isfinite(fd_shift) || fd_shift < 0.0) return fail(MFWQ_EINVAL, "fd_shift must be finite and >= 0");
+    if (!c_dev) {
+        CU(cudaStreamSynchronize(h->stream));
+        cudaFree(h->Cm64);
+        cudaFree(h->Cm32);
+        h->Cm64 = nullptr;
+        h->Cm32 = nullptr;
+    } else {
+        if (!h->Cm64) ST(dmalloc((void**)&h->Cm64, sizeof(double) * h->Nq));
+        if (h->mixed && !h->Cm32) ST(dmalloc((void**)&h->Cm32, sizeof(float) * h->Nq));
+        CU(cudaMemcpyAsync(h->Cm64, c_dev, sizeof(double) * h->Nq, cudaMemcpyDeviceToDevice, h->stream));
+        if (h->mixed) {
+            launch_begin(S_SETUP, h->stream);
+            k_fields_to_f32<<<1024, 256, 0, h->stream>>>(c_dev, h->Nq, h->Cm32, h->Nq, 1);
+            launch_end(S_SETUP, h->stream);
+            CU(cudaGetLastError());
+        }
+    }
+    if (fd_shift != h->fd_shift) {
+        CU(cudaStreamSynchronize(h->stream));  // no FD of this handle may be reading the tables
+        ST(upload_fd_shift(h, fd_shift));
+        h->fd_shift = fd_shift;
+    }
+    return MFWQ_OK;
+}
+
+int mfwq_grad_mass_coeff(mfwq_handle h, const double* lambda_dev, const double* u_dev, double* gc_dev) {
+    ProfScope _ps(h ? &h->prof : nullptr);
+    if (!h || !lambda_dev || !u_dev || !gc_dev) return fail(MFWQ_EINVAL, "bad argument");
+    return run_grad_mass<double>(ctx64(h), lambda_dev, u_dev, gc_dev);
 }
 
 int mfwq_load_vector(mfwq_handle h, int geometry, int forcing, double* f_dev) {
@@ -661,7 +733,7 @@ int mfwq_grad_coeff(mfwq_handle h, const double* lambda_dev, const double* u_dev
 
 static const char* kStageNames[S_NTAGS] = {
     "trial_z", "trial_y", "xstage", "test_y", "test_z", "test_zT", "test_yT", "xstage_T", "trial_yT", "trial_zT",
-    "xstage_grad", "fd_dim1", "fd_dim23", "fd_tc", "krylov", "setup", "fd_fold"};
+    "xstage_grad", "fd_dim1", "fd_dim23", "fd_tc", "krylov", "setup", "fd_fold", "mass"};
 
 const char* mfwq_stage_name(int stage) { return stage >= 0 && stage < S_NTAGS ? kStageNames[stage] : ""; }
 
@@ -756,6 +828,7 @@ int tune_xstage(mfwq_handle h, bool f32, int* err) {
     c.Nq = h->Nq;
     c.cs = h->cs;
     c.err = h->derr;
+    c.cm = f32 ? (const T*)h->Cm32 : (const T*)h->Cm64;
     c.scratch = static_cast<T*>(h->scratch);
     c.stream = h->stream;
     // one untimed apply, then three timed ones

@@ -23,6 +23,7 @@ struct OpCtx {
     int xcarve = 0;    // 1: forward x stage with the reduced shared-memory carveout (larger L1)
     int srows = 1;     // output rows per thread of the slow-dimension stages: 1, 2 or 4
     int* err = nullptr;  // device error word: set when a bounded wait times out
+    const T* cm = nullptr;  // reaction coefficient c = alpha det J at the WQ points [Nq], or none
 };
 
 constexpr int kXstageSmemMax = 227 * 1024;
@@ -35,6 +36,10 @@ template <typename T>
 int run_apply_T(const OpCtx<T>& c, const T* x, T* y, const int* skip);
 template <typename T>
 int run_grad(const OpCtx<T>& c, const T* lam, const T* u, T* g6);
+// gc = dJ/dc of the reaction coefficient (Algorithm 1's D)
+template <typename T>
+int run_grad_mass(const OpCtx<T>& c, const T* lam, const T* u, T* gc);
+int mass_smem_bytes(int elem_size, int n1, int nq1);
 
 size_t apply_scratch_elems(const int n[3], const int nq[3]);
 size_t rhs_scratch_elems(const int n[3], const int ng[3]);
@@ -46,6 +51,7 @@ int configure_xstage_smem(int bytes);
 int run_eval_coeff(const int nq[3], const double* const xq[3], int geom, const double* modes, int nmodes, double kscale,
                    double* C, cudaStream_t s);
 int run_load_vector(const DirD<double> d[3], int geom, int forcing, double* scratch, double* f, cudaStream_t s);
+int run_eval_mass(const int nq[3], const double* const xq[3], int geom, double alpha, double* c, cudaStream_t s);
 
 // FD preconditioner, FP64: z = P^-1 r; tmp holds N doubles.  skip as above.
 int run_fd64(const DirD<double> d[3], const double* r, double* z, double* tmp, const int* skip, cudaStream_t s);

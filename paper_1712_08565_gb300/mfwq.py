@@ -82,6 +82,9 @@ _SIGS = [
     ("mfwq_eval_coeff", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_double,
                                        ctypes.c_void_p]),
     ("mfwq_set_coeff", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    ("mfwq_eval_mass_coeff", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p]),
+    ("mfwq_set_mass_coeff", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
+    ("mfwq_grad_mass_coeff", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("mfwq_load_vector", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("mfwq_apply", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("mfwq_apply_T", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -267,6 +270,30 @@ class Operator:
     def set_coeff(self, C):
         import torch
         _check(lib().mfwq_set_coeff(self._h, _ptr(C, torch.float64, 6 * self.Nq, self.device)))
+
+    def eval_mass_coeff(self, geometry: str = "ring", alpha: float = 1.0, out=None):
+        """c = alpha |det J| at the WQ points, shape (nq3, nq2, nq1) (mfwq_eval_mass_coeff)."""
+        import torch
+        out = out if out is not None else self._new(self.qshape, torch.float64)
+        _check(lib().mfwq_eval_mass_coeff(self._h, GEOMETRY[geometry], float(alpha),
+                                          _ptr(out, torch.float64, self.Nq, self.device)))
+        return out
+
+    def set_mass_coeff(self, c=None, fd_shift: float = 0.0):
+        """Turn the reaction term on with c at the WQ points (None: off) and set
+        the FD shift (mfwq_set_mass_coeff)."""
+        import torch
+        ptr = None if c is None else _ptr(c, torch.float64, self.Nq, self.device)
+        _check(lib().mfwq_set_mass_coeff(self._h, ptr, float(fd_shift)))
+
+    def grad_mass_coeff(self, lam, u, out=None):
+        """dJ/dc at the WQ points (mfwq_grad_mass_coeff)."""
+        import torch
+        out = out if out is not None else self._new(self.qshape, torch.float64)
+        _check(lib().mfwq_grad_mass_coeff(self._h, _ptr(lam, torch.float64, self.N, self.device),
+                                          _ptr(u, torch.float64, self.N, self.device),
+                                          _ptr(out, torch.float64, self.Nq, self.device)))
+        return out
 
     def load_vector(self, geometry: str = "ring", forcing: str = "sines", out=None):
         import torch
