@@ -36,6 +36,7 @@ Readings of passages the paper leaves open (each is listed in the design doc):
 * R7  BiCGStab: right preconditioning, x0 given (default 0), r^_0 = r_0,
       convergence tested on the half step s and on the full step r.
 * R8  Load vector: tensor Gauss with p_l+1 points per span in direction l, c = |det J|.
+      The relative H1 error of Section 4 uses p_l+2 points per span in direction l.
 * R14 Mass weights: the 1D family W^(00) of the stiffness (exactness for
       int b_i b_j, Eq. (exactness1d)) in every direction, so the mass term
       uses the same weights as the (alpha != l, beta != l) stiffness factors.
@@ -840,8 +841,8 @@ def load_vector_rows(tabs, geometry, forcing, rows):
 
 def h1_error(tabs, U, geometry, exact_u, exact_grad):
     """Relative H1 error ||u - u_h||_H1 / ||u||_H1 (Section 4), tensor Gauss
-    with p+2 points per span, gradients pulled back with J^-T."""
-    gt = _gauss_tables(tabs, max(t.p for t in tabs) + 2)
+    with p_l+2 points per span in direction l, gradients pulled back with J^-T."""
+    gt = _gauss_tables(tabs, [t.p + 2 for t in tabs])
     X3, X2, X1 = np.meshgrid(gt[2][0], gt[1][0], gt[0][0], indexing="ij")
     x, det, J = _geom_at(geometry, X1, X2, X3)
     wgt = np.einsum("c,b,a->cba", gt[2][1], gt[1][1], gt[0][1]) * det
