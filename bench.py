@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extras", action="store_true", help="skip the p sweep, mixed solve and CPU baseline")
     ap.add_argument("--kernel-nel", default=None, help="with --kernel-run: elements per direction, e.g. 192,64,64")
+    ap.add_argument("--table1", default=None, metavar="NELS",
+                    help="run the k-refinement experiment of Section 4 (Table 1) for the given comma-separated "
+                         "elements per direction (e.g. 16,32,64,128,256), p = 2..10, and print its table as JSON")
+    ap.add_argument("--table1-p", default="2,3,4,5,6,7,8,9,10", help="degrees for --table1")
     ap.add_argument("--kernel-run", choices=["apply", "apply_T", "fd64", "fdtc", "fdbf16", "apply32"], default=None,
                     help="set up the workload, run one operator 3 times and exit (target for ncu captures)")
     return ap.parse_args()
@@ -586,8 +590,59 @@ def kernel_run(which, nel_override=None):
     return 0
 
 
+def table1(args):
+    """Section 4, Table 1: the ring with Eq. (exact-solution), FD-preconditioned
+    BiCGStab stopped by Eq. (stopping_criterion) with eta = 0.1.  The Galerkin
+    error on the right of the rule is estimated from a tight solve (rtol
+    1e-13, untimed); the timed part is the paper's "total computation time":
+    setup (tables, weights, FD factors, coefficient, load vector) + solve."""
+    import torch
+    from paper_1712_08565_gb300 import build
+    build.build()
+    from paper_1712_08565_gb300 import mfwq as mf
+    from paper_1712_08565_gb300 import inputs
+    dev = torch.device("cuda", 0)
+    nels = [int(v) for v in args.table1.split(",")]
+    ps = [int(v) for v in args.table1_p.split(",")]
+    rows = []
+    for nel in nels:
+        for p in ps:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            knots = [inputs.open_uniform_knots(p, nel)] * 3
+            op = mf.Operator(p, knots, device=dev)
+            C = op.eval_coeff("ring")
+            op.set_coeff(C)
+            f = op.load_vector("ring", "ring_exact")
+            op.sync()
+            t_setup = time.perf_counter() - t0
+            del C
+            u_ref, iref = op.solve(f, rtol=1e-13, maxit=5000)
+            e_ref = op.h1_error(u_ref, "ring", "ring")
+            del u_ref
+            rtol = max(0.1 * e_ref, 1e-14)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            u, info = op.solve(f, rtol=rtol, maxit=5000)
+            t_solve = time.perf_counter() - t1
+            e = op.h1_error(u, "ring", "ring")
+            rows.append({"p": p, "nel": nel, "N": op.N, "setup_s": t_setup, "solve_s": t_solve,
+                         "total_s": t_setup + t_solve, "iterations": info.iterations, "rtol": rtol,
+                         "converged": info.converged, "h1_error": e, "galerkin_h1_error": e_ref,
+                         "ref_solve_converged": iref.converged})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            op.close()
+            del u, f
+            torch.cuda.empty_cache()
+    print(json.dumps({"table1": rows, "eta": 0.1, "geometry": "ring (exact polar map)",
+                      "solution": "Eq. (exact-solution)", "device": torch.cuda.get_device_name(0)}))
+    return 0
+
+
 def main():
     args = parse()
+    if args.table1:
+        return table1(args)
     if args.kernel_run:
         return kernel_run(args.kernel_run, args.kernel_nel)
     if args.impl == "reference":

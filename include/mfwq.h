@@ -151,6 +151,20 @@ int mfwq_set_mass_coeff(mfwq_handle h, const double* c_dev, double fd_shift);
  * tensor Gauss quadrature with p+1 points per span.  Asynchronous. */
 int mfwq_load_vector(mfwq_handle h, int geometry, int forcing, double* f_dev);
 
+/* ---- error measure of Section 4 (post-processing, not the hot path) ------- */
+enum {
+    MFWQ_EXACT_SINES = 0,  /* u = sin(pi x) sin(pi y) sin(pi z): the cube with MFWQ_FORCING_SINES */
+    MFWQ_EXACT_RING = 1    /* Eq. (exact-solution) on the ring, MFWQ_FORCING_RING_EXACT */
+};
+
+/* *rel_err (host) = ||u - u_h||_H1 / ||u||_H1 for the discrete function with
+ * coefficients u_dev[n3][n2][n1] against the exact solution, by tensor Gauss
+ * quadrature with p_l + 2 points per span, physical gradients J^-T grad_xi.
+ * The Gauss-point values are formed by sum factorisation in slabs of about
+ * 0.5 GB (allocated and freed by the call).  MFWQ_ENOMEM if that fails.
+ * Synchronous. */
+int mfwq_h1_error(mfwq_handle h, int geometry, int solution, const double* u_dev, double* rel_err);
+
 /* ---- hot path ------------------------------------------------------------ */
 /* y = K~ x, FP64 (Algorithm 2, sum-factorised).  x_dev, y_dev: [n3][n2][n1].
  * Uses the handle's workspace, so calls on one handle must not overlap on the
@@ -301,7 +315,7 @@ int mfwq_batch_solve(mfwq_batch b, const double* const* f_dev, double* const* u_
  * xstage_T, trial_yT, trial_zT (the transpose), xstage_grad, fd_dim1,
  * fd_dim23, fd_tc (FD mode products), krylov (BiCGStab vector and scalar
  * kernels), setup, fd_fold (even/odd folding of the FP64 FD), mass (the
- * reaction-term passes). */
+ * reaction-term passes), h1_error (mfwq_h1_error). */
 #define MFWQ_NSTAGES 24
 typedef struct {
     double ms[MFWQ_NSTAGES];           /* summed device time per stage (CUDA events) */

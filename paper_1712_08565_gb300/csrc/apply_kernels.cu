@@ -18,6 +18,10 @@
 // direction-l family of W^(ab) is (a_l, b_l) = ([l=alpha], [l=beta]).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "kernels.h"
 #include "prof.h"
 #include "ptx_async.cuh"
@@ -1434,6 +1438,173 @@ int run_eval_mass(const int nq[3], const double* const xq[3], int geom, double a
     k_eval_mass<<<blocks, 256, 0, s>>>(geom, alpha, xq[0], xq[1], xq[2], nq[0], nq[1], nq[2], c);
     launch_end(S_SETUP, s);
     return cudaGetLastError() == cudaSuccess ? MFWQ_OK : MFWQ_ECUDA;
+}
+
+// ---- relative H1 error (Section 4, the error measure of Table 1)
+// Exact solutions: sin(pi x) sin(pi y) sin(pi z) (the cube's sines problem)
+// and Eq. (exact-solution) on the ring; value and physical gradient.
+__device__ void exact_at(int sol, const double X[3], double* u, double g[3]) {
+    if (sol == MFWQ_EXACT_RING) {
+        const double k = 5.0 * 3.141592653589793;
+        double s1, c1, s2, c2, s3, c3;
+        sincos(k * X[0], &s1, &c1);
+        sincos(k * X[1], &s2, &c2);
+        sincos(k * X[2], &s3, &c3);
+        const double rho = X[0] * X[0] + X[1] * X[1];
+        const double q = (rho - 1.0) * (rho - 4.0), dq = 2.0 * rho - 5.0;
+        const double S = s1 * s2 * s3;
+        *u = S * q;
+        g[0] = k * c1 * s2 * s3 * q + S * dq * 2.0 * X[0];
+        g[1] = k * s1 * c2 * s3 * q + S * dq * 2.0 * X[1];
+        g[2] = k * s1 * s2 * c3 * q;
+    } else {
+        const double k = 3.141592653589793;
+        double s1, c1, s2, c2, s3, c3;
+        sincos(k * X[0], &s1, &c1);
+        sincos(k * X[1], &s2, &c2);
+        sincos(k * X[2], &s3, &c3);
+        *u = s1 * s2 * s3;
+        g[0] = k * c1 * s2 * s3;
+        g[1] = k * s1 * c2 * s3;
+        g[2] = k * s1 * s2 * c3;
+    }
+}
+
+// One (g3, g2) line of error points per block: u_h and its parametric
+// gradient at the line's ne1 points from the y partials (Y00: values in y and
+// z, Y10: y-derivative, Y01: z-derivative), the exact solution at the mapped
+// points, the gradient pulled back with J^-T, weights w1 w2 w3 |det J|.
+// part[2 b], part[2 b + 1] = the block's error and norm sums.
+__global__ void __launch_bounds__(kThreads) k_h1_x(BandD<double> E1, const double* __restrict__ xe1,
+                                                   const double* __restrict__ we1, const double* __restrict__ xe2,
+                                                   const double* __restrict__ we2, const double* __restrict__ xe3,
+                                                   const double* __restrict__ we3, int n1, int ne1, int ne2, int g3a,
+                                                   const double* __restrict__ y00, const double* __restrict__ y10,
+                                                   const double* __restrict__ y01, int geom, int sol,
+                                                   double* __restrict__ part) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sY = reinterpret_cast<double*>(smem_raw);  // [3][n1]
+    __shared__ double red[2][kThreads / 32];
+    const int line = blockIdx.x;
+    const int g3 = g3a + line / ne2, g2 = line % ne2;
+    const size_t base = (size_t)line * n1;
+    for (int j = threadIdx.x; j < n1; j += blockDim.x) {
+        sY[j] = y00[base + j];
+        sY[n1 + j] = y10[base + j];
+        sY[2 * n1 + j] = y01[base + j];
+    }
+    __syncthreads();
+    double err = 0.0, nrm = 0.0;
+    const double w23 = we2[g2] * we3[g3];
+    for (int e = threadIdx.x; e < ne1; e += blockDim.x) {
+        const int s = E1.start[e], L = E1.len[e];
+        double u = 0, d1 = 0, d2 = 0, d3 = 0;
+        for (int t = 0; t < L; ++t) {
+            const double v = E1.lane(0, e, t), dv = E1.lane(1, e, t);
+            u = fma(v, sY[s + t], u);
+            d1 = fma(dv, sY[s + t], d1);
+            d2 = fma(v, sY[n1 + s + t], d2);
+            d3 = fma(v, sY[2 * n1 + s + t], d3);
+        }
+        double X[3], J[3][3];
+        geometry_at(geom, xe1[e], xe2[g2], xe3[g3], X, J);
+        // grad_x u = J^-T grad_xi u = adj(J)^T grad_xi u / det J
+        double A[3][3];
+        A[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+        A[0][1] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+        A[0][2] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+        A[1][0] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+        A[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+        A[1][2] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+        A[2][0] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+        A[2][1] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+        A[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+        const double det = J[0][0] * A[0][0] + J[0][1] * A[1][0] + J[0][2] * A[2][0];
+        const double gr[3] = {d1, d2, d3};
+        double gh[3];
+        for (int i = 0; i < 3; ++i) gh[i] = (A[0][i] * gr[0] + A[1][i] * gr[1] + A[2][i] * gr[2]) / det;
+        double ue, ge[3];
+        exact_at(sol, X, &ue, ge);
+        const double w = we1[e] * w23 * fabs(det);
+        const double e0 = ue - u, e1 = ge[0] - gh[0], e2 = ge[1] - gh[1], e3 = ge[2] - gh[2];
+        err += w * (e0 * e0 + e1 * e1 + e2 * e2 + e3 * e3);
+        nrm += w * (ue * ue + ge[0] * ge[0] + ge[1] * ge[1] + ge[2] * ge[2]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        err += __shfl_down_sync(0xffffffffu, err, o);
+        nrm += __shfl_down_sync(0xffffffffu, nrm, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = err;
+        red[1][threadIdx.x >> 5] = nrm;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a += red[0][w];
+            b += red[1][w];
+        }
+        part[2 * (size_t)blockIdx.x] = a;
+        part[2 * (size_t)blockIdx.x + 1] = b;
+    }
+}
+
+static int h1_smem_bytes(int n1) { return (int)(sizeof(double) * 3 * (size_t)n1); }
+
+// Relative H1 error of the discrete function with coefficients u: z stage
+// on all error planes, then slabs of g3 planes through the y stage and the
+// per-line error kernel; block sums added on the host in a fixed order.
+int run_h1_error(const DirD<double> d[3], int geom, int sol, const double* u, double* rel, cudaStream_t s) {
+    const int n1 = d[0].n, n2 = d[1].n, n3 = d[2].n, e1 = d[0].ne, e2 = d[1].ne, e3 = d[2].ne;
+    const size_t zsz = (size_t)e3 * n2 * n1;
+    const size_t slab_budget = (size_t)1 << 26;  // doubles per Y field (512 MB)
+    int ns = (int)std::max<size_t>(1, std::min<size_t>((size_t)e3, slab_budget / ((size_t)e2 * n1)));
+    double *Z = nullptr, *Y = nullptr, *part = nullptr;
+    const size_t ysz = (size_t)ns * e2 * n1;
+    const size_t nparts = (size_t)ns * e2;
+    int st = MFWQ_OK;
+    if (cudaMalloc(&Z, sizeof(double) * 2 * zsz) != cudaSuccess || cudaMalloc(&Y, sizeof(double) * 3 * ysz) != cudaSuccess ||
+        cudaMalloc(&part, sizeof(double) * 2 * nparts) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(Z);
+        cudaFree(Y);
+        cudaFree(part);
+        return MFWQ_ENOMEM;
+    }
+    std::vector<double> hp(2 * nparts);
+    double err = 0.0, nrm = 0.0;
+    if (h1_smem_bytes(n1) > 48 * 1024 &&
+        cudaFuncSetAttribute(k_h1_x, cudaFuncAttributeMaxDynamicSharedMemorySize, h1_smem_bytes(n1)) != cudaSuccess)
+        st = MFWQ_ECUDA;
+    OpTrialZ<double> oz{d[2].E, u, Z, Z + zsz};
+    if (launch_slow(S_H1, oz, 1, n3, e3, n2 * n1, nullptr, s) != cudaSuccess) st = MFWQ_ECUDA;
+    for (int g3a = 0; g3a < e3 && st == MFWQ_OK; g3a += ns) {
+        const int nsl = std::min(ns, e3 - g3a);
+        OpTrialY<double> oy{d[1].E, Z + (size_t)g3a * n2 * n1, Z + zsz + (size_t)g3a * n2 * n1, Y, Y + ysz, Y + 2 * ysz};
+        if (launch_slow(S_H1, oy, nsl, n2, e2, n1, nullptr, s) != cudaSuccess) { st = MFWQ_ECUDA; break; }
+        launch_begin(S_H1, s);
+        k_h1_x<<<nsl * e2, kThreads, sizeof(double) * 3 * n1, s>>>(d[0].E, d[0].xe, d[0].we, d[1].xe, d[1].we, d[2].xe,
+                                                                 d[2].we, n1, e1, e2, g3a, Y, Y + ysz, Y + 2 * ysz, geom,
+                                                                 sol, part);
+        launch_end(S_H1, s);
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(hp.data(), part, sizeof(double) * 2 * (size_t)nsl * e2, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            st = MFWQ_ECUDA;
+            break;
+        }
+        for (size_t b = 0; b < (size_t)nsl * e2; ++b) {
+            err += hp[2 * b];
+            nrm += hp[2 * b + 1];
+        }
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(Z);
+    cudaFree(Y);
+    cudaFree(part);
+    if (st == MFWQ_OK) *rel = nrm > 0.0 ? std::sqrt(err / nrm) : 0.0;
+    return st;
 }
 
 int run_load_vector(const DirD<double> d[3], int geom, int forcing, double* scratch, double* f, cudaStream_t s) {

@@ -265,7 +265,15 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
         return fail(MFWQ_EINVAL, "fd_precision must be MFWQ_FD_TF32 or MFWQ_FD_BF16 when mixed = 1");
     for (int l = 0; l < 3; ++l) {
         std::string why;
-        int st = build_dir(desc->degree[l], desc->nknots[l], desc->knots[l], h->dir[l], why);
+        // a direction with the degree and knots of an earlier one reuses its tables
+        int same = -1;
+        for (int k = 0; k < l && same < 0; ++k)
+            if (desc->degree[k] == desc->degree[l] && desc->nknots[k] == desc->nknots[l] &&
+                std::memcmp(desc->knots[k], desc->knots[l], sizeof(double) * desc->nknots[l]) == 0)
+                same = k;
+        int st = MFWQ_OK;
+        if (same >= 0) h->dir[l] = h->dir[same];
+        else st = build_dir(desc->degree[l], desc->nknots[l], desc->knots[l], h->dir[l], why);
         if (st != MFWQ_OK) return fail(st, "direction " + std::to_string(l + 1) + ": " + why);
         h->n[l] = h->dir[l].n;
         h->nq[l] = h->dir[l].nq;
@@ -278,9 +286,9 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
 
     // ---- tables
     Arena a;
-    BandOff bo[3][5];
+    BandOff bo[3][6];
     TileOff to[3][2];
-    size_t U64[3], UT64[3], L64[3], U32[3], UT32[3], L32[3], XQ[3], XG[3];
+    size_t U64[3], UT64[3], L64[3], U32[3], UT32[3], L32[3], XQ[3], XG[3], XE[3], WE[3];
     size_t VE[3] = {}, VET[3] = {}, VO[3] = {}, VOT[3] = {}, LS[3] = {};
     for (int l = 0; l < 3; ++l) {
         const Dir1D& d = h->dir[l];
@@ -289,6 +297,9 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
         bo[l][2] = stage_band(a, d.W);
         bo[l][3] = stage_band(a, d.WT);
         bo[l][4] = stage_band(a, d.GT);
+        bo[l][5] = stage_band(a, d.E);
+        XE[l] = a.add_vec(d.xe);
+        WE[l] = a.add_vec(d.we);
         to[l][0] = stage_tiles(a, d.B);
         to[l][1] = stage_tiles(a, d.W);
         U64[l] = a.add_vec(d.U);
@@ -326,6 +337,11 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
         y.W = band_at<float>(base, bo[l][2]);
         y.WT = band_at<float>(base, bo[l][3]);
         y.GT = band_at<float>(base, bo[l][4]);
+        x.E = band_at<double>(base, bo[l][5]);
+        y.E = band_at<float>(base, bo[l][5]);
+        x.ne = y.ne = h->dir[l].ne;
+        x.xe = y.xe = reinterpret_cast<const double*>(base + XE[l]);
+        x.we = y.we = reinterpret_cast<const double*>(base + WE[l]);
         x.BX = tiles_at<double>(base, to[l][0]);
         x.WX = tiles_at<double>(base, to[l][1]);
         y.BX = tiles_at<float>(base, to[l][0]);
@@ -652,6 +668,17 @@ int mfwq_grad_mass_coeff(mfwq_handle h, const double* lambda_dev, const double* 
     return run_grad_mass<double>(ctx64(h), lambda_dev, u_dev, gc_dev);
 }
 
+int mfwq_h1_error(mfwq_handle h, int geometry, int solution, const double* u_dev, double* rel_err) {
+    ProfScope _ps(h ? &h->prof : nullptr);
+    if (!h || !u_dev || !rel_err) return fail(MFWQ_EINVAL, "bad argument");
+    if (geometry != MFWQ_GEOM_CUBE && geometry != MFWQ_GEOM_RING) return fail(MFWQ_EINVAL, "unknown geometry");
+    if (solution != MFWQ_EXACT_SINES && solution != MFWQ_EXACT_RING) return fail(MFWQ_EINVAL, "unknown exact solution");
+    const int st = run_h1_error(h->d64, geometry, solution, u_dev, rel_err, h->stream);
+    if (st == MFWQ_ENOMEM) return fail(st, "device allocation for the error evaluation failed");
+    if (st != MFWQ_OK) return fail(st, "error evaluation failed");
+    return MFWQ_OK;
+}
+
 int mfwq_load_vector(mfwq_handle h, int geometry, int forcing, double* f_dev) {
     ProfScope _ps(h ? &h->prof : nullptr);
     if (!h || !f_dev) return fail(MFWQ_EINVAL, "bad argument");
@@ -733,7 +760,7 @@ int mfwq_grad_coeff(mfwq_handle h, const double* lambda_dev, const double* u_dev
 
 static const char* kStageNames[S_NTAGS] = {
     "trial_z", "trial_y", "xstage", "test_y", "test_z", "test_zT", "test_yT", "xstage_T", "trial_yT", "trial_zT",
-    "xstage_grad", "fd_dim1", "fd_dim23", "fd_tc", "krylov", "setup", "fd_fold", "mass"};
+    "xstage_grad", "fd_dim1", "fd_dim23", "fd_tc", "krylov", "setup", "fd_fold", "mass", "h1_error"};
 
 const char* mfwq_stage_name(int stage) { return stage >= 0 && stage < S_NTAGS ? kStageNames[stage] : ""; }
 

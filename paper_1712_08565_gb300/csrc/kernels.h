@@ -52,6 +52,9 @@ int run_eval_coeff(const int nq[3], const double* const xq[3], int geom, const d
                    double* C, cudaStream_t s);
 int run_load_vector(const DirD<double> d[3], int geom, int forcing, double* scratch, double* f, cudaStream_t s);
 int run_eval_mass(const int nq[3], const double* const xq[3], int geom, double alpha, double* c, cudaStream_t s);
+// Relative H1 error against an exact solution (MFWQ_EXACT_*); allocates its
+// temporaries, synchronises the stream.
+int run_h1_error(const DirD<double> d[3], int geom, int sol, const double* u, double* rel, cudaStream_t s);
 
 // FD preconditioner, FP64: z = P^-1 r; tmp holds N doubles.  skip as above.
 int run_fd64(const DirD<double> d[3], const double* r, double* z, double* tmp, const int* skip, cudaStream_t s);

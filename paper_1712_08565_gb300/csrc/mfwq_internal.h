@@ -39,6 +39,9 @@ struct Dir1D {
     Band1D W;    // rows i -> points q, fams f = 2a+b
     Band1D WT;   // rows q -> rows i, transposed W
     Band1D GT;   // rows j -> Gauss points g, value b_j(x_g) * w_g
+    std::vector<double> xe, we;  // error rule: Gauss, p+2 points per span
+    int ne = 0;
+    Band1D E;    // rows e (error points) -> columns j, fams: 0 = values, 1 = derivatives
     std::vector<double> U, UT, lam;  // FD: U [n][n] row-major, UT = U^T, lam[n]
     // FD even/odd split (knots symmetric about 1/2): he = n - n/2 even and
     // ho = n/2 odd modes; Ve [he][he], Vo [ho][ho] act on the folded vector
@@ -85,7 +88,11 @@ template <typename T>
 struct DirD {
     int n, nq, ng;
     BandD<T> B, BT, W, WT, GT;
+    BandD<T> E;       // B-spline values and derivatives at the error points
     TileD<T> BX, WX;  // B and W in two-row tiles (the tiled x stage)
+    int ne;           // error points
+    const double* xe; // error points and weights (always FP64)
+    const double* we;
     const T* U;     // [n][n]
     const T* UT;    // [n][n]
     const T* lam;   // [n]

@@ -2,9 +2,12 @@
 // 3.2; weights of Section 2.2; FD factors of the preconditioner of Section 4).
 // Runs once per handle, O(n p^2) work per direction; not on the hot path.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <thread>
 
 #include "mfwq_internal.h"
 
@@ -597,7 +600,12 @@ int build_dir(int p, int nknots, const double* knots, Dir1D& d, std::string& why
                 }
             return tot;
         };
-        for (int i = 0; i < n; ++i) {
+        // Rows are independent systems: solved on host threads, each row
+        // written by one thread only, so the tables do not depend on the
+        // thread count.
+        std::mutex fail_mu;
+        std::atomic<bool> failed{false};
+        auto solve_row = [&](int i) {
             std::vector<int> T;
             for (int j = std::max(0, i - p); j <= std::min(n - 1, i + p); ++j) T.push_back(j);
             int rows = (int)T.size(), cols = W.len[i];
@@ -622,13 +630,25 @@ int build_dir(int p, int nknots, const double* knots, Dir1D& d, std::string& why
                         char buf[160];
                         std::snprintf(buf, sizeof buf, "weight system (a=%d,b=%d) of row %d inconsistent: residual %.3e",
                                       a, b, i, gn > 0 ? res / gn : res);
-                        why = buf;
-                        return MFWQ_ESETUP;
+                        std::lock_guard<std::mutex> lk(fail_mu);
+                        if (!failed.exchange(true)) why = buf;
+                        return;
                     }
                     for (int c = 0; c < cols; ++c) W.at(2 * a + b, i, c) = w[c];
                 }
             }
-        }
+        };
+        const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+        const int nth = (int)std::min<unsigned>(std::min(hw, 64u), (unsigned)std::max(1, n / 4));
+        std::atomic<int> next{0};
+        auto worker = [&]() {
+            for (int i = next.fetch_add(1); i < n && !failed.load(); i = next.fetch_add(1)) solve_row(i);
+        };
+        std::vector<std::thread> pool;
+        for (int k = 1; k < nth; ++k) pool.emplace_back(worker);
+        worker();
+        for (std::thread& t : pool) t.join();
+        if (failed.load()) return MFWQ_ESETUP;
     }
 
     // Transposed bands.
@@ -673,6 +693,37 @@ int build_dir(int p, int nknots, const double* knots, Dir1D& d, std::string& why
             for (int k = 0; k < S.len[g]; ++k) S.at(0, g, k) = basis_at(gb[g], p, lo + k, 0) * d.wg[g];
         }
         transpose_band(S, d.GT);
+    }
+
+    // Error rule (relative H1 error, Section 4): Gauss with p+2 points per
+    // span; band rows e -> interior columns j with values and derivatives.
+    {
+        std::vector<double> ex, ew;
+        gauss_legendre(p + 2, ex, ew);
+        d.xe.clear();
+        d.we.clear();
+        for (int s = 0; s < nel; ++s) {
+            double a = u[s], b = u[s + 1];
+            for (int k = 0; k < p + 2; ++k) {
+                d.xe.push_back(0.5 * (a + b) + 0.5 * (b - a) * ex[k]);
+                d.we.push_back(0.5 * (b - a) * ew[k]);
+            }
+        }
+        const int ne = d.ne = (int)d.xe.size();
+        Band1D& E = d.E;
+        E.rows = ne; E.cols = n; E.fams = 2; E.width = p + 1;
+        E.start.assign(ne, 0); E.len.assign(ne, 0);
+        E.val.assign((size_t)2 * ne * (p + 1), 0.0);
+        for (int g = 0; g < ne; ++g) {
+            const PointBasis eb = eval_point(t, p, m, d.xe[g]);
+            int lo = std::max(1, eb.span - p), hi = std::min(m - 2, eb.span);
+            E.start[g] = lo - 1;
+            E.len[g] = std::max(0, hi - lo + 1);
+            for (int k = 0; k < E.len[g]; ++k) {
+                E.at(0, g, k) = basis_at(eb, p, lo + k, 0);
+                E.at(1, g, k) = basis_at(eb, p, lo + k, 1);
+            }
+        }
     }
 
     // FD factors: K_l = G^{11}, M_l = G^{00}; U^T M U = I, U^T K U = diag(lambda).

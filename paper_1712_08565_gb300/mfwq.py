@@ -23,6 +23,7 @@ STATUS = {0: "MFWQ_OK", -1: "MFWQ_EINVAL", -2: "MFWQ_ENOMEM", -3: "MFWQ_ECUDA", 
 FD_PRECISION = {"fp64": 0, "tf32": 1, "bf16": 2}
 GEOMETRY = {"cube": 0, "ring": 1}
 FORCING = {"sines": 0, "ring_exact": 1}
+EXACT = {"sines": 0, "ring": 1}
 
 _c_int3 = ctypes.c_int * 3
 _c_dptr = ctypes.POINTER(ctypes.c_double)
@@ -85,6 +86,8 @@ _SIGS = [
     ("mfwq_eval_mass_coeff", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_void_p]),
     ("mfwq_set_mass_coeff", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double]),
     ("mfwq_grad_mass_coeff", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    ("mfwq_h1_error", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p,
+                                     ctypes.POINTER(ctypes.c_double)]),
     ("mfwq_load_vector", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_void_p]),
     ("mfwq_apply", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
     ("mfwq_apply_T", ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -294,6 +297,15 @@ class Operator:
                                           _ptr(u, torch.float64, self.N, self.device),
                                           _ptr(out, torch.float64, self.Nq, self.device)))
         return out
+
+    def h1_error(self, u, geometry: str = "ring", solution: str = "ring") -> float:
+        """Relative H1 error of the discrete function u against an exact
+        solution ('sines' on the cube, 'ring' = Eq. (exact-solution)); synchronous."""
+        import torch
+        v = ctypes.c_double()
+        _check(lib().mfwq_h1_error(self._h, GEOMETRY[geometry], EXACT[solution],
+                                   _ptr(u, torch.float64, self.N, self.device), ctypes.byref(v)))
+        return v.value
 
     def load_vector(self, geometry: str = "ring", forcing: str = "sines", out=None):
         import torch
