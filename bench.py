@@ -324,6 +324,36 @@ def p_sweep(mf, device):
     return out
 
 
+def reaction(mf, device, alpha=10.0):
+    """The bench ring with the reaction term alpha u (c = alpha det J, FD shift
+    alpha): apply time with and without the term, and the FP64 solve."""
+    import torch
+    from paper_1712_08565_gb300 import inputs
+    op, _ = make_op(mf, WORKLOAD["p"], WORKLOAD["nel"], device=device)
+    x = torch.from_numpy(inputs.uniform_vector(op.shape, 1)).to(device)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        op.apply(x, y)
+    ms_plain = event_time(op.stream, lambda: op.apply(x, y), 10)
+    op.set_mass_coeff(op.eval_mass_coeff("ring", alpha), fd_shift=alpha)
+    for _ in range(3):
+        op.apply(x, y)
+    ms_mass = event_time(op.stream, lambda: op.apply(x, y), 10)
+    f = op.load_vector(WORKLOAD["geometry"], WORKLOAD["forcing"])
+    op.solve(f, rtol=WORKLOAD["rtol"], maxit=1000)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(op.stream)
+    _, info = op.solve(f, rtol=WORKLOAD["rtol"], maxit=1000)
+    e1.record(op.stream)
+    e1.synchronize()
+    out = {"workload": WORKLOAD["name"] + "-alpha%g" % alpha, "alpha": alpha, "fd_shift": alpha,
+           "apply_ms": ms_mass, "apply_ms_without_reaction": ms_plain, "solve_s": e0.elapsed_time(e1) / 1e3,
+           "iterations": info.iterations, "rel_residual": info.rel_residual, "converged": info.converged}
+    op.close()
+    return out
+
+
 def mixed_vs_fp64(mf, device):
     import torch
     from paper_1712_08565_gb300 import inputs
@@ -530,6 +560,7 @@ def run_ours(args):
         extras["p_sweep_nel128"] = p_sweep(mf, device)
         extras["mixed_vs_fp64"] = mixed_vs_fp64(mf, device)
         extras["batched_64"] = batched(mf, device)
+        extras["reaction"] = reaction(mf, device)
     line = {
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

@@ -1070,23 +1070,26 @@ __global__ void k_eval_mass(int geom, double alpha, const double* __restrict__ x
     }
 }
 
-__device__ double forcing_at(int forcing, const double X[3]) {
+// The forcing at the physical point (X0, X1, x3), with the z-factors
+// sin(k x3), cos(k x3) given: k = 5 pi for the ring's exact solution
+// (f = -Laplace of Eq. (exact-solution)), pi for 3 pi^2 sin sin sin.
+__device__ double forcing_line_at(int forcing, double X0, double X1, double s3, double c3) {
     const double pi = 3.141592653589793;
+    (void)c3;
     if (forcing == MFWQ_FORCING_RING_EXACT) {
         const double k = 5.0 * pi;
-        double s1, c1, s2, c2, s3, c3;
-        sincos(k * X[0], &s1, &c1);
-        sincos(k * X[1], &s2, &c2);
-        sincos(k * X[2], &s3, &c3);
-        const double rho = X[0] * X[0] + X[1] * X[1];
+        double s1, c1, s2, c2;
+        sincos(k * X0, &s1, &c1);
+        sincos(k * X1, &s2, &c2);
+        const double rho = X0 * X0 + X1 * X1;
         const double q = (rho - 1.0) * (rho - 4.0);
         const double S = s1 * s2 * s3;
         const double lapS = -3.0 * k * k * S;
-        const double gsq = (2.0 * rho - 5.0) * 2.0 * (X[0] * k * c1 * s2 * s3 + X[1] * k * s1 * c2 * s3);
+        const double gsq = (2.0 * rho - 5.0) * 2.0 * (X0 * k * c1 * s2 * s3 + X1 * k * s1 * c2 * s3);
         const double lapq = 8.0 * rho + (2.0 * rho - 5.0) * 4.0;
         return -(q * lapS + 2.0 * gsq + S * lapq);
     }
-    return 3.0 * pi * pi * sin(pi * X[0]) * sin(pi * X[1]) * sin(pi * X[2]);
+    return 3.0 * pi * pi * sin(pi * X0) * sin(pi * X1) * s3;
 }
 
 // Load vector, x stage: out[g3][g2][j1] = sum_g1 GT1[j1] |det J| f(F(xi)) on
@@ -1098,12 +1101,27 @@ __global__ void __launch_bounds__(kThreads) k_rhs_x(int geom, int forcing, BandD
     double* sF = reinterpret_cast<double*>(smem_raw);  // [ng1]
     const int line = blockIdx.x;
     const int g2 = line % ng2, g3 = line / ng2;
+    // Along a line only xi1 varies: the ring's angle pi/2 xi2 and the
+    // z-factors of the forcing (x3 = xi3 in both geometries) are computed once.
+    const double pi = 3.141592653589793, hp = 0.5 * pi;
+    const double xi2 = xg2[g2], xi3 = xg3[g3];
+    double sn, cs;
+    sincos(hp * xi2, &sn, &cs);
+    double s3, c3;
+    sincos((forcing == MFWQ_FORCING_RING_EXACT ? 5.0 * pi : pi) * xi3, &s3, &c3);
     for (int g = threadIdx.x; g < ng1; g += blockDim.x) {
-        double X[3], J[3][3];
-        geometry_at(geom, xg1[g], xg2[g2], xg3[g3], X, J);
-        const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
-                           J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
-        sF[g] = fabs(det) * forcing_at(forcing, X);
+        double X0, X1, det;
+        if (geom == MFWQ_GEOM_RING) {
+            const double r = 1.0 + xg1[g];
+            X0 = r * cs;
+            X1 = r * sn;
+            det = r * hp;  // |det J| of the polar map
+        } else {
+            X0 = xg1[g];
+            X1 = xi2;
+            det = 1.0;
+        }
+        sF[g] = det * forcing_line_at(forcing, X0, X1, s3, c3);
     }
     __syncthreads();
     for (int j = threadIdx.x; j < n1; j += blockDim.x) {
