@@ -728,6 +728,162 @@ __global__ void __launch_bounds__(kThreads) k_xstage_tiled(XArgs<T> a, const T* 
     }
 }
 
+// ---- stencil forward x stage (mode 6): translation-invariant interiors
+// For uniform knots the interior rows of B (pairs of points) and W (outputs)
+// are one filter shifted along the line (StencilD); boundary rows use the
+// band tables.  A block owns 8 lines.
+//  trial: lanes = consecutive pairs of points of one line; the pair's window
+//    of P + 2 Y values gives G_b at both points (filter taps are kernel
+//    parameters), then the three H^(alpha b) = C_(alpha b) G_b with coalesced
+//    coefficient loads, stored to shared memory;
+//  test: lanes = (line, alpha), 24 of 32; a lane walks segments of 8 outputs
+//    of its own row with the window (2P + 15 values) in registers: 8(2P + 1)
+//    multiply-adds per window.  Row strides are 1 mod 32 and the alpha slabs
+//    8 rows apart, so the 24 lanes hit 24 different banks;
+//  outputs staged in shared memory (aliasing Y) and written out coalesced.
+constexpr int kStLines = 8;  // the (line, alpha) lane map and the copy-out assume 8
+constexpr int kSeg = 8;
+static_assert(kStLines == 8, "stencil x stage: 3 x 8 (line, alpha) lanes per warp");
+
+// row stride >= n with stride = 1 (mod 32)
+__host__ __device__ inline int st_stride(int n) { return ((n + 30) / 32) * 32 + 1; }
+
+template <typename T, int P, int BF>
+__device__ __forceinline__ void st_pair(const StencilD<T>& st, const T* Y, T& g0, T& g1) {
+    constexpr int NB = P + 2;
+    T a = 0, b = 0;
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+        const T y = Y[t];
+        a = fmaT(st.bf[BF][0][t], y, a);
+        b = fmaT(st.bf[BF][1][t], y, b);
+    }
+    g0 = a;
+    g1 = b;
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void st_seg(const T* w, const T* H, T* To) {
+    constexpr int NW = 2 * P + 1, WIN = 2 * (kSeg - 1) + NW;
+    T h[WIN];
+#pragma unroll
+    for (int u = 0; u < WIN; ++u) h[u] = H[u];
+#pragma unroll
+    for (int r = 0; r < kSeg; ++r) {
+        T acc = 0;
+#pragma unroll
+        for (int t = 0; t < NW; ++t) acc = fmaT(w[t], h[2 * r + t], acc);
+        To[r] = acc;
+    }
+}
+
+template <typename T, int P, int BETA>
+__device__ __forceinline__ void st_beta(const XArgs<T>& a, const StencilD<T>& st, const T* __restrict__ yb,
+                                        T* __restrict__ tout, size_t tstride, int line0, int nl, T* sY, T* sH) {
+    constexpr int BF = BETA == 0 ? 1 : 0;  // trial family: derivative in direction 1 for beta = 1
+    constexpr int NW = 2 * P + 1;
+    const int n1 = a.n1, nq1 = a.nq1;
+    const int rY = st_stride(n1), rG = st_stride(nq1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int c0 = BETA == 0 ? 0 : 2 + BETA, c1 = BETA == 1 ? 1 : 3 + BETA, c2 = BETA == 2 ? 2 : 4 + BETA;
+    __syncthreads();  // previous beta's outputs copied out of sY
+    for (int ll = warp; ll < kStLines; ll += nwarps) {
+        const T* src = yb + (size_t)(line0 + ll) * n1;
+        for (int j = lane; j < n1; j += 32) sY[ll * rY + j] = ll < nl ? src[j] : T(0);
+    }
+    __syncthreads();
+    // trial, interior pairs: warp-sized chunks of consecutive pairs of one line
+    const int npairs = (st.q_hi - st.q_lo) >> 1;
+    const int nch = (npairs + 31) >> 5;
+    for (int it = warp, ll = 0, ch = warp; it < kStLines * nch; it += nwarps, ch += nwarps) {
+        while (ch >= nch) {  // (line, chunk) of item it without a division
+            ch -= nch;
+            ++ll;
+        }
+        const int k = (ch << 5) + lane;
+        if (k >= npairs) continue;
+        T g0, g1;
+        st_pair<T, P, BF>(st, sY + ll * rY + st.jb + k, g0, g1);
+        const int q = st.q_lo + 2 * k;
+        T* H = sH + ll * rG + q;
+        if (ll < nl) {
+            const T* C = a.C + (size_t)(line0 + ll) * nq1 + q;
+            H[0] = C[(size_t)c0 * a.cs] * g0;
+            H[1] = C[(size_t)c0 * a.cs + 1] * g1;
+            H[kStLines * rG] = C[(size_t)c1 * a.cs] * g0;
+            H[kStLines * rG + 1] = C[(size_t)c1 * a.cs + 1] * g1;
+            H[2 * kStLines * rG] = C[(size_t)c2 * a.cs] * g0;
+            H[2 * kStLines * rG + 1] = C[(size_t)c2 * a.cs + 1] * g1;
+        } else {
+            H[0] = H[1] = H[kStLines * rG] = H[kStLines * rG + 1] = H[2 * kStLines * rG] = H[2 * kStLines * rG + 1] = 0;
+        }
+    }
+    // trial, boundary points: one item per (line, point)
+    const int nbq = st.q_lo + (nq1 - st.q_hi);
+    for (int ll = warp; ll < kStLines; ll += nwarps)
+        for (int k = lane; k < nbq; k += 32) {
+            const int q = k < st.q_lo ? k : st.q_hi + (k - st.q_lo);
+            const int s0 = a.B.start[q], L = a.B.len[q];
+            const T* Y = sY + ll * rY + s0;
+            T g = 0;
+            for (int t = 0; t < L; ++t) g = fmaT(a.B.lane(BF, q, t), Y[t], g);
+            T* H = sH + ll * rG + q;
+            const bool live = ll < nl;
+            const size_t cb = (size_t)(line0 + ll) * nq1 + q;
+            H[0] = live ? a.C[(size_t)c0 * a.cs + cb] * g : T(0);
+            H[kStLines * rG] = live ? a.C[(size_t)c1 * a.cs + cb] * g : T(0);
+            H[2 * kStLines * rG] = live ? a.C[(size_t)c2 * a.cs + cb] * g : T(0);
+        }
+    __syncthreads();
+    // test: lane = (line l, alpha al) for lane < 24
+    const int nseg = (st.i_hi - st.i_lo) / kSeg;
+    const int i_st = st.i_lo + nseg * kSeg;
+    const int nbi = st.i_lo + (n1 - i_st);
+    const int rT = rY;
+    T* sT = sY;  // [3 alpha][8][rT]: outputs of this beta (Y no longer needed)
+    if (lane < 3 * kStLines) {
+        const int al = lane >> 3, l = lane & 7;
+        const int fam = al == 0 ? 2 + BF : BF;
+        T w[NW];
+#pragma unroll
+        for (int t = 0; t < NW; ++t) w[t] = al == 0 ? st.wf[2 + BF][t] : st.wf[BF][t];
+        const T* Hl = sH + (al * kStLines + l) * rG;
+        T* To = sT + (al * kStLines + l) * rT;
+        for (int sg = warp; sg < nseg; sg += nwarps)
+            st_seg<T, P>(w, Hl + st.qw + 2 * kSeg * sg, To + st.i_lo + kSeg * sg);
+        for (int k = warp; k < nbi; k += nwarps) {
+            const int i = k < st.i_lo ? k : i_st + (k - st.i_lo);
+            const int s0 = a.W.start[i], L = a.W.len[i];
+            T acc = 0;
+            for (int t = 0; t < L; ++t) acc = fmaT(a.W.lane(fam, i, t), Hl[s0 + t], acc);
+            To[i] = acc;
+        }
+    }
+    __syncthreads();
+    for (int row = warp; row < 3 * kStLines; row += nwarps) {
+        const int al = row >> 3, ll = row & 7;  // kStLines = 8
+        if (ll >= nl) continue;
+        T* o = tout + (size_t)(3 * al + BETA) * tstride + (size_t)(line0 + ll) * n1;
+        const T* src = sT + (al * kStLines + ll) * rT;
+        for (int i = lane; i < n1; i += 32) o[i] = src[i];
+    }
+}
+
+template <typename T, int P>
+__global__ void __launch_bounds__(kThreads) k_xstage_stencil(XArgs<T> a, StencilD<T> st, const T* __restrict__ y0,
+                                                             const T* __restrict__ y1, const T* __restrict__ y2,
+                                                             T* __restrict__ tout, size_t tstride, const int* skip) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sY = reinterpret_cast<T*>(smem_raw);           // Y rows of one beta, then the staged outputs [3][8][rY]
+    T* sH = sY + 3 * kStLines * st_stride(a.n1);      // [3 alpha][8][rG]
+    const int line0 = blockIdx.x * kStLines;
+    const int nl = min(kStLines, a.nlines - line0);
+    st_beta<T, P, 0>(a, st, y0, tout, tstride, line0, nl, sY, sH);
+    st_beta<T, P, 1>(a, st, y1, tout, tstride, line0, nl, sY, sH);
+    st_beta<T, P, 2>(a, st, y2, tout, tstride, line0, nl, sY, sH);
+}
+
 // Transposed x stage: R (9 inputs [line][n1]) -> S^(ab) = W1^T R at q1 ->
 // E_b = sum_a C_ab S^(ab) -> X_b = B1^(b)T E_b (3 outputs [line][n1]).
 template <typename T>
@@ -1149,6 +1305,21 @@ static void scratch_strides(const OpCtx<T>& c, size_t* SP, size_t* SQ) {
     scratch_strides(n, nq, SP, SQ);
 }
 
+template <typename T>
+void launch_stencil(const StencilD<T>& S, int nlines, size_t sm, cudaStream_t st, const XArgs<T>& a, const T* y0,
+                    const T* y1, const T* y2, T* tout, size_t tstride, const int* skip) {
+    const dim3 grid((nlines + kStLines - 1) / kStLines);
+    switch (S.P) {
+        case 2: k_xstage_stencil<T, 2><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
+        case 3: k_xstage_stencil<T, 3><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
+        case 4: k_xstage_stencil<T, 4><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
+        case 5: k_xstage_stencil<T, 5><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
+        case 6: k_xstage_stencil<T, 6><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
+        case 7: k_xstage_stencil<T, 7><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
+        default: k_xstage_stencil<T, 8><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
+    }
+}
+
 template <typename T, int CARVE>
 void launch_xstage_mode(int mode, int L, dim3 grid, size_t sm, cudaStream_t st, const XArgs<T>& a, const T* y0,
                         const T* y1, const T* y2, T* tout, size_t tstride, const int* skip, int* err) {
@@ -1186,16 +1357,18 @@ int run_apply(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
     {
         XArgs<T> a = xargs(d1, q3 * q2, c.cs, c.C);
         int L = c.xlines == 2 || c.xlines == 8 ? c.xlines : 4;
-        int mode = c.xmode >= 0 && c.xmode <= 5 ? c.xmode : 0;
-        if (mode >= 4) L = kTileLines;
-        if (!xstage_mode_valid((int)sizeof(T), n1, q1, L, mode) || (mode >= 2 && mode <= 3 && c.cs % 4 != 0)) {
+        int mode = c.xmode >= 0 && c.xmode <= 6 ? c.xmode : 0;
+        if (mode >= 4) L = mode == 6 ? kStLines : kTileLines;
+        if (!xstage_mode_valid((int)sizeof(T), n1, q1, L, mode) || (mode >= 2 && mode <= 3 && c.cs % 4 != 0) ||
+            (mode == 6 && !d1.SX.ok)) {
             mode = 0;
             L = 4;
         }
         const size_t sm = (size_t)xstage_smem_bytes((int)sizeof(T), n1, q1, L, mode);
         dim3 grid((q3 * q2 + L - 1) / L);
         launch_begin(S_XSTAGE, c.stream);
-        if (c.xcarve) launch_xstage_mode<T, 1>(mode, L, grid, sm, c.stream, a, Y[0], Y[1], Y[2], Tt[0], SP, skip, c.err);
+        if (mode == 6) launch_stencil<T>(d1.SX, q3 * q2, sm, c.stream, a, Y[0], Y[1], Y[2], Tt[0], SP, skip);
+        else if (c.xcarve) launch_xstage_mode<T, 1>(mode, L, grid, sm, c.stream, a, Y[0], Y[1], Y[2], Tt[0], SP, skip, c.err);
         else launch_xstage_mode<T, 0>(mode, L, grid, sm, c.stream, a, Y[0], Y[1], Y[2], Tt[0], SP, skip, c.err);
         launch_end(S_XSTAGE, c.stream);
         if (cudaGetLastError() != cudaSuccess) return MFWQ_ECUDA;
@@ -1354,6 +1527,8 @@ size_t rhs_scratch_elems(const int n[3], const int ng[3]) {
 }
 
 int xstage_smem_bytes(int elem_size, int n1, int nq1, int lines, int mode) {
+    if (mode == 6)  // stencil: Y rows / staged outputs and H rows of 8 lines, 3 slabs each
+        return (int)((size_t)3 * kStLines * (st_stride(n1) + (size_t)st_stride(nq1)) * elem_size);
     if (mode >= 4) {  // tiled: two lines-innermost slabs of 3 x (rows + 4) padded rows
         const int pr = 128 / (kTileLines * elem_size), pad = 16 / elem_size;
         auto tr = [&](int r) { return (size_t)r * kTileLines + (size_t)(r / pr) * pad; };
@@ -1365,8 +1540,9 @@ int xstage_smem_bytes(int elem_size, int n1, int nq1, int lines, int mode) {
 }
 
 bool xstage_mode_valid(int elem_size, int n1, int nq1, int lines, int mode) {
-    if (mode < 0 || mode > 5) return false;
-    if (mode >= 4 && lines != kTileLines) return false;
+    if (mode < 0 || mode > 6) return false;
+    if (mode == 6 && lines != kStLines) return false;
+    if ((mode == 4 || mode == 5) && lines != kTileLines) return false;
     if (mode >= 2 && (lines * elem_size) % 16 != 0) return false;
     return xstage_smem_bytes(elem_size, n1, nq1, lines, mode) <= kXstageSmemMax;
 }
@@ -1411,6 +1587,18 @@ static cudaError_t set_xstage_smem_all(int bytes) {
     return e;
 }
 
+template <typename T>
+static cudaError_t set_stencil_smem(int bytes) {
+    cudaError_t e = set_kernel_smem(k_xstage_stencil<T, 2>, bytes, 0);
+    if (e == cudaSuccess) e = set_kernel_smem(k_xstage_stencil<T, 3>, bytes, 0);
+    if (e == cudaSuccess) e = set_kernel_smem(k_xstage_stencil<T, 4>, bytes, 0);
+    if (e == cudaSuccess) e = set_kernel_smem(k_xstage_stencil<T, 5>, bytes, 0);
+    if (e == cudaSuccess) e = set_kernel_smem(k_xstage_stencil<T, 6>, bytes, 0);
+    if (e == cudaSuccess) e = set_kernel_smem(k_xstage_stencil<T, 7>, bytes, 0);
+    if (e == cudaSuccess) e = set_kernel_smem(k_xstage_stencil<T, 8>, bytes, 0);
+    return e;
+}
+
 // The dynamic shared-memory limit is a per-kernel attribute shared by all
 // handles, so it only ever grows.
 int configure_xstage_smem(int bytes) {
@@ -1420,6 +1608,8 @@ int configure_xstage_smem(int bytes) {
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
     e = set_xstage_smem_all<0>(bytes);
     if (e == cudaSuccess) e = set_xstage_smem_all<1>(bytes);
+    if (e == cudaSuccess) e = set_stencil_smem<float>(bytes);
+    if (e == cudaSuccess) e = set_stencil_smem<double>(bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_applyT<double>, A, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_grad<double>, A, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_applyT<float>, A, bytes);

@@ -130,6 +130,105 @@ TileOff stage_tiles(Arena& a, const Band1D& b) {
     return o;
 }
 
+// Translation-invariant interior of the direction's B and W bands (StencilD):
+// the largest ranges around the middle rows whose rows equal the middle
+// (phase) row shifted by one column per pair of points, or by two points
+// per output, to 1e-12 relative, and whose fixed-size windows stay inside
+// the band columns.  ok = 0 when the degree exceeds kStencilMaxP or no
+// interior exists (e.g. non-uniform knots).
+StencilD<double> detect_stencil(const Dir1D& d) {
+    StencilD<double> S{};
+    S.ok = 0;
+    const int P = d.p;
+    if (P < 2 || P > kStencilMaxP) return S;
+    S.P = P;
+    const Band1D& B = d.B;
+    const Band1D& W = d.W;
+    const int NB = P + 2, NW = 2 * P + 1;
+    auto same_vals = [](const Band1D& b, int r, int r0, int fams) {
+        if (b.len[r] != b.len[r0]) return false;
+        double mx = 0.0;
+        for (int f = 0; f < fams; ++f)
+            for (int t = 0; t < b.len[r0]; ++t) mx = std::max(mx, std::fabs(b.at(f, r0, t)));
+        for (int f = 0; f < fams; ++f)
+            for (int t = 0; t < b.len[r0]; ++t)
+                if (std::fabs(b.at(f, r, t) - b.at(f, r0, t)) > 1e-12 * mx) return false;
+        return true;
+    };
+    // points: pairs (r0 + 2k, r0 + 2k + 1) around the middle
+    const int nq = B.rows, n = B.cols;
+    int r0 = nq / 2;
+    if (r0 + 1 >= nq) return S;
+    auto pair_ok = [&](int k) {  // pair starting at r0 + 2k
+        const int a = r0 + 2 * k, b = a + 1;
+        if (a < 0 || b >= nq) return false;
+        if (B.start[a] != B.start[r0] + k || B.start[b] != B.start[r0 + 1] + k) return false;
+        return same_vals(B, a, r0, 2) && same_vals(B, b, r0 + 1, 2);
+    };
+    if (!pair_ok(0)) return S;
+    int klo = 0, khi = 1;  // pairs [klo, khi)
+    while (pair_ok(klo - 1)) --klo;
+    while (pair_ok(khi)) ++khi;
+    const int jmin0 = std::min(B.start[r0], B.start[r0 + 1]);
+    const int jmax0 = std::max(B.start[r0] + B.len[r0], B.start[r0 + 1] + B.len[r0 + 1]);
+    if (jmax0 - jmin0 > NB) return S;
+    // every pair's fixed window [jmin0 + k, jmin0 + k + NB) inside [0, n)
+    while (klo < khi && jmin0 + klo < 0) ++klo;
+    while (khi > klo && jmin0 + (khi - 1) + NB > n) --khi;
+    if (khi - klo < 1) return S;
+    S.q_lo = r0 + 2 * klo;
+    S.q_hi = r0 + 2 * khi;
+    S.jb = jmin0 + klo;
+    for (int f = 0; f < 2; ++f)
+        for (int ph = 0; ph < 2; ++ph) {
+            const int r = r0 + ph, off = B.start[r] - jmin0;
+            for (int t = 0; t < NB; ++t) S.bf[f][ph][t] = 0.0;
+            for (int t = 0; t < B.len[r]; ++t) S.bf[f][ph][off + t] = B.at(f, r, t);
+        }
+    // outputs: rows i = w0 + m, start = start[w0] + 2m
+    const int nr = W.rows, w0 = nr / 2;
+    if (W.len[w0] > NW) return S;
+    auto row_ok = [&](int m) {
+        const int i = w0 + m;
+        if (i < 0 || i >= nr) return false;
+        return W.start[i] == W.start[w0] + 2 * m && same_vals(W, i, w0, 4);
+    };
+    int mlo = 0, mhi = 1;
+    while (row_ok(mlo - 1)) --mlo;
+    while (row_ok(mhi)) ++mhi;
+    while (mlo < mhi && W.start[w0] + 2 * mlo < 0) ++mlo;
+    while (mhi > mlo && W.start[w0] + 2 * (mhi - 1) + NW > d.nq) --mhi;
+    if (mhi - mlo < 1) return S;
+    S.i_lo = w0 + mlo;
+    S.i_hi = w0 + mhi;
+    S.qw = W.start[w0] + 2 * mlo;
+    for (int f = 0; f < 4; ++f) {
+        for (int t = 0; t < NW; ++t) S.wf[f][t] = 0.0;
+        for (int t = 0; t < W.len[w0]; ++t) S.wf[f][t] = W.at(f, w0, t);
+    }
+    S.ok = 1;
+    return S;
+}
+
+template <typename T>
+StencilD<T> stencil_as(const StencilD<double>& a) {
+    StencilD<T> b;
+    b.ok = a.ok;
+    b.P = a.P;
+    b.q_lo = a.q_lo;
+    b.q_hi = a.q_hi;
+    b.jb = a.jb;
+    b.i_lo = a.i_lo;
+    b.i_hi = a.i_hi;
+    b.qw = a.qw;
+    for (int f = 0; f < 2; ++f)
+        for (int ph = 0; ph < 2; ++ph)
+            for (int t = 0; t < kStencilMaxP + 2; ++t) b.bf[f][ph][t] = (T)a.bf[f][ph][t];
+    for (int f = 0; f < 4; ++f)
+        for (int t = 0; t < 2 * kStencilMaxP + 1; ++t) b.wf[f][t] = (T)a.wf[f][t];
+    return b;
+}
+
 template <typename T>
 TileD<T> tiles_at(unsigned char* base, const TileOff& o) {
     TileD<T> t;
@@ -344,6 +443,8 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
         x.we = y.we = reinterpret_cast<const double*>(base + WE[l]);
         x.BX = tiles_at<double>(base, to[l][0]);
         x.WX = tiles_at<double>(base, to[l][1]);
+        x.SX = detect_stencil(h->dir[l]);
+        y.SX = stencil_as<float>(x.SX);
         y.BX = tiles_at<float>(base, to[l][0]);
         y.WX = tiles_at<float>(base, to[l][1]);
         x.U = reinterpret_cast<const double*>(base + U64[l]);
@@ -402,7 +503,7 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
     if (smem > kXstageSmemMax) return fail(MFWQ_EINVAL, "direction-1 size too large for the x-stage tile");
     h->max_xlines = xstage_smem_bytes(8, h->n[0], h->nq[0], 8, 0) <= kXstageSmemMax ? 8 : 4;
     for (int es : {8, 4})
-        for (int mode = 0; mode < 6; ++mode)
+        for (int mode = 0; mode < 7; ++mode)
             for (int L : {2, 4, 8})
                 if (xstage_mode_valid(es, h->n[0], h->nq[0], L, mode))
                     smem = std::max(smem, xstage_smem_bytes(es, h->n[0], h->nq[0], L, mode));
@@ -874,10 +975,14 @@ int tune_xstage(mfwq_handle h, bool f32, int* err) {
     int best_mode = 0, best_L = 4, best_R = 1, best_carve = 0;
     c.srows = 1;
     for (int carve = 0; carve < 2 && *err == MFWQ_OK; ++carve)
-        for (int mode = 0; mode < 6 && *err == MFWQ_OK; ++mode)
+        for (int mode = 0; mode < 7 && *err == MFWQ_OK; ++mode)
             for (int L : {2, 4, 8}) {
-                if ((mode < 4 && L > h->max_xlines) || !xstage_mode_valid((int)sizeof(T), h->n[0], h->nq[0], L, mode))
+                // modes 4-6 fix their lines per block; they are timed once (code digit 8)
+                if (mode >= 4 && L != 8) continue;
+                const int Lv = mode == 6 ? 8 : L;
+                if ((mode < 4 && L > h->max_xlines) || !xstage_mode_valid((int)sizeof(T), h->n[0], h->nq[0], Lv, mode))
                     continue;
+                if (mode == 6 && (carve || !(f32 ? h->d32[0].SX.ok : h->d64[0].SX.ok))) continue;
                 c.xlines = L;
                 c.xmode = mode;
                 c.xcarve = carve;

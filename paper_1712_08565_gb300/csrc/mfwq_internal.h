@@ -84,12 +84,34 @@ struct TileD {
     MFWQ_HD const T* pair(int f, int u, int k) const { return val + (((size_t)f * width + u) * ntile + k) * 2; }
 };
 
+// Translation-invariant interior of a direction's B and W bands (uniform
+// knots): interior points q_lo <= q < q_hi come in pairs q_lo + 2k + phase
+// whose rows are the phase's representative row shifted by k columns;
+// interior outputs i_lo <= i < i_hi are the representative W row shifted by
+// 2 points per output.  Filters are zero-padded to the fixed tap counts
+// P + 2 (a pair's union window) and 2P + 1; the host guarantees that every
+// fixed-size window stays inside the band's columns.
+constexpr int kStencilMaxP = 8;
+
+template <typename T>
+struct StencilD {
+    int ok;               // 1: the tables below are valid for degree P
+    int P;
+    int q_lo, q_hi;       // interior points, an even count
+    int jb;               // first column of pair 0's union window
+    int i_lo, i_hi;       // interior outputs
+    int qw;               // first point of output i_lo's window
+    T bf[2][2][kStencilMaxP + 2];  // [family][phase][t] on the pair's union window
+    T wf[4][2 * kStencilMaxP + 1];  // [family][t]
+};
+
 template <typename T>
 struct DirD {
     int n, nq, ng;
     BandD<T> B, BT, W, WT, GT;
     BandD<T> E;       // B-spline values and derivatives at the error points
     TileD<T> BX, WX;  // B and W in two-row tiles (the tiled x stage)
+    StencilD<T> SX;   // translation-invariant interior of B and W (the stencil x stage)
     int ne;           // error points
     const double* xe; // error points and weights (always FP64)
     const double* we;

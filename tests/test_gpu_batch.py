@@ -149,12 +149,63 @@ def test_every_fp32_xstage_variant(mf, tmp_path, mode, lines):
     op.close()
 
 
+@pytest.mark.parametrize("p,nel", [(2, (21, 6, 5)), (3, (18, 5, 6)), (4, (17, 6, 4)), (5, (20, 4, 5)),
+                                   (6, (19, 4, 4)), (7, (22, 3, 4)), (8, (24, 3, 3))])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_stencil_xstage(mf, tmp_path, p, nel, prec):
+    """The stencil mapping (code 68: mode 6) on uniform knots, p = 2..8: interior
+    filters from the translation-invariant rows, boundary rows from the band
+    tables, 16 lines per block with a partial last block."""
+    knots = [inputs.open_uniform_knots(p, nel[l]) for l in range(3)]
+    op = mf.Operator(p, knots, mixed=(prec == "fp32"), device=DEV)
+    tabs = [O.tables_1d(knots[l], p) for l in range(3)]
+    C6 = O.coefficient_grid(tabs, "ring", inputs.fourier_modes(6), 0.3)
+    op.set_coeff(torch.from_numpy(np.ascontiguousarray(C6)).to(DEV))
+    cache = str(tmp_path / "stencil.jsonl")
+    base = "xstage p=%d n1=%d nq1=%d nq2=%d nq3=%d" % (p, op.n[0], op.nq[0], op.nq[1], op.nq[2])
+    with open(cache, "w") as fh:
+        fh.write('{"key": "%s fp64", "xstage": 68}\n{"key": "%s fp32", "xstage": 68}\n' % (base, base))
+    op.autotune(cache)
+    x = inputs.uniform_vector(op.shape, 11 + p)
+    ref = O.apply_alg2(tabs, O.full_coeff(C6), x)
+    if prec == "fp64":
+        y = op.apply(torch.from_numpy(x).to(DEV)).cpu().numpy()
+        assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    else:
+        y = op.apply_f32(torch.from_numpy(x).float().to(DEV)).double().cpu().numpy()
+        assert np.abs(y - ref).max() <= 1e-5 * np.abs(ref).max()
+    op.close()
+
+
+def test_stencil_xstage_falls_back_on_graded_knots(mf, tmp_path):
+    """Jittered knots have no translation-invariant interior: a forced stencil
+    code runs the plain mapping and the apply still matches the oracle."""
+    p = 3
+    knots = [inputs.jittered_knots(p, 9, seed=4), inputs.open_uniform_knots(p, 4), inputs.open_uniform_knots(p, 5)]
+    op = mf.Operator(p, knots, mixed=True, device=DEV)
+    tabs = [O.tables_1d(knots[l], p) for l in range(3)]
+    C6 = O.coefficient_grid(tabs, "ring")
+    op.set_coeff(torch.from_numpy(np.ascontiguousarray(C6)).to(DEV))
+    cache = str(tmp_path / "stencil_fallback.jsonl")
+    base = "xstage p=%d n1=%d nq1=%d nq2=%d nq3=%d" % (p, op.n[0], op.nq[0], op.nq[1], op.nq[2])
+    with open(cache, "w") as fh:
+        fh.write('{"key": "%s fp64", "xstage": 68}\n{"key": "%s fp32", "xstage": 68}\n' % (base, base))
+    op.autotune(cache)
+    x = inputs.uniform_vector(op.shape, 12)
+    ref = O.apply_alg2(tabs, O.full_coeff(C6), x)
+    y = op.apply(torch.from_numpy(x).to(DEV)).cpu().numpy()
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    y32 = op.apply_f32(torch.from_numpy(x).float().to(DEV)).double().cpu().numpy()
+    assert np.abs(y32 - ref).max() <= 1e-5 * np.abs(ref).max()
+    op.close()
+
+
 def test_autotune_keeps_parity(mf, tmp_path):
     p, nel = 4, (9, 8, 10)
     op = _patch(mf, p, nel, 2)
     cache = str(tmp_path / "tune.jsonl")
     L = op.autotune(cache)
-    assert L % 10 in (2, 4, 8) and (L // 10) % 10 in (0, 1, 2, 3, 4, 5) and (L // 100) % 10 in (1, 2, 4)
+    assert L % 10 in (2, 4, 8) and (L // 10) % 10 in (0, 1, 2, 3, 4, 5, 6) and (L // 100) % 10 in (1, 2, 4)
     assert L // 1000 in (0, 1)
     assert os.path.exists(cache) and '"xstage": %d' % L in open(cache).read()
     assert op.autotune(cache) == L  # cache hit
