@@ -57,7 +57,8 @@ def parse():
                     help="run the k-refinement experiment of Section 4 (Table 1) for the given comma-separated "
                          "elements per direction (e.g. 16,32,64,128,256), p = 2..10, and print its table as JSON")
     ap.add_argument("--table1-p", default="2,3,4,5,6,7,8,9,10", help="degrees for --table1")
-    ap.add_argument("--kernel-run", choices=["apply", "apply_T", "fd64", "fdtc", "fdbf16", "apply32"], default=None,
+    ap.add_argument("--kernel-run", choices=["apply", "apply_T", "fd64", "fdtc", "fdbf16", "apply32", "mixed_solve"],
+                    default=None,
                     help="set up the workload, run one operator 3 times and exit (target for ncu captures)")
     return ap.parse_args()
 
@@ -601,11 +602,20 @@ def kernel_run(which, nel_override=None):
     from paper_1712_08565_gb300 import mfwq as mf
     from paper_1712_08565_gb300 import inputs
     dev = torch.device("cuda", 0)
-    mixed = which in ("fdtc", "fdbf16", "apply32")
+    mixed = which in ("fdtc", "fdbf16", "apply32", "mixed_solve")
     p, nel = (MIXED["p"], MIXED["nel"]) if mixed else (WORKLOAD["p"], WORKLOAD["nel"])
     if nel_override:
         nel = tuple(int(v) for v in nel_override.split(","))
     op, _ = make_op(mf, p, nel, mixed=mixed, fd="bf16" if which == "fdbf16" else "tf32", device=dev)
+    if which == "mixed_solve":  # one warm-up and one measured mixed-precision solve to 1e-8
+        f = op.load_vector("ring", "sines")
+        for _ in range(2):
+            u, info = op.solve(f, rtol=MIXED["rtol"])
+        op.sync()
+        print(f"kernel-run mixed_solve ok: N={op.N}, iterations={info.iterations}, outer={info.outer_iterations}, "
+              f"residual={info.rel_residual:.3e}")
+        op.close()
+        return 0
     x = torch.from_numpy(inputs.uniform_vector(op.shape, 1)).to(dev)
     if mixed:
         x = x.float()
