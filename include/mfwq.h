@@ -309,6 +309,16 @@ void mfwq_batch_destroy(mfwq_batch b);
 int mfwq_batch_solve(mfwq_batch b, const double* const* f_dev, double* const* u_dev, const mfwq_solve_opts* opts,
                      mfwq_solve_info* infos);
 
+/* ---- self-test of the bounded device waits (no counterpart in the paper) ---
+ * Every wait of the library's kernels on an asynchronous copy or MMA is
+ * bounded; on timeout the kernel records it in the handle's error word (read
+ * by mfwq_sync as MFWQ_ETIMEOUT) and returns.  This call runs that machinery
+ * on purpose: one block arms an mbarrier for 16 bytes that no copy delivers
+ * and waits at most limit_cycles (1 .. ~4e9 SM cycles) on `stream` (may be
+ * NULL).  Returns MFWQ_ETIMEOUT when the wait gave up as designed (the
+ * context stays usable), MFWQ_EINTERNAL if it did not.  Synchronous. */
+int mfwq_selftest_bounded_wait(long long limit_cycles, void* stream);
+
 /* ---- instrumentation (no counterpart in the paper) -------------------------
  * Kernel stages, in the index order of mfwq_profile_stats: trial_z, trial_y,
  * xstage, test_y, test_z (the five stages of the apply), test_zT, test_yT,

@@ -31,11 +31,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity) {
     return ok != 0;
 }
 
-// Bounded wait for the phase with the given parity: false after kWaitCycles.
-__device__ inline bool mbar_wait(uint32_t a, uint32_t parity) {
+// Bounded wait for the phase with the given parity: false after `limit`
+// cycles (kWaitCycles unless a caller asks for less).
+__device__ inline bool mbar_wait(uint32_t a, uint32_t parity, long long limit = kWaitCycles) {
     const long long t0 = clock64();
     while (!mbar_try_wait(a, parity)) {
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }

@@ -111,6 +111,7 @@ _SIGS = [
     ("mfwq_batch_destroy", None, [ctypes.c_void_p]),
     ("mfwq_batch_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfoC)]),
+    ("mfwq_selftest_bounded_wait", ctypes.c_int, [ctypes.c_longlong, ctypes.c_void_p]),
     ("mfwq_fd_precond_noalloc", ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p),
                                                ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
