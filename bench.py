@@ -15,8 +15,10 @@ flush is needed between steps.
 value = MF-WQ apply throughput delivered inside the solve: N x (operator
 applies per solve) / (time per solve), in DoF/s.  The line also carries the
 solve time and iteration count, the isolated apply and FD times, the apply
-DoF/s for p = 2..6 at 128 elements, and the mixed-precision versus FP64 solve
-to 1e-8 on the p = 6, 192-element ring.
+DoF/s for p = 2..6 at 128 elements, the mixed-precision versus FP64 solve to
+1e-8 on the p = 6, 192-element ring, the 64-patch batched solves, the
+reaction term, and the transposed apply / coefficient gradient on the
+adjoint workload (ring p = 3, 64 elements, K = exp(0.3 g) I).
 """
 from __future__ import annotations
 
@@ -355,6 +357,64 @@ def reaction(mf, device, alpha=10.0):
     return out
 
 
+ADJOINT = dict(name="ring-p3-nel64-kexp", p=3, nel=64, kscale=0.3, modes_seed=123, rtol=1e-10)
+
+
+def adjoint(mf, device):
+    """Rows a9-a10 on the adjoint workload (ring p = 3, 64 elements, K =
+    exp(0.3 g) I): per-launch times of the transposed apply and of the
+    coefficient gradient with their FP64-pipe fractions, and the whole
+    gradient pipeline (forward solve, adjoint solve K~^T lam = u - u_t, dJ/dC)."""
+    import torch
+    from paper_1712_08565_gb300 import inputs
+    p, nel = ADJOINT["p"], ADJOINT["nel"]
+    modes = inputs.fourier_modes(ADJOINT["modes_seed"])
+    op, knots = make_op(mf, p, nel, device=device)
+    f = op.load_vector("ring", "sines")
+    u_t, _ = op.solve(f, rtol=ADJOINT["rtol"], maxit=1000)
+    op.set_coeff(op.eval_coeff("ring", modes, ADJOINT["kscale"]))
+    x = torch.from_numpy(inputs.uniform_vector(op.shape, 3)).to(device)
+    y = torch.empty_like(x)
+    g = torch.empty((6,) + op.qshape, dtype=torch.float64, device=device)
+    for _ in range(3):
+        op.apply_T(x, y)
+        op.grad_coeff(x, y, g)
+    op.profile(True)
+    op.profile_read(reset=True)
+    ms_T = event_time(op.stream, lambda: op.apply_T(x, y), 10)
+    ms_g = event_time(op.stream, lambda: op.grad_coeff(x, y, g), 10)
+    stages = op.profile_read(reset=True)
+    op.profile(False)
+    flops, n, nq = stage_flops(mf, p, knots)
+    per = {k: v[0] / v[1] for k, v in stages.items()}
+    peak = fp64_peak_tflops()
+    xT = per.get("xstage_T")
+    xg = per.get("xstage_grad")
+    Lgrad = flops["xstage"] - float(nq[2] * nq[1]) * 9.0 * nq[0] + float(nq[2] * nq[1]) * 12.0 * nq[0]
+
+    def pipeline():
+        u, i1 = op.solve(f, rtol=ADJOINT["rtol"], maxit=1000)
+        lam, i2 = op.solve_T(u - u_t, rtol=ADJOINT["rtol"], maxit=1000)
+        op.grad_coeff(lam, u, g)
+        return i1, i2
+
+    pipeline()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(op.stream)
+    i1, i2 = pipeline()
+    e1.record(op.stream)
+    e1.synchronize()
+    out = {"workload": ADJOINT["name"], "N": op.N, "apply_T_ms": ms_T, "grad_coeff_ms": ms_g,
+           "stages_ms_per_launch": {k: round(v, 5) for k, v in per.items()},
+           "xstage_T_fp64_pipe_frac": flops["xstage"] / (xT * 1e-3) / 1e12 / peak if xT else None,
+           "xstage_grad_fp64_pipe_frac": Lgrad / (xg * 1e-3) / 1e12 / peak if xg else None,
+           "gradient_pipeline_s": e0.elapsed_time(e1) / 1e3, "forward_iterations": i1.iterations,
+           "adjoint_iterations": i2.iterations}
+    op.close()
+    return out
+
+
 def mixed_vs_fp64(mf, device):
     import torch
     from paper_1712_08565_gb300 import inputs
@@ -562,6 +622,7 @@ def run_ours(args):
         extras["mixed_vs_fp64"] = mixed_vs_fp64(mf, device)
         extras["batched_64"] = batched(mf, device)
         extras["reaction"] = reaction(mf, device)
+        extras["adjoint"] = adjoint(mf, device)
     line = {
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",

@@ -1316,7 +1316,8 @@ void launch_stencil(const StencilD<T>& S, int nlines, size_t sm, cudaStream_t st
         case 5: k_xstage_stencil<T, 5><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
         case 6: k_xstage_stencil<T, 6><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
         case 7: k_xstage_stencil<T, 7><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
-        default: k_xstage_stencil<T, 8><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
+        case 8: k_xstage_stencil<T, 8><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
+        default: break;  // unreachable: the stencil tables exist only for P <= kStencilMaxP (checked at dispatch)
     }
 }
 
@@ -1360,7 +1361,7 @@ int run_apply(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
         int mode = c.xmode >= 0 && c.xmode <= 6 ? c.xmode : 0;
         if (mode >= 4) L = mode == 6 ? kStLines : kTileLines;
         if (!xstage_mode_valid((int)sizeof(T), n1, q1, L, mode) || (mode >= 2 && mode <= 3 && c.cs % 4 != 0) ||
-            (mode == 6 && !d1.SX.ok)) {
+            (mode == 6 && (!d1.SX.ok || d1.SX.P < 2 || d1.SX.P > kStencilMaxP))) {
             mode = 0;
             L = 4;
         }
