@@ -107,6 +107,11 @@ def test_mixed_196_cubed(mf):
     assert np.abs(z64 - ref).max() <= 1e-12 * np.abs(ref).max()
     z32 = op.fd_precond_f32(torch.from_numpy(r).float().to(DEV)).double().cpu().numpy()
     assert np.linalg.norm(z32 - ref) <= 1e-2 * np.linalg.norm(ref)
+    # the FP32 operator in its autotuned launch shape, sampled rows computed one by one
+    y32 = op.apply_f32(torch.from_numpy(r).float().to(DEV)).double().cpu().numpy()
+    rows32 = _rows(op.shape, 30, 5)
+    ref32 = O.apply_rows(tabs, O.coefficient_box_fn(tabs, "ring"), r, rows32)
+    assert np.abs(np.array([y32[q] for q in rows32]) - ref32).max() <= 1e-5 * np.abs(ref32).max()
     f = op.load_vector("ring", "sines")
     u, info = op.solve(f, rtol=1e-8, inner_rtol=1e-4)
     assert info.converged and info.rel_residual <= 1e-8
