@@ -59,7 +59,7 @@ def parse():
                     help="run the k-refinement experiment of Section 4 (Table 1) for the given comma-separated "
                          "elements per direction (e.g. 16,32,64,128,256), p = 2..10, and print its table as JSON")
     ap.add_argument("--table1-p", default="2,3,4,5,6,7,8,9,10", help="degrees for --table1")
-    ap.add_argument("--kernel-run", choices=["apply", "apply_T", "fd64", "fdtc", "fdbf16", "apply32", "mixed_solve"],
+    ap.add_argument("--kernel-run", choices=["apply", "apply_T", "grad", "fd64", "fdtc", "fdbf16", "apply32", "mixed_solve"],
                     default=None,
                     help="set up the workload, run one operator 3 times and exit (target for ncu captures)")
     return ap.parse_args()
@@ -681,6 +681,14 @@ def kernel_run(which, nel_override=None):
     if mixed:
         x = x.float()
     y = torch.empty_like(x)
+    if which == "grad":  # dJ/dC from two coefficient vectors
+        g = torch.empty((6,) + op.qshape, dtype=torch.float64, device=dev)
+        for _ in range(3):
+            op.grad_coeff(x, y.copy_(x), g)
+        op.sync()
+        print(f"kernel-run grad ok: N={op.N}, |g|={float(g.norm()):.6e}")
+        op.close()
+        return 0
     fn = {"apply": op.apply, "apply_T": op.apply_T, "fd64": op.fd_precond, "fdtc": op.fd_precond_f32,
           "fdbf16": op.fd_precond_f32, "apply32": op.apply_f32}[which]
     for _ in range(3):

@@ -884,10 +884,24 @@ __global__ void __launch_bounds__(kThreads) k_xstage_stencil(XArgs<T> a, Stencil
     st_beta<T, P, 2>(a, st, y2, tout, tstride, line0, nl, sY, sH);
 }
 
+// Threads of the transposed and gradient x stages: their heavy phase has one
+// item per (line, point), kLines * nq1 items, so the block takes as few
+// rounds of up to kAuxMaxThreads threads as those items need, with the items
+// spread evenly over the rounds (e.g. 532 items: two rounds of 288 threads
+// rather than three of 256).
+constexpr int kAuxMaxThreads = 512;
+
+static int aux_threads(int nq1) {
+    const int items = kLines * nq1;
+    const int rounds = (items + kAuxMaxThreads - 1) / kAuxMaxThreads;
+    const int per = (items + rounds - 1) / rounds;
+    return std::max(64, std::min(kAuxMaxThreads, (per + 31) / 32 * 32));
+}
+
 // Transposed x stage: R (9 inputs [line][n1]) -> S^(ab) = W1^T R at q1 ->
 // E_b = sum_a C_ab S^(ab) -> X_b = B1^(b)T E_b (3 outputs [line][n1]).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_xstage_applyT(XArgs<T> a, Ptr9<T> rin,
+__global__ void __launch_bounds__(kAuxMaxThreads) k_xstage_applyT(XArgs<T> a, Ptr9<T> rin,
                                                             T* __restrict__ x1, T* __restrict__ x2, T* __restrict__ x3,
                                                             const int* skip) {
     if (skip && *skip) return;
@@ -956,7 +970,7 @@ __global__ void __launch_bounds__(kThreads) k_xstage_applyT(XArgs<T> a, Ptr9<T> 
 // Gradient x stage: G_b from Y (trial partials of u), S^(ab) from R (test
 // partials of lambda); g_ab = -S^(ab) G_b folded into 6 symmetric slots.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_xstage_grad(XArgs<T> a, const T* __restrict__ y0, const T* __restrict__ y1,
+__global__ void __launch_bounds__(kAuxMaxThreads) k_xstage_grad(XArgs<T> a, const T* __restrict__ y0, const T* __restrict__ y1,
                                                           const T* __restrict__ y2, Ptr9<T> rin, T* __restrict__ g6) {
     extern __shared__ unsigned char smem_raw[];
     T* sY = reinterpret_cast<T*>(smem_raw);  // [3][kLines][n1]
@@ -1440,7 +1454,7 @@ int run_apply_T(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
         Ptr9<T> rp;
         for (int k = 0; k < 9; ++k) rp.p[k] = P + (3 + k) * SP;
         launch_begin(S_XSTAGE_T, c.stream);
-        k_xstage_applyT<T><<<grid, kThreads, sm, c.stream>>>(a, rp, P, P + SP, P + 2 * SP, skip);
+        k_xstage_applyT<T><<<grid, aux_threads(q1), sm, c.stream>>>(a, rp, P, P + SP, P + 2 * SP, skip);
         launch_end(S_XSTAGE_T, c.stream);
         if (cudaGetLastError() != cudaSuccess) return MFWQ_ECUDA;
         if (c.cm) {  // reaction term: X1 += B1^(0)T (c W1^(00)T R^(11))
@@ -1483,7 +1497,7 @@ int run_grad(const OpCtx<T>& c, const T* lam, const T* u, T* g6) {
     Ptr9<T> rp;
     for (int k = 0; k < 9; ++k) rp.p[k] = P + (3 + k) * SP;
     launch_begin(S_XSTAGE_GRAD, c.stream);
-    k_xstage_grad<T><<<grid, kThreads, sm, c.stream>>>(a, P, P + SP, P + 2 * SP, rp, g6);
+    k_xstage_grad<T><<<grid, aux_threads(d1.nq), sm, c.stream>>>(a, P, P + SP, P + 2 * SP, rp, g6);
     launch_end(S_XSTAGE_GRAD, c.stream);
     if (cudaGetLastError() != cudaSuccess) return MFWQ_ECUDA;
     (void)n3;
