@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "kernels.h"
@@ -1615,10 +1616,14 @@ static cudaError_t set_stencil_smem(int bytes) {
 }
 
 // The dynamic shared-memory limit is a per-kernel attribute shared by all
-// handles, so it only ever grows.
+// handles on a device, so it only ever grows (one record per device).
 int configure_xstage_smem(int bytes) {
-    static int configured = 0;
-    if (bytes <= configured) return MFWQ_OK;
+    static std::mutex mu;
+    static int configured[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return MFWQ_ECUDA;
+    std::lock_guard<std::mutex> lk(mu);
+    if (bytes <= configured[dev]) return MFWQ_OK;
     cudaError_t e = cudaSuccess;
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
     e = set_xstage_smem_all<0>(bytes);
@@ -1633,7 +1638,7 @@ int configure_xstage_smem(int bytes) {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mass_xT<double>, A, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mass_xT<float>, A, bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_mass_grad<double>, A, bytes);
-    if (e == cudaSuccess) configured = bytes;
+    if (e == cudaSuccess) configured[dev] = bytes;
     return e == cudaSuccess ? MFWQ_OK : MFWQ_ECUDA;
 }
 
