@@ -793,30 +793,43 @@ __device__ __forceinline__ void st_beta(const XArgs<T>& a, const StencilD<T>& st
         for (int j = lane; j < n1; j += 32) sY[ll * rY + j] = ll < nl ? src[j] : T(0);
     }
     __syncthreads();
-    // trial, interior pairs: warp-sized chunks of consecutive pairs of one line
+    // trial, interior pairs: warp-sized chunks of consecutive pairs of one
+    // line; a warp takes two chunks per pass and loads both chunks'
+    // coefficients before computing, so twelve loads per lane are in flight
     const int npairs = (st.q_hi - st.q_lo) >> 1;
     const int nch = (npairs + 31) >> 5;
-    for (int it = warp, ll = 0, ch = warp; it < kStLines * nch; it += nwarps, ch += nwarps) {
-        while (ch >= nch) {  // (line, chunk) of item it without a division
-            ch -= nch;
-            ++ll;
+    const int nitems = kStLines * nch;
+    for (int it0 = warp; it0 < nitems; it0 += 2 * nwarps) {
+        T c[2][6];
+        int ll[2], kk[2];
+        bool ok[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int it = it0 + h * nwarps;
+            ll[h] = it / nch;  // one division per chunk of 32 pairs
+            kk[h] = ((it - ll[h] * nch) << 5) + lane;
+            ok[h] = it < nitems && kk[h] < npairs;
+            const bool live = ok[h] && ll[h] < nl;
+            const T* C = a.C + (size_t)(line0 + (live ? ll[h] : 0)) * nq1 + st.q_lo + 2 * (live ? kk[h] : 0);
+            c[h][0] = live ? C[(size_t)c0 * a.cs] : T(0);
+            c[h][1] = live ? C[(size_t)c0 * a.cs + 1] : T(0);
+            c[h][2] = live ? C[(size_t)c1 * a.cs] : T(0);
+            c[h][3] = live ? C[(size_t)c1 * a.cs + 1] : T(0);
+            c[h][4] = live ? C[(size_t)c2 * a.cs] : T(0);
+            c[h][5] = live ? C[(size_t)c2 * a.cs + 1] : T(0);
         }
-        const int k = (ch << 5) + lane;
-        if (k >= npairs) continue;
-        T g0, g1;
-        st_pair<T, P, BF>(st, sY + ll * rY + st.jb + k, g0, g1);
-        const int q = st.q_lo + 2 * k;
-        T* H = sH + ll * rG + q;
-        if (ll < nl) {
-            const T* C = a.C + (size_t)(line0 + ll) * nq1 + q;
-            H[0] = C[(size_t)c0 * a.cs] * g0;
-            H[1] = C[(size_t)c0 * a.cs + 1] * g1;
-            H[kStLines * rG] = C[(size_t)c1 * a.cs] * g0;
-            H[kStLines * rG + 1] = C[(size_t)c1 * a.cs + 1] * g1;
-            H[2 * kStLines * rG] = C[(size_t)c2 * a.cs] * g0;
-            H[2 * kStLines * rG + 1] = C[(size_t)c2 * a.cs + 1] * g1;
-        } else {
-            H[0] = H[1] = H[kStLines * rG] = H[kStLines * rG + 1] = H[2 * kStLines * rG] = H[2 * kStLines * rG + 1] = 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!ok[h]) continue;
+            T g0, g1;
+            st_pair<T, P, BF>(st, sY + ll[h] * rY + st.jb + kk[h], g0, g1);
+            T* H = sH + ll[h] * rG + st.q_lo + 2 * kk[h];
+            H[0] = c[h][0] * g0;
+            H[1] = c[h][1] * g1;
+            H[kStLines * rG] = c[h][2] * g0;
+            H[kStLines * rG + 1] = c[h][3] * g1;
+            H[2 * kStLines * rG] = c[h][4] * g0;
+            H[2 * kStLines * rG + 1] = c[h][5] * g1;
         }
     }
     // trial, boundary points: one item per (line, point)

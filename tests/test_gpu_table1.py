@@ -91,3 +91,30 @@ def test_table1_coarse_levels_on_gpu(mf, p):
         op.close()
     assert 0.2 < errs[0] < 1.2
     assert table[p][1] / 1.5 < errs[1] < table[p][1] * 1.5
+
+
+@pytest.mark.parametrize("p", [9, 10])
+def test_high_degree_apply_and_fd(mf, p):
+    """The degrees of Table 1's last rows: apply, transposed apply and FD
+    against the oracle (weights in extended precision on both sides)."""
+    nel = (12, 11, 13)
+    knots = [inputs.open_uniform_knots(p, n) for n in nel]
+    tabs = [O.tables_1d(knots[l], p) for l in range(3)]
+    op = _op(mf, p, knots, "ring")
+    x = inputs.uniform_vector(op.shape, 80 + p)
+    C6 = O.coefficient_grid(tabs, "ring")
+    ref = O.apply_alg2(tabs, O.full_coeff(C6), x)
+    y = op.apply(torch.from_numpy(x).to(DEV)).cpu().numpy()
+    assert np.abs(y - ref).max() <= 1e-12 * np.abs(ref).max()
+    refT = O.apply_T_alg2(tabs, O.full_coeff(C6), x)
+    yT = op.apply_T(torch.from_numpy(x).to(DEV)).cpu().numpy()
+    assert np.abs(yT - refT).max() <= 1e-12 * np.abs(refT).max()
+    z = op.fd_precond(torch.from_numpy(x).to(DEV)).cpu().numpy()
+    fd = O.fd_setup(tabs)
+    zr = O.fd_apply(fd, x)
+    # The FD factors solve K_l u = lambda M_l u; at p = 9, 10 cond(M_l) reaches
+    # 1e4 (4.1e4 at p = 10 on 12 elements), and two correct eigensolvers
+    # agree only to about eps * cond(M_l), so the bound scales with it.
+    tol = max(1e-12, 10 * np.finfo(float).eps * max(np.linalg.cond(M) for M in fd.M))
+    assert np.abs(z - zr).max() <= tol * np.abs(zr).max()
+    op.close()
