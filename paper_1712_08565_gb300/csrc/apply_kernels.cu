@@ -744,6 +744,7 @@ __global__ void __launch_bounds__(kThreads) k_xstage_tiled(XArgs<T> a, const T* 
 //  outputs staged in shared memory (aliasing Y) and written out coalesced.
 constexpr int kStLines = 8;  // the (line, alpha) lane map and the copy-out assume 8
 constexpr int kSeg = 8;
+constexpr int kStUnroll = 2;  // chunks of 32 pairs per warp pass in the stencil trial (4 measured no faster)
 static_assert(kStLines == 8, "stencil x stage: 3 x 8 (line, alpha) lanes per warp");
 
 // row stride >= n with stride = 1 (mod 32)
@@ -794,17 +795,17 @@ __device__ __forceinline__ void st_beta(const XArgs<T>& a, const StencilD<T>& st
     }
     __syncthreads();
     // trial, interior pairs: warp-sized chunks of consecutive pairs of one
-    // line; a warp takes two chunks per pass and loads both chunks'
-    // coefficients before computing, so twelve loads per lane are in flight
+    // line; a warp takes kStUnroll chunks per pass and loads all their
+    // coefficients before computing, so 6 kStUnroll loads per lane are in flight
     const int npairs = (st.q_hi - st.q_lo) >> 1;
     const int nch = (npairs + 31) >> 5;
     const int nitems = kStLines * nch;
-    for (int it0 = warp; it0 < nitems; it0 += 2 * nwarps) {
-        T c[2][6];
-        int ll[2], kk[2];
-        bool ok[2];
+    for (int it0 = warp; it0 < nitems; it0 += kStUnroll * nwarps) {
+        T c[kStUnroll][6];
+        int ll[kStUnroll], kk[kStUnroll];
+        bool ok[kStUnroll];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < kStUnroll; ++h) {
             const int it = it0 + h * nwarps;
             ll[h] = it / nch;  // one division per chunk of 32 pairs
             kk[h] = ((it - ll[h] * nch) << 5) + lane;
@@ -819,7 +820,7 @@ __device__ __forceinline__ void st_beta(const XArgs<T>& a, const StencilD<T>& st
             c[h][5] = live ? C[(size_t)c2 * a.cs + 1] : T(0);
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < kStUnroll; ++h) {
             if (!ok[h]) continue;
             T g0, g1;
             st_pair<T, P, BF>(st, sY + ll[h] * rY + st.jb + kk[h], g0, g1);
