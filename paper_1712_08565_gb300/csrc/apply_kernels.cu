@@ -453,16 +453,23 @@ __global__ void __launch_bounds__(kThreads) k_xstage_apply(XArgs<T> a, const T* 
         const int c1 = b == 1 ? 1 : 3 + b;
         const int c2 = b == 2 ? 2 : 4 + b;
         if (MAP == 0) {
+            // points in parity order (even q, then odd q): interior points of one
+            // parity have bands of one length, so a warp's lanes leave the tap loop together
+            const int half = (nq1 + 1) >> 1;
             for (int e = threadIdx.x; e < nl * nq1; e += blockDim.x) {
-                const int l = e / nq1, q = e - l * nq1;
+                const int l = e / nq1, r = e - l * nq1;
+                const int q = r < half ? 2 * r : 2 * (r - half) + 1;
                 const int s = a.B.start[q], L = a.B.len[q];
+                // the three coefficients are loaded before the tap loop, so their
+                // latency overlaps it
+                const T k0 = cval(c0, l, q), k1 = cval(c1, l, q), k2 = cval(c2, l, q);
                 const T* Y = sY + (b * LINES + l) * n1 + s;
                 T g = 0;
                 for (int t = 0; t < L; ++t) g = fmaT(a.B.lane(bfam, q, t), Y[t], g);
                 T* H = sH + l * nq1 + q;
-                H[0 * hs] = cval(c0, l, q) * g;
-                H[1 * hs] = cval(c1, l, q) * g;
-                H[2 * hs] = cval(c2, l, q) * g;
+                H[0 * hs] = k0 * g;
+                H[1 * hs] = k1 * g;
+                H[2 * hs] = k2 * g;
             }
         } else {
             for (int q = threadIdx.x; q < nq1; q += blockDim.x) {
