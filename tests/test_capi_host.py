@@ -116,3 +116,26 @@ def test_binding_refuses_without_gpu_tensor(libpath):
     torch = pytest.importorskip("torch")
     with pytest.raises((TypeError, ValueError)):
         mfwq._ptr(torch.zeros(4, dtype=torch.float64), torch.float64)
+
+
+def _c_driver_build(out):
+    """Compile tests/c_driver/solve_ring.c against include/mfwq.h and link it
+    with libmfwq.so and the CUDA runtime; returns the command's result."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    if cc is None or not os.path.exists(os.path.join(cuda, "include", "cuda_runtime.h")):
+        pytest.skip("no C compiler or CUDA headers")
+    pkg = os.path.join(ROOT, "paper_1712_08565_gb300")
+    libdirs = [d for d in (os.path.join(cuda, "lib64"), os.path.join(cuda, "lib")) if os.path.isdir(d)]
+    cmd = [cc, "-std=c99", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+           "-I", os.path.join(cuda, "include"), os.path.join(ROOT, "tests", "c_driver", "solve_ring.c"),
+           "-L", pkg, "-lmfwq"] + [f"-L{d}" for d in libdirs] + ["-lcudart", "-o", out]
+    return subprocess.run(cmd, capture_output=True, text=True)
+
+
+def test_c_driver_compiles_and_links(tmp_path):
+    """The C ABI is usable from plain C: the driver builds warning-free."""
+    r = _c_driver_build(str(tmp_path / "solve_ring"))
+    assert r.returncode == 0, r.stderr
