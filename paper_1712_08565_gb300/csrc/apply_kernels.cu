@@ -857,22 +857,40 @@ __device__ __forceinline__ void st_beta(const XArgs<T>& a, const StencilD<T>& st
             H[2 * kStLines * rG] = live ? a.C[(size_t)c2 * a.cs + cb] * g : T(0);
         }
     __syncthreads();
-    // test: lane = (line l, alpha al) for lane < 24
+    // test: lane = (line l, alpha al) for lane < 24 (FP32, conflict-free banks);
+    // FP64 interior segments use all 32 lanes (below)
     const int nseg = (st.i_hi - st.i_lo) / kSeg;
     const int i_st = st.i_lo + nseg * kSeg;
     const int nbi = st.i_lo + (n1 - i_st);
     const int rT = rY;
     T* sT = sY;  // [3 alpha][8][rT]: outputs of this beta (Y no longer needed)
+    if (sizeof(T) == 8) {
+        // FP64 is bound by the FP64 pipe, not by shared-memory banks: all 32
+        // lanes work, as (line l, segment offset s4) for one alpha per warp pass
+        const int l = lane & 7, s4 = lane >> 3;
+        const int nm = (nseg + 3) >> 2;
+        for (int it = warp; it < 3 * nm; it += nwarps) {
+            const int al = it / nm, sg = 4 * (it - al * nm) + s4;
+            if (sg >= nseg) continue;
+            T w[NW];
+#pragma unroll
+            for (int t = 0; t < NW; ++t) w[t] = al == 0 ? st.wf[2 + BF][t] : st.wf[BF][t];
+            st_seg<T, P>(w, sH + (al * kStLines + l) * rG + st.qw + 2 * kSeg * sg,
+                         sT + (al * kStLines + l) * rT + st.i_lo + kSeg * sg);
+        }
+    }
     if (lane < 3 * kStLines) {
         const int al = lane >> 3, l = lane & 7;
         const int fam = al == 0 ? 2 + BF : BF;
-        T w[NW];
-#pragma unroll
-        for (int t = 0; t < NW; ++t) w[t] = al == 0 ? st.wf[2 + BF][t] : st.wf[BF][t];
         const T* Hl = sH + (al * kStLines + l) * rG;
         T* To = sT + (al * kStLines + l) * rT;
-        for (int sg = warp; sg < nseg; sg += nwarps)
-            st_seg<T, P>(w, Hl + st.qw + 2 * kSeg * sg, To + st.i_lo + kSeg * sg);
+        if (sizeof(T) != 8) {
+            T w[NW];
+#pragma unroll
+            for (int t = 0; t < NW; ++t) w[t] = al == 0 ? st.wf[2 + BF][t] : st.wf[BF][t];
+            for (int sg = warp; sg < nseg; sg += nwarps)
+                st_seg<T, P>(w, Hl + st.qw + 2 * kSeg * sg, To + st.i_lo + kSeg * sg);
+        }
         for (int k = warp; k < nbi; k += nwarps) {
             const int i = k < st.i_lo ? k : i_st + (k - st.i_lo);
             const int s0 = a.W.start[i], L = a.W.len[i];
