@@ -666,7 +666,10 @@ def kernel_run(which, nel_override=None):
     mixed = which in ("fdtc", "fdbf16", "apply32", "mixed_solve")
     p, nel = (MIXED["p"], MIXED["nel"]) if mixed else (WORKLOAD["p"], WORKLOAD["nel"])
     if nel_override:
-        nel = tuple(int(v) for v in nel_override.split(","))
+        vals = tuple(int(v) for v in nel_override.split(","))
+        if len(vals) not in (1, 3):
+            raise SystemExit("--kernel-nel takes one value or three (per direction)")
+        nel = vals[0] if len(vals) == 1 else vals
     op, _ = make_op(mf, p, nel, mixed=mixed, fd="bf16" if which == "fdbf16" else "tf32", device=dev)
     if which == "mixed_solve":  # one warm-up and one measured mixed-precision solve to 1e-8
         f = op.load_vector("ring", "sines")
