@@ -54,5 +54,24 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                  : "memory");
 }
 
+// Hint to the copy engine: bring [p, p + bytes) into L2 (cp.async.bulk.prefetch.L2);
+// p 16-byte aligned, bytes a multiple of 16.  No completion, no effect on results.
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(reinterpret_cast<uint64_t>(p)), "r"(bytes)
+                 : "memory");
+}
+
+// The same for any byte range: only its 16-byte-aligned interior is prefetched,
+// so nothing outside [begin, begin + bytes) is touched; pieces of at most 64 KB.
+__device__ inline void prefetch_l2_range(const void* begin, size_t bytes) {
+    uint64_t a = (reinterpret_cast<uint64_t>(begin) + 15) & ~uint64_t(15);
+    const uint64_t e = (reinterpret_cast<uint64_t>(begin) + bytes) & ~uint64_t(15);
+    while (a < e) {
+        const uint32_t n = (uint32_t)(e - a < 65536 ? e - a : 65536);
+        prefetch_l2(reinterpret_cast<const void*>(a), n);
+        a += n;
+    }
+}
+
 }  // namespace ptx
 }  // namespace mfwq

@@ -421,6 +421,7 @@ constexpr int kStLines = 8;  // the (line, alpha) lane map and the copy-out assu
 constexpr int kSeg = 8;
 constexpr int kStUnroll = 2;  // chunks of 32 pairs per warp pass in the stencil trial (4 measured no faster)
 static_assert(kStLines == 8, "stencil x stage: 3 x 8 (line, alpha) lanes per warp");
+static_assert(kThreads / 32 == kStLines, "stencil x stage: one warp per line in the trial");
 
 // row stride >= n with stride = 1 (mod 32)
 __host__ __device__ inline int st_stride(int n) { return ((n + 30) / 32) * 32 + 1; }
@@ -461,72 +462,71 @@ __device__ __forceinline__ void st_beta(const XArgs<T>& a, const StencilD<T>& st
     constexpr int NW = 2 * P + 1;
     const int n1 = a.n1, nq1 = a.nq1;
     const int rY = st_stride(n1), rG = st_stride(nq1);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c0 = BETA == 0 ? 0 : 2 + BETA, c1 = BETA == 1 ? 1 : 3 + BETA, c2 = BETA == 2 ? 2 : 4 + BETA;
+    // warp w owns line w in the load and trial phases (kStLines warps)
+    const bool live = warp < nl;
     __syncthreads();  // previous beta's outputs copied out of sY
-    for (int ll = warp; ll < kStLines; ll += nwarps) {
-        const T* src = yb + (size_t)(line0 + ll) * n1;
-        for (int j = lane; j < n1; j += 32) sY[ll * rY + j] = ll < nl ? src[j] : T(0);
+    {
+        const T* src = yb + (size_t)(line0 + (live ? warp : 0)) * n1;
+        for (int j = lane; j < n1; j += 32) sY[warp * rY + j] = live ? src[j] : T(0);
     }
     __syncthreads();
-    // trial, interior pairs: warp-sized chunks of consecutive pairs of one
-    // line; a warp takes kStUnroll chunks per pass and loads all their
-    // coefficients before computing, so 6 kStUnroll loads per lane are in flight
-    const int npairs = (st.q_hi - st.q_lo) >> 1;
-    const int nch = (npairs + 31) >> 5;
-    const int nitems = kStLines * nch;
-    for (int it0 = warp; it0 < nitems; it0 += kStUnroll * nwarps) {
-        T c[kStUnroll][6];
-        int ll[kStUnroll], kk[kStUnroll];
-        bool ok[kStUnroll];
+    if (live) {
+        // trial, interior pairs: lane = pair k of the chunk; the three
+        // coefficient rows advance by 64 points per chunk; kStUnroll chunks
+        // load their 6 coefficients each before any is used
+        const int npairs = (st.q_hi - st.q_lo) >> 1;
+        const size_t cl = (size_t)(line0 + warp) * nq1 + st.q_lo + 2 * lane;
+        const T* C0 = a.C + (size_t)c0 * a.cs + cl;
+        const T* C1 = a.C + (size_t)c1 * a.cs + cl;
+        const T* C2 = a.C + (size_t)c2 * a.cs + cl;
+        const T* Yl = sY + warp * rY + st.jb + lane;
+        T* Hl = sH + warp * rG + st.q_lo + 2 * lane;
+        for (int k0 = 0; k0 < npairs; k0 += 32 * kStUnroll) {
+            T c[kStUnroll][6];
 #pragma unroll
-        for (int h = 0; h < kStUnroll; ++h) {
-            const int it = it0 + h * nwarps;
-            ll[h] = it / nch;  // one division per chunk of 32 pairs
-            kk[h] = ((it - ll[h] * nch) << 5) + lane;
-            ok[h] = it < nitems && kk[h] < npairs;
-            const bool live = ok[h] && ll[h] < nl;
-            const T* C = a.C + (size_t)(line0 + (live ? ll[h] : 0)) * nq1 + st.q_lo + 2 * (live ? kk[h] : 0);
-            c[h][0] = live ? C[(size_t)c0 * a.cs] : T(0);
-            c[h][1] = live ? C[(size_t)c0 * a.cs + 1] : T(0);
-            c[h][2] = live ? C[(size_t)c1 * a.cs] : T(0);
-            c[h][3] = live ? C[(size_t)c1 * a.cs + 1] : T(0);
-            c[h][4] = live ? C[(size_t)c2 * a.cs] : T(0);
-            c[h][5] = live ? C[(size_t)c2 * a.cs + 1] : T(0);
-        }
+            for (int h = 0; h < kStUnroll; ++h) {
+                const int o = 2 * (k0 + 32 * h);
+                const bool ok = k0 + 32 * h + lane < npairs;
+                c[h][0] = ok ? C0[o] : T(0);
+                c[h][1] = ok ? C0[o + 1] : T(0);
+                c[h][2] = ok ? C1[o] : T(0);
+                c[h][3] = ok ? C1[o + 1] : T(0);
+                c[h][4] = ok ? C2[o] : T(0);
+                c[h][5] = ok ? C2[o + 1] : T(0);
+            }
 #pragma unroll
-        for (int h = 0; h < kStUnroll; ++h) {
-            if (!ok[h]) continue;
-            T g0, g1;
-            st_pair<T, P, BF>(st, sY + ll[h] * rY + st.jb + kk[h], g0, g1);
-            T* H = sH + ll[h] * rG + st.q_lo + 2 * kk[h];
-            H[0] = c[h][0] * g0;
-            H[1] = c[h][1] * g1;
-            H[kStLines * rG] = c[h][2] * g0;
-            H[kStLines * rG + 1] = c[h][3] * g1;
-            H[2 * kStLines * rG] = c[h][4] * g0;
-            H[2 * kStLines * rG + 1] = c[h][5] * g1;
+            for (int h = 0; h < kStUnroll; ++h) {
+                if (k0 + 32 * h + lane >= npairs) break;
+                T g0, g1;
+                st_pair<T, P, BF>(st, Yl + k0 + 32 * h, g0, g1);
+                T* H = Hl + 2 * (k0 + 32 * h);
+                H[0] = c[h][0] * g0;
+                H[1] = c[h][1] * g1;
+                H[kStLines * rG] = c[h][2] * g0;
+                H[kStLines * rG + 1] = c[h][3] * g1;
+                H[2 * kStLines * rG] = c[h][4] * g0;
+                H[2 * kStLines * rG + 1] = c[h][5] * g1;
+            }
         }
-    }
-    // trial, boundary points: one item per (line, point)
-    const int nbq = st.q_lo + (nq1 - st.q_hi);
-    for (int ll = warp; ll < kStLines; ll += nwarps)
+        // trial, boundary points of this line (band tables)
+        const int nbq = st.q_lo + (nq1 - st.q_hi);
+        const size_t lb = (size_t)(line0 + warp) * nq1;
         for (int k = lane; k < nbq; k += 32) {
             const int q = k < st.q_lo ? k : st.q_hi + (k - st.q_lo);
             const int s0 = a.B.start[q], L = a.B.len[q];
-            const T* Y = sY + ll * rY + s0;
+            const T* Y = sY + warp * rY + s0;
             T g = 0;
             for (int t = 0; t < L; ++t) g = fmaT(a.B.lane(BF, q, t), Y[t], g);
-            T* H = sH + ll * rG + q;
-            const bool live = ll < nl;
-            const size_t cb = (size_t)(line0 + ll) * nq1 + q;
-            H[0] = live ? a.C[(size_t)c0 * a.cs + cb] * g : T(0);
-            H[kStLines * rG] = live ? a.C[(size_t)c1 * a.cs + cb] * g : T(0);
-            H[2 * kStLines * rG] = live ? a.C[(size_t)c2 * a.cs + cb] * g : T(0);
+            T* H = sH + warp * rG + q;
+            H[0] = a.C[(size_t)c0 * a.cs + lb + q] * g;
+            H[kStLines * rG] = a.C[(size_t)c1 * a.cs + lb + q] * g;
+            H[2 * kStLines * rG] = a.C[(size_t)c2 * a.cs + lb + q] * g;
         }
+    }
     __syncthreads();
-    // test: lane = (line l, alpha al) for lane < 24 (FP32, conflict-free banks);
-    // FP64 interior segments use all 32 lanes (below)
+    // test: interior segments of kSeg outputs with the window in registers
     const int nseg = (st.i_hi - st.i_lo) / kSeg;
     const int i_st = st.i_lo + nseg * kSeg;
     const int nbi = st.i_lo + (n1 - i_st);
@@ -537,7 +537,7 @@ __device__ __forceinline__ void st_beta(const XArgs<T>& a, const StencilD<T>& st
         // lanes work, as (line l, segment offset s4) for one alpha per warp pass
         const int l = lane & 7, s4 = lane >> 3;
         const int nm = (nseg + 3) >> 2;
-        for (int it = warp; it < 3 * nm; it += nwarps) {
+        for (int it = warp; it < 3 * nm; it += kStLines) {
             const int al = it / nm, sg = 4 * (it - al * nm) + s4;
             if (sg >= nseg) continue;
             T w[NW];
@@ -546,33 +546,33 @@ __device__ __forceinline__ void st_beta(const XArgs<T>& a, const StencilD<T>& st
             st_seg<T, P>(w, sH + (al * kStLines + l) * rG + st.qw + 2 * kSeg * sg,
                          sT + (al * kStLines + l) * rT + st.i_lo + kSeg * sg);
         }
-    }
-    if (lane < 3 * kStLines) {
+    } else if (lane < 3 * kStLines) {
+        // lane = (line l, alpha al): 24 rows 1 mod 32 apart, conflict-free
         const int al = lane >> 3, l = lane & 7;
-        const int fam = al == 0 ? 2 + BF : BF;
-        const T* Hl = sH + (al * kStLines + l) * rG;
-        T* To = sT + (al * kStLines + l) * rT;
-        if (sizeof(T) != 8) {
-            T w[NW];
+        T w[NW];
 #pragma unroll
-            for (int t = 0; t < NW; ++t) w[t] = al == 0 ? st.wf[2 + BF][t] : st.wf[BF][t];
-            for (int sg = warp; sg < nseg; sg += nwarps)
-                st_seg<T, P>(w, Hl + st.qw + 2 * kSeg * sg, To + st.i_lo + kSeg * sg);
-        }
-        for (int k = warp; k < nbi; k += nwarps) {
-            const int i = k < st.i_lo ? k : i_st + (k - st.i_lo);
-            const int s0 = a.W.start[i], L = a.W.len[i];
-            T acc = 0;
-            for (int t = 0; t < L; ++t) acc = fmaT(a.W.lane(fam, i, t), Hl[s0 + t], acc);
-            To[i] = acc;
-        }
+        for (int t = 0; t < NW; ++t) w[t] = al == 0 ? st.wf[2 + BF][t] : st.wf[BF][t];
+        const T* Hl = sH + (al * kStLines + l) * rG + st.qw;
+        T* To = sT + (al * kStLines + l) * rT + st.i_lo;
+        for (int sg = warp; sg < nseg; sg += kStLines) st_seg<T, P>(w, Hl + 2 * kSeg * sg, To + kSeg * sg);
+    }
+    // test, boundary outputs: one (output, row) item per thread, rows fastest
+    for (int it = threadIdx.x; it < nbi * 3 * kStLines; it += kThreads) {
+        const int k = it / (3 * kStLines), row = it - k * (3 * kStLines);
+        const int i = k < st.i_lo ? k : i_st + (k - st.i_lo);
+        const int fam = row < kStLines ? 2 + BF : BF;  // alpha = 1 tests the derivative
+        const int s0 = a.W.start[i], L = a.W.len[i];
+        const T* Hr = sH + row * rG + s0;
+        T acc = 0;
+        for (int t = 0; t < L; ++t) acc = fmaT(a.W.lane(fam, i, t), Hr[t], acc);
+        sT[row * rT + i] = acc;
     }
     __syncthreads();
-    for (int row = warp; row < 3 * kStLines; row += nwarps) {
+    for (int row = warp; row < 3 * kStLines; row += kStLines) {
         const int al = row >> 3, ll = row & 7;  // kStLines = 8
         if (ll >= nl) continue;
         T* o = tout + (size_t)(3 * al + BETA) * tstride + (size_t)(line0 + ll) * n1;
-        const T* src = sT + (al * kStLines + ll) * rT;
+        const T* src = sT + row * rT;
         for (int i = lane; i < n1; i += 32) o[i] = src[i];
     }
 }
@@ -582,11 +582,18 @@ __global__ void __launch_bounds__(kThreads) k_xstage_stencil(XArgs<T> a, Stencil
                                                              const T* __restrict__ y1, const T* __restrict__ y2,
                                                              T* __restrict__ tout, size_t tstride, const int* skip) {
     if (skip && *skip) return;
+    const int line0 = blockIdx.x * kStLines;
+    const int nl = min(kStLines, a.nlines - line0);
+    if (threadIdx.x < 9) {  // the block's inputs (6 coefficient rows, 3 Y slabs) requested into L2 up front
+        const int f = threadIdx.x;
+        if (f < 6)
+            ptx::prefetch_l2_range(a.C + (size_t)f * a.cs + (size_t)line0 * a.nq1, sizeof(T) * (size_t)nl * a.nq1);
+        else
+            ptx::prefetch_l2_range((f == 6 ? y0 : f == 7 ? y1 : y2) + (size_t)line0 * a.n1, sizeof(T) * (size_t)nl * a.n1);
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sY = reinterpret_cast<T*>(smem_raw);           // Y rows of one beta, then the staged outputs [3][8][rY]
     T* sH = sY + 3 * kStLines * st_stride(a.n1);      // [3 alpha][8][rG]
-    const int line0 = blockIdx.x * kStLines;
-    const int nl = min(kStLines, a.nlines - line0);
     st_beta<T, P, 0>(a, st, y0, tout, tstride, line0, nl, sY, sH);
     st_beta<T, P, 1>(a, st, y1, tout, tstride, line0, nl, sY, sH);
     st_beta<T, P, 2>(a, st, y2, tout, tstride, line0, nl, sY, sH);
