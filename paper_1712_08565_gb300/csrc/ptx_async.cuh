@@ -54,6 +54,18 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                  : "memory");
 }
 
+// Per-thread asynchronous global -> shared copy of one 4- or 8-byte element
+// (cp.async); completion by cp_async_wait_all in the issuing thread.
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "cp.async.ca copies 4, 8 or 16 bytes");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(src)),
+                 "n"((int)sizeof(T))
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Hint to the copy engine: bring [p, p + bytes) into L2 (cp.async.bulk.prefetch.L2);
 // p 16-byte aligned, bytes a multiple of 16.  No completion, no effect on results.
 __device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {

@@ -407,16 +407,19 @@ __global__ void __launch_bounds__(kThreads) k_xstage_tiled(XArgs<T> a, const T* 
 // ---- stencil forward x stage (mode 6): translation-invariant interiors
 // For uniform knots the interior rows of B (pairs of points) and W (outputs)
 // are one filter shifted along the line (StencilD); boundary rows use the
-// band tables.  A block owns 8 lines.
-//  trial: lanes = consecutive pairs of points of one line; the pair's window
-//    of P + 2 Y values gives G_b at both points (filter taps are kernel
+// band tables.  A block owns 8 lines and takes the three trial gradients
+// beta in turn; the block's inputs are requested into L2 when it starts.
+//  trial: warp w = line w, lanes = consecutive pairs of points; the pair's
+//    window of P + 2 Y values gives G_b at both points (filter taps are kernel
 //    parameters), then the three H^(alpha b) = C_(alpha b) G_b with coalesced
 //    coefficient loads, stored to shared memory;
 //  test: lanes = (line, alpha), 24 of 32; a lane walks segments of 8 outputs
 //    of its own row with the window (2P + 15 values) in registers: 8(2P + 1)
 //    multiply-adds per window.  Row strides are 1 mod 32 and the alpha slabs
 //    8 rows apart, so the 24 lanes hit 24 different banks;
-//  outputs staged in shared memory (aliasing Y) and written out coalesced.
+//  outputs staged in shared memory and written out coalesced while the next
+//    beta's trial runs; the next beta's Y slab arrives by cp.async during the
+//    test, so each beta costs two barriers.
 constexpr int kStLines = 8;  // the (line, alpha) lane map and the copy-out assume 8
 constexpr int kSeg = 8;
 constexpr int kStUnroll = 2;  // chunks of 32 pairs per warp pass in the stencil trial (4 measured no faster)
@@ -455,83 +458,94 @@ __device__ __forceinline__ void st_seg(const T* w, const T* H, T* To) {
     }
 }
 
+// The Y slab of one beta for this block's lines: warp w copies line w's row
+// asynchronously (cp.async) into sY.
+template <typename T>
+__device__ __forceinline__ void st_load_y(const T* __restrict__ yb, int n1, int line0, int nl, T* sY) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp >= nl) return;
+    const T* src = yb + (size_t)(line0 + warp) * n1;
+    T* dst = sY + warp * st_stride(n1);
+    for (int j = lane; j < n1; j += 32) ptx::cp_async_elem(dst + j, src + j);
+}
+
+// Trial side of one beta: G_beta at every point of line w (warp w) from its Y
+// row, times the three coefficients C_(alpha beta), into the H rows.
 template <typename T, int P, int BETA>
-__device__ __forceinline__ void st_beta(const XArgs<T>& a, const StencilD<T>& st, const T* __restrict__ yb,
-                                        T* __restrict__ tout, size_t tstride, int line0, int nl, T* sY, T* sH) {
+__device__ __forceinline__ void st_trial(const XArgs<T>& a, const StencilD<T>& st, int line0, int nl, const T* sY,
+                                         T* sH) {
     constexpr int BF = BETA == 0 ? 1 : 0;  // trial family: derivative in direction 1 for beta = 1
-    constexpr int NW = 2 * P + 1;
     const int n1 = a.n1, nq1 = a.nq1;
     const int rY = st_stride(n1), rG = st_stride(nq1);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c0 = BETA == 0 ? 0 : 2 + BETA, c1 = BETA == 1 ? 1 : 3 + BETA, c2 = BETA == 2 ? 2 : 4 + BETA;
-    // warp w owns line w in the load and trial phases (kStLines warps)
-    const bool live = warp < nl;
-    __syncthreads();  // previous beta's outputs copied out of sY
-    {
-        const T* src = yb + (size_t)(line0 + (live ? warp : 0)) * n1;
-        for (int j = lane; j < n1; j += 32) sY[warp * rY + j] = live ? src[j] : T(0);
-    }
-    __syncthreads();
-    if (live) {
-        // trial, interior pairs: lane = pair k of the chunk; the three
-        // coefficient rows advance by 64 points per chunk; kStUnroll chunks
-        // load their 6 coefficients each before any is used
-        const int npairs = (st.q_hi - st.q_lo) >> 1;
-        const size_t cl = (size_t)(line0 + warp) * nq1 + st.q_lo + 2 * lane;
-        const T* C0 = a.C + (size_t)c0 * a.cs + cl;
-        const T* C1 = a.C + (size_t)c1 * a.cs + cl;
-        const T* C2 = a.C + (size_t)c2 * a.cs + cl;
-        const T* Yl = sY + warp * rY + st.jb + lane;
-        T* Hl = sH + warp * rG + st.q_lo + 2 * lane;
-        for (int k0 = 0; k0 < npairs; k0 += 32 * kStUnroll) {
-            T c[kStUnroll][6];
+    if (warp >= nl) return;
+    // interior pairs: lane = pair k of the chunk; the three coefficient rows
+    // advance by 64 points per chunk; kStUnroll chunks load their 6
+    // coefficients each before any is used
+    const int npairs = (st.q_hi - st.q_lo) >> 1;
+    const size_t cl = (size_t)(line0 + warp) * nq1 + st.q_lo + 2 * lane;
+    const T* C0 = a.C + (size_t)c0 * a.cs + cl;
+    const T* C1 = a.C + (size_t)c1 * a.cs + cl;
+    const T* C2 = a.C + (size_t)c2 * a.cs + cl;
+    const T* Yl = sY + warp * rY + st.jb + lane;
+    T* Hl = sH + warp * rG + st.q_lo + 2 * lane;
+    for (int k0 = 0; k0 < npairs; k0 += 32 * kStUnroll) {
+        T c[kStUnroll][6];
 #pragma unroll
-            for (int h = 0; h < kStUnroll; ++h) {
-                const int o = 2 * (k0 + 32 * h);
-                const bool ok = k0 + 32 * h + lane < npairs;
-                c[h][0] = ok ? C0[o] : T(0);
-                c[h][1] = ok ? C0[o + 1] : T(0);
-                c[h][2] = ok ? C1[o] : T(0);
-                c[h][3] = ok ? C1[o + 1] : T(0);
-                c[h][4] = ok ? C2[o] : T(0);
-                c[h][5] = ok ? C2[o + 1] : T(0);
-            }
-#pragma unroll
-            for (int h = 0; h < kStUnroll; ++h) {
-                if (k0 + 32 * h + lane >= npairs) break;
-                T g0, g1;
-                st_pair<T, P, BF>(st, Yl + k0 + 32 * h, g0, g1);
-                T* H = Hl + 2 * (k0 + 32 * h);
-                H[0] = c[h][0] * g0;
-                H[1] = c[h][1] * g1;
-                H[kStLines * rG] = c[h][2] * g0;
-                H[kStLines * rG + 1] = c[h][3] * g1;
-                H[2 * kStLines * rG] = c[h][4] * g0;
-                H[2 * kStLines * rG + 1] = c[h][5] * g1;
-            }
+        for (int h = 0; h < kStUnroll; ++h) {
+            const int o = 2 * (k0 + 32 * h);
+            const bool ok = k0 + 32 * h + lane < npairs;
+            c[h][0] = ok ? C0[o] : T(0);
+            c[h][1] = ok ? C0[o + 1] : T(0);
+            c[h][2] = ok ? C1[o] : T(0);
+            c[h][3] = ok ? C1[o + 1] : T(0);
+            c[h][4] = ok ? C2[o] : T(0);
+            c[h][5] = ok ? C2[o + 1] : T(0);
         }
-        // trial, boundary points of this line (band tables)
-        const int nbq = st.q_lo + (nq1 - st.q_hi);
-        const size_t lb = (size_t)(line0 + warp) * nq1;
-        for (int k = lane; k < nbq; k += 32) {
-            const int q = k < st.q_lo ? k : st.q_hi + (k - st.q_lo);
-            const int s0 = a.B.start[q], L = a.B.len[q];
-            const T* Y = sY + warp * rY + s0;
-            T g = 0;
-            for (int t = 0; t < L; ++t) g = fmaT(a.B.lane(BF, q, t), Y[t], g);
-            T* H = sH + warp * rG + q;
-            H[0] = a.C[(size_t)c0 * a.cs + lb + q] * g;
-            H[kStLines * rG] = a.C[(size_t)c1 * a.cs + lb + q] * g;
-            H[2 * kStLines * rG] = a.C[(size_t)c2 * a.cs + lb + q] * g;
+#pragma unroll
+        for (int h = 0; h < kStUnroll; ++h) {
+            if (k0 + 32 * h + lane >= npairs) break;
+            T g0, g1;
+            st_pair<T, P, BF>(st, Yl + k0 + 32 * h, g0, g1);
+            T* H = Hl + 2 * (k0 + 32 * h);
+            H[0] = c[h][0] * g0;
+            H[1] = c[h][1] * g1;
+            H[kStLines * rG] = c[h][2] * g0;
+            H[kStLines * rG + 1] = c[h][3] * g1;
+            H[2 * kStLines * rG] = c[h][4] * g0;
+            H[2 * kStLines * rG + 1] = c[h][5] * g1;
         }
     }
-    __syncthreads();
-    // test: interior segments of kSeg outputs with the window in registers
+    // boundary points of this line (band tables)
+    const int nbq = st.q_lo + (nq1 - st.q_hi);
+    const size_t lb = (size_t)(line0 + warp) * nq1;
+    for (int k = lane; k < nbq; k += 32) {
+        const int q = k < st.q_lo ? k : st.q_hi + (k - st.q_lo);
+        const int s0 = a.B.start[q], L = a.B.len[q];
+        const T* Y = sY + warp * rY + s0;
+        T g = 0;
+        for (int t = 0; t < L; ++t) g = fmaT(a.B.lane(BF, q, t), Y[t], g);
+        T* H = sH + warp * rG + q;
+        H[0] = a.C[(size_t)c0 * a.cs + lb + q] * g;
+        H[kStLines * rG] = a.C[(size_t)c1 * a.cs + lb + q] * g;
+        H[2 * kStLines * rG] = a.C[(size_t)c2 * a.cs + lb + q] * g;
+    }
+}
+
+// Test side of one beta: the 24 rows (alpha, line) of H against the WQ
+// weights of their family, outputs into sT.
+template <typename T, int P, int BETA>
+__device__ __forceinline__ void st_test(const XArgs<T>& a, const StencilD<T>& st, const T* sH, T* sT) {
+    constexpr int BF = BETA == 0 ? 1 : 0;
+    constexpr int NW = 2 * P + 1;
+    const int n1 = a.n1, nq1 = a.nq1;
+    const int rT = st_stride(n1), rG = st_stride(nq1);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // interior segments of kSeg outputs with the window in registers
     const int nseg = (st.i_hi - st.i_lo) / kSeg;
     const int i_st = st.i_lo + nseg * kSeg;
     const int nbi = st.i_lo + (n1 - i_st);
-    const int rT = rY;
-    T* sT = sY;  // [3 alpha][8][rT]: outputs of this beta (Y no longer needed)
     if (sizeof(T) == 8) {
         // FP64 is bound by the FP64 pipe, not by shared-memory banks: all 32
         // lanes work, as (line l, segment offset s4) for one alpha per warp pass
@@ -556,7 +570,7 @@ __device__ __forceinline__ void st_beta(const XArgs<T>& a, const StencilD<T>& st
         T* To = sT + (al * kStLines + l) * rT + st.i_lo;
         for (int sg = warp; sg < nseg; sg += kStLines) st_seg<T, P>(w, Hl + 2 * kSeg * sg, To + kSeg * sg);
     }
-    // test, boundary outputs: one (output, row) item per thread, rows fastest
+    // boundary outputs: one (output, row) item per thread, rows fastest
     for (int it = threadIdx.x; it < nbi * 3 * kStLines; it += kThreads) {
         const int k = it / (3 * kStLines), row = it - k * (3 * kStLines);
         const int i = k < st.i_lo ? k : i_st + (k - st.i_lo);
@@ -567,7 +581,14 @@ __device__ __forceinline__ void st_beta(const XArgs<T>& a, const StencilD<T>& st
         for (int t = 0; t < L; ++t) acc = fmaT(a.W.lane(fam, i, t), Hr[t], acc);
         sT[row * rT + i] = acc;
     }
-    __syncthreads();
+}
+
+// Staged outputs of one beta to T^(alpha beta): warp w copies rows w, w + 8, w + 16.
+template <typename T, int BETA>
+__device__ __forceinline__ void st_copy_out(int n1, int line0, int nl, const T* sT, T* __restrict__ tout,
+                                            size_t tstride) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int rT = st_stride(n1);
     for (int row = warp; row < 3 * kStLines; row += kStLines) {
         const int al = row >> 3, ll = row & 7;  // kStLines = 8
         if (ll >= nl) continue;
@@ -577,6 +598,8 @@ __device__ __forceinline__ void st_beta(const XArgs<T>& a, const StencilD<T>& st
     }
 }
 
+// One block = 8 lines.  Per beta two barriers: (trial of beta, copy-out of
+// beta - 1) | (test of beta, Y of beta + 1 arriving by cp.async).
 template <typename T, int P>
 __global__ void __launch_bounds__(kThreads) k_xstage_stencil(XArgs<T> a, StencilD<T> st, const T* __restrict__ y0,
                                                              const T* __restrict__ y1, const T* __restrict__ y2,
@@ -584,19 +607,43 @@ __global__ void __launch_bounds__(kThreads) k_xstage_stencil(XArgs<T> a, Stencil
     if (skip && *skip) return;
     const int line0 = blockIdx.x * kStLines;
     const int nl = min(kStLines, a.nlines - line0);
+    const int n1 = a.n1;
     if (threadIdx.x < 9) {  // the block's inputs (6 coefficient rows, 3 Y slabs) requested into L2 up front
         const int f = threadIdx.x;
         if (f < 6)
             ptx::prefetch_l2_range(a.C + (size_t)f * a.cs + (size_t)line0 * a.nq1, sizeof(T) * (size_t)nl * a.nq1);
         else
-            ptx::prefetch_l2_range((f == 6 ? y0 : f == 7 ? y1 : y2) + (size_t)line0 * a.n1, sizeof(T) * (size_t)nl * a.n1);
+            ptx::prefetch_l2_range((f == 6 ? y0 : f == 7 ? y1 : y2) + (size_t)line0 * n1, sizeof(T) * (size_t)nl * n1);
     }
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sY = reinterpret_cast<T*>(smem_raw);           // Y rows of one beta, then the staged outputs [3][8][rY]
-    T* sH = sY + 3 * kStLines * st_stride(a.n1);      // [3 alpha][8][rG]
-    st_beta<T, P, 0>(a, st, y0, tout, tstride, line0, nl, sY, sH);
-    st_beta<T, P, 1>(a, st, y1, tout, tstride, line0, nl, sY, sH);
-    st_beta<T, P, 2>(a, st, y2, tout, tstride, line0, nl, sY, sH);
+    T* sY = reinterpret_cast<T*>(smem_raw);             // [8][rY]: Y rows of one beta
+    T* sT = sY + kStLines * st_stride(n1);              // [3 alpha][8][rT]: staged outputs of one beta
+    T* sH = sT + 3 * kStLines * st_stride(n1);          // [3 alpha][8][rG]
+    st_load_y(y0, n1, line0, nl, sY);
+    ptx::cp_async_commit();
+    ptx::cp_async_wait_all();
+    __syncthreads();
+    st_trial<T, P, 0>(a, st, line0, nl, sY, sH);
+    __syncthreads();
+    st_load_y(y1, n1, line0, nl, sY);
+    ptx::cp_async_commit();
+    st_test<T, P, 0>(a, st, sH, sT);
+    ptx::cp_async_wait_all();
+    __syncthreads();
+    st_copy_out<T, 0>(n1, line0, nl, sT, tout, tstride);
+    st_trial<T, P, 1>(a, st, line0, nl, sY, sH);
+    __syncthreads();
+    st_load_y(y2, n1, line0, nl, sY);
+    ptx::cp_async_commit();
+    st_test<T, P, 1>(a, st, sH, sT);
+    ptx::cp_async_wait_all();
+    __syncthreads();
+    st_copy_out<T, 1>(n1, line0, nl, sT, tout, tstride);
+    st_trial<T, P, 2>(a, st, line0, nl, sY, sH);
+    __syncthreads();
+    st_test<T, P, 2>(a, st, sH, sT);
+    __syncthreads();
+    st_copy_out<T, 2>(n1, line0, nl, sT, tout, tstride);
 }
 
 }  // namespace
@@ -651,8 +698,8 @@ cudaError_t launch_forward_xstage(const OpCtx<T>& c, const XArgs<T>& a, const T*
 }
 
 int xstage_smem_bytes(int elem_size, int n1, int nq1, int lines, int mode) {
-    if (mode == 6)  // stencil: Y rows / staged outputs and H rows of 8 lines, 3 slabs each
-        return (int)((size_t)3 * kStLines * (st_stride(n1) + (size_t)st_stride(nq1)) * elem_size);
+    if (mode == 6)  // stencil: Y rows of 8 lines, staged outputs and H rows of 8 lines x 3 alpha
+        return (int)((size_t)kStLines * (4 * (size_t)st_stride(n1) + 3 * (size_t)st_stride(nq1)) * elem_size);
     if (mode >= 4) {  // tiled: two lines-innermost slabs of 3 x (rows + 4) padded rows
         const int pr = 128 / (kTileLines * elem_size), pad = 16 / elem_size;
         auto tr = [&](int r) { return (size_t)r * kTileLines + (size_t)(r / pr) * pad; };
