@@ -422,7 +422,6 @@ __global__ void __launch_bounds__(kThreads) k_xstage_tiled(XArgs<T> a, const T* 
 //    test, so each beta costs two barriers.
 constexpr int kStLines = 8;  // the (line, alpha) lane map and the copy-out assume 8
 constexpr int kSeg = 8;
-constexpr int kStUnroll = 2;  // chunks of 32 pairs per warp pass in the stencil trial (4 measured no faster)
 static_assert(kStLines == 8, "stencil x stage: 3 x 8 (line, alpha) lanes per warp");
 static_assert(kThreads / 32 == kStLines, "stencil x stage: one warp per line in the trial");
 
@@ -480,31 +479,47 @@ __device__ __forceinline__ void st_trial(const XArgs<T>& a, const StencilD<T>& s
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int c0 = BETA == 0 ? 0 : 2 + BETA, c1 = BETA == 1 ? 1 : 3 + BETA, c2 = BETA == 2 ? 2 : 4 + BETA;
     if (warp >= nl) return;
-    // interior pairs: lane = pair k of the chunk; the three coefficient rows
-    // advance by 64 points per chunk; kStUnroll chunks load their 6
-    // coefficients each before any is used
+    const size_t lb = (size_t)(line0 + warp) * nq1;
+    const T* C0 = a.C + (size_t)c0 * a.cs + lb;
+    const T* C1 = a.C + (size_t)c1 * a.cs + lb;
+    const T* C2 = a.C + (size_t)c2 * a.cs + lb;
+    // boundary points of this line: their coefficients (first 32 points) are
+    // requested before the interior loop so that the latency overlaps it
+    const int nbq = st.q_lo + (nq1 - st.q_hi);
+    const int qb = lane < st.q_lo ? lane : st.q_hi + (lane - st.q_lo);
+    const bool bl = lane < nbq;
+    const T cb0 = bl ? C0[qb] : T(0), cb1 = bl ? C1[qb] : T(0), cb2 = bl ? C2[qb] : T(0);
+    // interior pairs: lane = pair k of a chunk of 32; two chunks per pass,
+    // the next pass's 12 coefficients loaded before this pass computes
     const int npairs = (st.q_hi - st.q_lo) >> 1;
-    const size_t cl = (size_t)(line0 + warp) * nq1 + st.q_lo + 2 * lane;
-    const T* C0 = a.C + (size_t)c0 * a.cs + cl;
-    const T* C1 = a.C + (size_t)c1 * a.cs + cl;
-    const T* C2 = a.C + (size_t)c2 * a.cs + cl;
     const T* Yl = sY + warp * rY + st.jb + lane;
     T* Hl = sH + warp * rG + st.q_lo + 2 * lane;
-    for (int k0 = 0; k0 < npairs; k0 += 32 * kStUnroll) {
-        T c[kStUnroll][6];
+    const int qo = st.q_lo + 2 * lane;
+    auto load6 = [&](int k, T* c) {
+        const bool ok = k + lane < npairs;
+        const int o = qo + 2 * k;
+        c[0] = ok ? C0[o] : T(0);
+        c[1] = ok ? C0[o + 1] : T(0);
+        c[2] = ok ? C1[o] : T(0);
+        c[3] = ok ? C1[o + 1] : T(0);
+        c[4] = ok ? C2[o] : T(0);
+        c[5] = ok ? C2[o + 1] : T(0);
+    };
+    T cn[2][6];
+    load6(0, cn[0]);
+    load6(32, cn[1]);
+    for (int k0 = 0; k0 < npairs; k0 += 64) {
+        T c[2][6];
 #pragma unroll
-        for (int h = 0; h < kStUnroll; ++h) {
-            const int o = 2 * (k0 + 32 * h);
-            const bool ok = k0 + 32 * h + lane < npairs;
-            c[h][0] = ok ? C0[o] : T(0);
-            c[h][1] = ok ? C0[o + 1] : T(0);
-            c[h][2] = ok ? C1[o] : T(0);
-            c[h][3] = ok ? C1[o + 1] : T(0);
-            c[h][4] = ok ? C2[o] : T(0);
-            c[h][5] = ok ? C2[o + 1] : T(0);
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int e = 0; e < 6; ++e) c[h][e] = cn[h][e];
+        if (k0 + 64 < npairs) {
+            load6(k0 + 64, cn[0]);
+            load6(k0 + 96, cn[1]);
         }
 #pragma unroll
-        for (int h = 0; h < kStUnroll; ++h) {
+        for (int h = 0; h < 2; ++h) {
             if (k0 + 32 * h + lane >= npairs) break;
             T g0, g1;
             st_pair<T, P, BF>(st, Yl + k0 + 32 * h, g0, g1);
@@ -517,9 +532,7 @@ __device__ __forceinline__ void st_trial(const XArgs<T>& a, const StencilD<T>& s
             H[2 * kStLines * rG + 1] = c[h][5] * g1;
         }
     }
-    // boundary points of this line (band tables)
-    const int nbq = st.q_lo + (nq1 - st.q_hi);
-    const size_t lb = (size_t)(line0 + warp) * nq1;
+    // boundary points (band tables)
     for (int k = lane; k < nbq; k += 32) {
         const int q = k < st.q_lo ? k : st.q_hi + (k - st.q_lo);
         const int s0 = a.B.start[q], L = a.B.len[q];
@@ -527,9 +540,10 @@ __device__ __forceinline__ void st_trial(const XArgs<T>& a, const StencilD<T>& s
         T g = 0;
         for (int t = 0; t < L; ++t) g = fmaT(a.B.lane(BF, q, t), Y[t], g);
         T* H = sH + warp * rG + q;
-        H[0] = a.C[(size_t)c0 * a.cs + lb + q] * g;
-        H[kStLines * rG] = a.C[(size_t)c1 * a.cs + lb + q] * g;
-        H[2 * kStLines * rG] = a.C[(size_t)c2 * a.cs + lb + q] * g;
+        const bool first = k < 32;
+        H[0] = (first ? cb0 : C0[q]) * g;
+        H[kStLines * rG] = (first ? cb1 : C1[q]) * g;
+        H[2 * kStLines * rG] = (first ? cb2 : C2[q]) * g;
     }
 }
 
@@ -570,8 +584,9 @@ __device__ __forceinline__ void st_test(const XArgs<T>& a, const StencilD<T>& st
         T* To = sT + (al * kStLines + l) * rT + st.i_lo;
         for (int sg = warp; sg < nseg; sg += kStLines) st_seg<T, P>(w, Hl + 2 * kSeg * sg, To + kSeg * sg);
     }
-    // boundary outputs: one (output, row) item per thread, rows fastest
-    for (int it = threadIdx.x; it < nbi * 3 * kStLines; it += kThreads) {
+    // boundary outputs: one (output, row) item per thread, rows fastest, handed
+    // out from the last warp down (the first warps take the extra interior segments)
+    for (int it = kThreads - 1 - threadIdx.x; it < nbi * 3 * kStLines; it += kThreads) {
         const int k = it / (3 * kStLines), row = it - k * (3 * kStLines);
         const int i = k < st.i_lo ? k : i_st + (k - st.i_lo);
         const int fam = row < kStLines ? 2 + BF : BF;  // alpha = 1 tests the derivative
