@@ -442,6 +442,21 @@ def mixed_vs_fp64(mf, device):
         else:
             res[name]["rel_err_vs_fp64"] = float(torch.linalg.vector_norm(u - u64) / torch.linalg.vector_norm(u64))
     res["speedup"] = res["fp64"]["time_s"] / res["mixed_tf32"]["time_s"]
+    # the same mixed solve with the FD mode products in BF16 (FP32 accumulate)
+    opb, _ = make_op(mf, MIXED["p"], MIXED["nel"], mixed=True, fd="bf16", device=device)
+    fb = opb.load_vector("ring", "sines")
+    opb.solve(fb, rtol=MIXED["rtol"], maxit=2000, inner_rtol=1e-4)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ub, infob = opb.solve(fb, rtol=MIXED["rtol"], maxit=2000, inner_rtol=1e-4)
+    torch.cuda.synchronize()
+    res["mixed_bf16"] = {"time_s": time.perf_counter() - t0, "iterations": infob.iterations,
+                         "outer": infob.outer_iterations, "rel_residual": infob.rel_residual,
+                         "converged": infob.converged,
+                         "rel_err_vs_fp64": float(torch.linalg.vector_norm(ub - u64) / torch.linalg.vector_norm(u64))}
+    res["speedup_bf16"] = res["fp64"]["time_s"] / res["mixed_bf16"]["time_s"]
+    opb.close()
+    del ub, fb
     x = torch.from_numpy(inputs.uniform_vector(op.shape, 1)).to(device)
     x32 = x.float()
     y, y32 = torch.empty_like(x), torch.empty_like(x32)
