@@ -207,8 +207,10 @@ typedef struct {
 
 /* Solves K~ u = f with right-FD-preconditioned BiCGStab (Section 4): FP64
  * throughout, or -- on a mixed handle -- FP64 iterative refinement around
- * inner FP32 BiCGStab solves (FP32 operator, tensor-core FD, FP64 dot
- * products).  f_dev, u_dev: [n3][n2][n1].  Synchronous; returns info->status. */
+ * inner FP32 BiCGStab solves (FP32 operator, tensor-core FD, FP32 vector
+ * updates, dot products taken per thread by the compensated Dot2 scheme in
+ * FP32 and summed across threads in FP64).  f_dev, u_dev: [n3][n2][n1].
+ * Synchronous; returns info->status. */
 int mfwq_solve(mfwq_handle h, const double* f_dev, double* u_dev,
                const mfwq_solve_opts* opts, mfwq_solve_info* info);
 

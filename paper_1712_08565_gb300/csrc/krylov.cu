@@ -7,7 +7,8 @@
 //   s^ = P^-1 s, t = A s^, omega = t.s / t.t
 //   x += alpha p^ + omega s^, r = s - omega t                     [stop if |r| <= tol |f|]
 // Dot products are reduced deterministically (fixed grid, per-block partial
-// sums, one finishing block) and accumulated in FP64 for FP32 vectors too.
+// sums, one finishing block) and accumulated in FP64; for FP32 vectors each
+// thread's part is a Dot2 sum in FP32 (twice-FP32 accuracy, see Dot2F).
 // Scalar updates run in one-thread "finish" kernels; the host only reads the
 // scalar block to decide when to stop, so the launch sequence of an
 // iteration is fixed and the kernels of a finished solve return at once.
@@ -66,6 +67,75 @@ struct VArgs {
     int x_given;  // V_INIT: x holds x0 and r = f - A x0 (r preset by the caller)
 };
 
+// A dot product's running part in FP32 as the Dot2 algorithm of Ogita, Rump
+// and Oishi (Accurate sum and dot product, SIAM J. Sci. Comput. 26, 2005):
+// every product split exactly into its rounded value and error (one FMA),
+// the rounded values summed with the exact error of each addition (TwoSum)
+// kept beside them, so p + s is as accurate as a sum taken in twice the FP32
+// precision.  Intrinsics keep the compiler from contracting the error terms.
+struct Dot2F {
+    float p = 0.f, s = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float h = __fmul_rn(a, b);
+        const float r = fmaf(a, b, -h);
+        const float x = __fadd_rn(p, h);
+        const float z = __fsub_rn(x, p);
+        const float q = __fadd_rn(__fsub_rn(p, __fsub_rn(x, z)), __fsub_rn(h, z));
+        p = x;
+        s = __fadd_rn(s, __fadd_rn(q, r));
+    }
+    __device__ __forceinline__ double value() const { return (double)p + (double)s; }
+};
+
+// FP32 vectors (the inner solve of the mixed-precision refinement): the
+// updates in FP32, as an FP32 BiCGStab computes them; each thread's part of a
+// dot product by Dot2 in FP32, the block and grid reductions in FP64.  (FP64
+// conversions and arithmetic per element would make these memory-streaming
+// kernels FP64-pipe bound on this part.)
+template <int OP>
+__device__ __forceinline__ void vec_f32(const VArgs<float>& a, const KScal* __restrict__ sc, double& s0, double& s1) {
+    const float beta = (float)sc->beta, omega = (float)sc->omega, alpha = (float)sc->alpha;
+    const int half = sc->half;
+    Dot2F k0, k1;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += (size_t)gridDim.x * blockDim.x) {
+        if (OP == V_INIT) {
+            const float fi = a.f[i];
+            const float ri = a.x_given ? a.r[i] : fi;
+            if (!a.x_given) a.x[i] = 0.f;
+            a.r[i] = ri;
+            a.rhat[i] = ri;
+            a.p[i] = 0.f;
+            a.v[i] = 0.f;
+            k0.add(ri, ri);
+            k1.add(fi, fi);
+        } else if (OP == V_P) {
+            a.p[i] = fmaf(beta, fmaf(-omega, a.v[i], a.p[i]), a.r[i]);
+        } else if (OP == V_DOT_RV) {
+            k0.add(a.rhat[i], a.v[i]);
+        } else if (OP == V_S) {
+            const float si = fmaf(-alpha, a.v[i], a.r[i]);
+            a.s[i] = si;
+            k0.add(si, si);
+        } else if (OP == V_DOT_TS) {
+            const float ti = a.t[i];
+            k0.add(ti, a.s[i]);
+            k1.add(ti, ti);
+        } else if (OP == V_XR) {
+            if (half) {
+                a.x[i] = fmaf(alpha, a.ph[i], a.x[i]);
+            } else {
+                a.x[i] = fmaf(omega, a.sh[i], fmaf(alpha, a.ph[i], a.x[i]));
+                const float ri = fmaf(-omega, a.t[i], a.s[i]);
+                a.r[i] = ri;
+                k0.add(ri, ri);
+                k1.add(a.rhat[i], ri);
+            }
+        }
+    }
+    s0 = k0.value();
+    s1 = k1.value();
+}
+
 template <typename T, int OP>
 __global__ void __launch_bounds__(kRedThreads) k_vec(VArgs<T> a, const KScal* __restrict__ sc, double* __restrict__ part) {
     if (OP == V_DOT_TS ? sc->skip2 : sc->skip1) return;
@@ -73,36 +143,40 @@ __global__ void __launch_bounds__(kRedThreads) k_vec(VArgs<T> a, const KScal* __
     double s0 = 0.0, s1 = 0.0;
     const double beta = sc->beta, omega = sc->omega, alpha = sc->alpha;
     const int half = sc->half;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += (size_t)gridDim.x * blockDim.x) {
-        if (OP == V_INIT) {
-            T ri = a.x_given ? a.r[i] : a.f[i];
-            if (!a.x_given) a.x[i] = 0;
-            a.r[i] = ri;
-            a.rhat[i] = ri;
-            a.p[i] = 0;
-            a.v[i] = 0;
-            s0 += D(ri) * D(ri);
-            s1 += D(a.f[i]) * D(a.f[i]);
-        } else if (OP == V_P) {
-            a.p[i] = (T)(D(a.r[i]) + beta * (D(a.p[i]) - omega * D(a.v[i])));
-        } else if (OP == V_DOT_RV) {
-            s0 += D(a.rhat[i]) * D(a.v[i]);
-        } else if (OP == V_S) {
-            T si = (T)(D(a.r[i]) - alpha * D(a.v[i]));
-            a.s[i] = si;
-            s0 += D(si) * D(si);
-        } else if (OP == V_DOT_TS) {
-            s0 += D(a.t[i]) * D(a.s[i]);
-            s1 += D(a.t[i]) * D(a.t[i]);
-        } else if (OP == V_XR) {
-            if (half) {
-                a.x[i] = (T)(D(a.x[i]) + alpha * D(a.ph[i]));
-            } else {
-                a.x[i] = (T)(D(a.x[i]) + alpha * D(a.ph[i]) + omega * D(a.sh[i]));
-                T ri = (T)(D(a.s[i]) - omega * D(a.t[i]));
+    if constexpr (sizeof(T) == 4) {
+        vec_f32<OP>(a, sc, s0, s1);
+    } else {
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += (size_t)gridDim.x * blockDim.x) {
+            if (OP == V_INIT) {
+                T ri = a.x_given ? a.r[i] : a.f[i];
+                if (!a.x_given) a.x[i] = 0;
                 a.r[i] = ri;
+                a.rhat[i] = ri;
+                a.p[i] = 0;
+                a.v[i] = 0;
                 s0 += D(ri) * D(ri);
-                s1 += D(a.rhat[i]) * D(ri);
+                s1 += D(a.f[i]) * D(a.f[i]);
+            } else if (OP == V_P) {
+                a.p[i] = (T)(D(a.r[i]) + beta * (D(a.p[i]) - omega * D(a.v[i])));
+            } else if (OP == V_DOT_RV) {
+                s0 += D(a.rhat[i]) * D(a.v[i]);
+            } else if (OP == V_S) {
+                T si = (T)(D(a.r[i]) - alpha * D(a.v[i]));
+                a.s[i] = si;
+                s0 += D(si) * D(si);
+            } else if (OP == V_DOT_TS) {
+                s0 += D(a.t[i]) * D(a.s[i]);
+                s1 += D(a.t[i]) * D(a.t[i]);
+            } else if (OP == V_XR) {
+                if (half) {
+                    a.x[i] = (T)(D(a.x[i]) + alpha * D(a.ph[i]));
+                } else {
+                    a.x[i] = (T)(D(a.x[i]) + alpha * D(a.ph[i]) + omega * D(a.sh[i]));
+                    T ri = (T)(D(a.s[i]) - omega * D(a.t[i]));
+                    a.r[i] = ri;
+                    s0 += D(ri) * D(ri);
+                    s1 += D(a.rhat[i]) * D(ri);
+                }
             }
         }
     }

@@ -11,7 +11,10 @@ Tolerances (derived from the arithmetic, not from the paper, which is FP64):
   7e-3 (BF16).  Asserted with a factor 5 margin: 1e-2 and 3.5e-2.
 * Refinement: the FP64 residual ||f - K~ u|| / ||f|| <= 1e-8 is asserted
   with the oracle's operator, and the solution must agree with the FP64
-  solve to the accuracy that residual buys (1e-7).
+  solve to the accuracy the two residuals buy:
+  ||u - u64|| <= ||K~^-1||_2 (||f - K~ u|| + ||f - K~ u64||), with the
+  smallest singular value of the oracle's dense K~ (1% for the rounding of
+  the norms themselves).
 """
 import numpy as np
 import pytest
@@ -91,7 +94,11 @@ def test_mixed_refinement_reaches_fp64_residual(mf, fd):
     assert res <= 1.01e-8
     u64, i64 = op.solve(f, rtol=1e-12, force_fp64=True)
     assert i64.converged
-    assert _nrel(u.cpu().numpy(), u64.cpu().numpy()) <= 1e-7
+    un, u64n = u.cpu().numpy().ravel(), u64.cpu().numpy().ravel()
+    Kd = K.toarray() if hasattr(K, "toarray") else np.asarray(K)
+    smin = np.linalg.svd(Kd, compute_uv=False)[-1]
+    bound = (np.linalg.norm(fn.ravel() - K @ un) + np.linalg.norm(fn.ravel() - K @ u64n)) / smin
+    assert np.linalg.norm(un - u64n) <= 1.01 * bound, (np.linalg.norm(un - u64n), bound)
     op.sync()
     op.close()
 
