@@ -357,6 +357,43 @@ def reaction(mf, device, alpha=10.0):
     return out
 
 
+def fp64_low_fd(mf, device):
+    """The bench solve (ring, p = 4, 128 elements, FP64 BiCGStab to 1e-10) with
+    the FD applied on the tensor cores (TF32, then BF16) instead of in FP64:
+    the iterate, operator and residual stay FP64, only the preconditioner is
+    inexact.  Times against the plain FP64 solve on the same handle."""
+    import torch
+    op, _ = make_op(mf, WORKLOAD["p"], WORKLOAD["nel"], mixed=True, fd="tf32", device=device)
+    f = op.load_vector(WORKLOAD["geometry"], WORKLOAD["forcing"])
+
+    def timed(**kw):
+        op.solve(f, rtol=WORKLOAD["rtol"], maxit=1000, **kw)  # warm-up
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(op.stream)
+        u, info = op.solve(f, rtol=WORKLOAD["rtol"], maxit=1000, **kw)
+        e1.record(op.stream)
+        e1.synchronize()
+        return u, info, e0.elapsed_time(e1) / 1e3
+
+    u64, i64, t64 = timed(force_fp64=True)
+    out = {"workload": WORKLOAD["name"], "rtol": WORKLOAD["rtol"],
+           "fp64_fd": {"solve_s": t64, "iterations": i64.iterations, "rel_residual": i64.rel_residual}}
+    u, info, t = timed(fp64_low_fd=True)
+    out["tf32_fd"] = {"solve_s": t, "iterations": info.iterations, "rel_residual": info.rel_residual,
+                      "converged": info.converged, "speedup": t64 / t,
+                      "rel_diff_vs_fp64_fd": float(torch.linalg.vector_norm(u - u64) / torch.linalg.vector_norm(u64))}
+    op.close()
+    opb, _ = make_op(mf, WORKLOAD["p"], WORKLOAD["nel"], mixed=True, fd="bf16", device=device)
+    op = opb
+    u, info, t = timed(fp64_low_fd=True)
+    out["bf16_fd"] = {"solve_s": t, "iterations": info.iterations, "rel_residual": info.rel_residual,
+                      "converged": info.converged, "speedup": t64 / t,
+                      "rel_diff_vs_fp64_fd": float(torch.linalg.vector_norm(u - u64) / torch.linalg.vector_norm(u64))}
+    opb.close()
+    return out
+
+
 ADJOINT = dict(name="ring-p3-nel64-kexp", p=3, nel=64, kscale=0.3, modes_seed=123, rtol=1e-10)
 
 
@@ -637,6 +674,7 @@ def run_ours(args):
         extras["mixed_vs_fp64"] = mixed_vs_fp64(mf, device)
         extras["batched_64"] = batched(mf, device)
         extras["reaction"] = reaction(mf, device)
+        extras["fp64_solve_low_fd"] = fp64_low_fd(mf, device)
         extras["adjoint"] = adjoint(mf, device)
     line = {
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,

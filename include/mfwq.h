@@ -196,6 +196,12 @@ typedef struct {
     int force_fp64;        /* 1: plain FP64 solve even on a mixed handle */
     double* res_hist;      /* host, may be NULL: relative residual after each iteration
                               (maxit + 1 entries) */
+    int fp64_low_fd;       /* 1 (mixed handle, single patch): FP64 BiCGStab as with force_fp64,
+                              with the FD applied in the handle's low precision (FP64 -> FP32,
+                              tensor-core mode products, FP32 -> FP64).  The iterate, the
+                              operator and the residual stay FP64, so the tolerance is met in
+                              FP64; only the preconditioner is inexact.  MFWQ_EINVAL on a
+                              handle without mixed = 1 and in mfwq_batch_solve. */
 } mfwq_solve_opts;
 
 typedef struct {

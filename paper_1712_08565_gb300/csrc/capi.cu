@@ -541,6 +541,24 @@ int solve64(mfwq_handle h, const double* f, double* u, const mfwq_solve_opts& o,
     double* tmp = h->fd_tmp64;
     cudaStream_t s = h->stream;
     LinOp<double> P = [d, tmp, s](const double* in, double* out, const int* skip) { return run_fd64(d, in, out, tmp, skip, s); };
+    if (o.fp64_low_fd) {
+        // the FD in the handle's low precision: FP32 copies in the mixed refinement's
+        // work vectors (unused by an FP64 solve), tensor-core mode products
+        if (!h->mixed) return fail(MFWQ_EINVAL, "fp64_low_fd needs a handle set up with mixed = 1");
+        const size_t N = h->N;
+        float* x32 = h->kv32 + 8 * N;
+        float* z32 = h->kv32 + 9 * N;
+        DirD<float> d32[3] = {h->d32[0], h->d32[1], h->d32[2]};
+        float* tmp32 = h->fd_tmp32;
+        int* err = h->derr;
+        const int prec = h->fd_prec;
+        P = [=](const double* in, double* out, const int* skip) {
+            int st = convert_into<double, float>(in, x32, N, skip, s);
+            if (st == MFWQ_OK) st = run_fd_tc(d32, prec, x32, z32, tmp32, err, skip, s);
+            if (st == MFWQ_OK) st = convert_into<float, double>(z32, out, N, skip, s);
+            return st;
+        };
+    }
     int iters = 0, status = MFWQ_OK;
     double rel = 0.0;
     ST(bicgstab<double>(A, P, f, u, o.use_initial_guess != 0, o.rtol, o.maxit, bufs64(h), h->dsc, h->hsc, h->part, h->N, s,
@@ -825,7 +843,7 @@ int mfwq_solve(mfwq_handle h, const double* f_dev, double* u_dev, const mfwq_sol
     if (!h || !f_dev || !u_dev || f_dev == u_dev) return fail(MFWQ_EINVAL, "bad argument");
     mfwq_solve_opts o = opts ? *opts : default_opts();
     if (!(o.rtol > 0) || o.maxit < 0) return fail(MFWQ_EINVAL, "rtol must be > 0 and maxit >= 0");
-    if (h->mixed && !o.force_fp64) return solve_mixed(h, f_dev, u_dev, o, info);
+    if (h->mixed && !o.force_fp64 && !o.fp64_low_fd) return solve_mixed(h, f_dev, u_dev, o, info);
     return solve64(h, f_dev, u_dev, o, info, false);
 }
 
@@ -1302,6 +1320,7 @@ extern "C" int mfwq_batch_solve(mfwq_batch b, const double* const* f_dev, double
     const int count = (int)b->h.size();
     mfwq_solve_opts o = opts ? *opts : default_opts();
     if (!(o.rtol > 0) || o.maxit < 0) return fail(MFWQ_EINVAL, "rtol must be > 0 and maxit >= 0");
+    if (o.fp64_low_fd) return fail(MFWQ_EINVAL, "fp64_low_fd is for single-patch solves");
     for (int i = 0; i < count; ++i)
         if (!f_dev[i] || !u_dev[i] || f_dev[i] == u_dev[i]) return fail(MFWQ_EINVAL, "bad patch vectors");
     if (!o.force_fp64) {

@@ -426,7 +426,23 @@ __global__ void k_add_f32_scaled(double* __restrict__ u, const float* __restrict
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
         u[i] += sc * (double)d[i];
 }
+template <typename S, typename D>
+__global__ void k_convert(const S* __restrict__ x, D* __restrict__ y, size_t N, const int* skip) {
+    if (skip && *skip) return;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (size_t)gridDim.x * blockDim.x)
+        y[i] = (D)x[i];
+}
 }  // namespace
+
+template <typename S, typename D>
+int convert_into(const S* x, D* y, size_t N, const int* skip, cudaStream_t s) {
+    launch_begin(S_FD_TC, s);
+    k_convert<S, D><<<kRedBlocks, kRedThreads, 0, s>>>(x, y, N, skip);
+    launch_end(S_FD_TC, s);
+    return cudaGetLastError() == cudaSuccess ? MFWQ_OK : MFWQ_ECUDA;
+}
+template int convert_into<double, float>(const double*, float*, size_t, const int*, cudaStream_t);
+template int convert_into<float, double>(const float*, double*, size_t, const int*, cudaStream_t);
 
 template <typename T>
 int axpby_into(const T* f, const T* v, T* r, size_t N, cudaStream_t s) {

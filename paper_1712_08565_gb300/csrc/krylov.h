@@ -53,5 +53,7 @@ int axpby_into(const T* f, const T* v, T* r, size_t N, cudaStream_t s);  // r = 
 int norm2_into(const double* x, size_t N, double* part, double* out, cudaStream_t s);  // *out = |x|^2
 int to_f32_scaled(const double* x, const double* nrm2, float* y, size_t N, cudaStream_t s);   // y = x / |x|
 int add_f32_scaled(double* u, const float* d, const double* nrm2, size_t N, cudaStream_t s);  // u += |x| d
+template <typename S, typename D>
+int convert_into(const S* x, D* y, size_t N, const int* skip, cudaStream_t s);  // y = x rounded to D (skip: no-op)
 
 }  // namespace mfwq

@@ -37,7 +37,7 @@ class SetupDesc(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("inner_maxit", ctypes.c_int), ("use_initial_guess", ctypes.c_int), ("force_fp64", ctypes.c_int),
-                ("res_hist", _c_dptr)]
+                ("res_hist", _c_dptr), ("fp64_low_fd", ctypes.c_int)]
 
 
 class ProfileStats(ctypes.Structure):
@@ -345,8 +345,9 @@ class Operator:
         _check(lib().fd_precond_f32(self._h, _ptr(r, torch.float32, self.N, self.device), _ptr(out, torch.float32, self.N, self.device)))
         return out
 
-    def _opts(self, rtol, maxit, inner_rtol, inner_maxit, x0, force_fp64, history):
+    def _opts(self, rtol, maxit, inner_rtol, inner_maxit, x0, force_fp64, history, fp64_low_fd=False):
         o = SolveOpts()
+        o.fp64_low_fd = 1 if fp64_low_fd else 0
         o.rtol = rtol
         o.maxit = maxit
         o.inner_rtol = inner_rtol
@@ -359,11 +360,11 @@ class Operator:
             o.res_hist = hist.ctypes.data_as(_c_dptr)
         return o, hist
 
-    def _solve(self, fn, f, u, rtol, maxit, inner_rtol, inner_maxit, force_fp64, history, check):
+    def _solve(self, fn, f, u, rtol, maxit, inner_rtol, inner_maxit, force_fp64, history, check, fp64_low_fd=False):
         import torch
         x0 = u is not None
         u = u if u is not None else self._new(self.shape, torch.float64)
-        o, hist = self._opts(rtol, maxit, inner_rtol, inner_maxit, x0, force_fp64, history)
+        o, hist = self._opts(rtol, maxit, inner_rtol, inner_maxit, x0, force_fp64, history, fp64_low_fd)
         info = SolveInfoC()
         st = fn(self._h, _ptr(f, torch.float64, self.N, self.device), _ptr(u, torch.float64, self.N, self.device),
                 ctypes.byref(o), ctypes.byref(info))
@@ -371,19 +372,22 @@ class Operator:
             _check(st)
         h = None
         if hist is not None:
-            last = info.outer_iterations if (self.mixed and not force_fp64) else info.iterations
+            last = info.outer_iterations if (self.mixed and not force_fp64 and not fp64_low_fd) else info.iterations
             h = list(hist[: last + 1])
         return u, SolveInfo(info.status, info.iterations, info.outer_iterations, info.rel_residual, h)
 
     def solve(self, f, u=None, rtol=1e-10, maxit=500, inner_rtol=0.0, inner_maxit=0, force_fp64=False,
-              history=False, check=False):
+              history=False, check=False, fp64_low_fd=False):
         """Solve K~ u = f (FP64 BiCGStab + FD, or mixed refinement on a mixed
-        operator).  u, if given, is the initial guess and receives the result."""
-        return self._solve(lib().mfwq_solve, f, u, rtol, maxit, inner_rtol, inner_maxit, force_fp64, history, check)
+        operator).  u, if given, is the initial guess and receives the result.
+        fp64_low_fd (mixed operator): FP64 BiCGStab with the FD in the
+        operator's low precision (tensor cores); the tolerance is met in FP64."""
+        return self._solve(lib().mfwq_solve, f, u, rtol, maxit, inner_rtol, inner_maxit, force_fp64, history, check,
+                           fp64_low_fd)
 
-    def solve_T(self, g, lam=None, rtol=1e-10, maxit=500, history=False, check=False):
-        """Solve the adjoint system K~^T lambda = g (FP64)."""
-        return self._solve(lib().mfwq_solve_T, g, lam, rtol, maxit, 0.0, 0, True, history, check)
+    def solve_T(self, g, lam=None, rtol=1e-10, maxit=500, history=False, check=False, fp64_low_fd=False):
+        """Solve the adjoint system K~^T lambda = g (FP64; fp64_low_fd as in solve)."""
+        return self._solve(lib().mfwq_solve_T, g, lam, rtol, maxit, 0.0, 0, True, history, check, fp64_low_fd)
 
     def solve_host(self, f_host: np.ndarray, out: np.ndarray | None = None, x0: np.ndarray | None = None,
                    rtol=1e-10, maxit=500, inner_rtol=0.0, inner_maxit=0, force_fp64=False):

@@ -48,7 +48,7 @@ int main(int argc, char** argv) {
     double* fh = (double*)malloc(sizeof(double) * N);
     double* uh = (double*)malloc(sizeof(double) * N);
     cudaMemcpy(fh, f, sizeof(double) * N, cudaMemcpyDeviceToHost);
-    mfwq_solve_opts o = {rtol, 1000, 0.0, 0, 0, 0, NULL};
+    mfwq_solve_opts o = {.rtol = rtol, .maxit = 1000, .res_hist = NULL};
     mfwq_solve_info info;
     const int st = mfwq_solve_host(h, fh, uh, &o, &info);
     if (st != MFWQ_OK) {

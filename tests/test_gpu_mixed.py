@@ -103,6 +103,44 @@ def test_mixed_refinement_reaches_fp64_residual(mf, fd):
     op.close()
 
 
+@pytest.mark.parametrize("fd", ["tf32", "bf16"])
+def test_fp64_solve_with_low_precision_fd(mf, fd):
+    """FP64 BiCGStab with the tensor-core FD as preconditioner (fp64_low_fd):
+    the iterate, the operator and the residual are FP64, so the FP64 tolerance
+    holds with the oracle's operator, for K~ and for K~^T; the solution agrees
+    with the plain FP64 solve to what the two residuals guarantee."""
+    ps, nel = (4, 4, 4), (10, 9, 11)
+    op, tabs, C6 = _setup(mf, ps, nel, fd)
+    f = op.load_vector("ring", "sines")
+    u, info = op.solve(f, rtol=1e-10, fp64_low_fd=True)
+    assert info.converged and info.outer_iterations == 0 and info.rel_residual <= 1e-10, info
+    K = O.stiffness_wq(tabs, O.full_coeff(C6))
+    fn = f.cpu().numpy().ravel()
+    un = u.cpu().numpy().ravel()
+    assert np.linalg.norm(fn - K @ un) <= 1.01e-10 * np.linalg.norm(fn)
+    u64, i64 = op.solve(f, rtol=1e-10, force_fp64=True)
+    assert i64.converged
+    u64n = u64.cpu().numpy().ravel()
+    Kd = K.toarray() if hasattr(K, "toarray") else np.asarray(K)
+    smin = np.linalg.svd(Kd, compute_uv=False)[-1]
+    bound = (np.linalg.norm(fn - K @ un) + np.linalg.norm(fn - K @ u64n)) / smin
+    assert np.linalg.norm(un - u64n) <= 1.01 * bound
+    lam, il = op.solve_T(f, rtol=1e-10, fp64_low_fd=True)
+    assert il.converged
+    assert np.linalg.norm(fn - K.T @ lam.cpu().numpy().ravel()) <= 1.01e-10 * np.linalg.norm(fn)
+    op.close()
+
+
+def test_fp64_low_fd_needs_a_mixed_handle(mf):
+    knots = [inputs.open_uniform_knots(3, n) for n in (5, 6, 7)]
+    op = mf.Operator(3, knots, device=DEV)
+    op.set_coeff(op.eval_coeff("ring"))
+    f = op.load_vector("ring", "sines")
+    with pytest.raises(mf.MfwqError):
+        op.solve(f, fp64_low_fd=True)
+    op.close()
+
+
 def test_mixed_requires_small_directions(mf):
     knots = [inputs.open_uniform_knots(2, 300)] * 3
     with pytest.raises(mf.MfwqError) as e:
