@@ -28,6 +28,7 @@ struct XArgs {
     TileD<T> BX;   // B in two-point tiles (tiled mapping)
     TileD<T> WX;   // W in two-output tiles (tiled mapping)
     int n1, nq1, nlines;
+    int wnb;       // W rows at each end with a band length other than the middle row's
     size_t cs;     // element stride between the coefficient fields of C
     size_t gs;     // element stride between the fields of the gradient output
     const T* C;    // [6][cs], the first Nq of each field used
@@ -47,6 +48,7 @@ XArgs<T> xargs(const DirD<T>& d1, int nlines, size_t cs, const T* C) {
     a.n1 = d1.n;
     a.nq1 = d1.nq;
     a.nlines = nlines;
+    a.wnb = d1.wnb;
     a.cs = cs;
     a.gs = 0;
     a.C = C;

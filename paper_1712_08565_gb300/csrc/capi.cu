@@ -443,6 +443,16 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
         x.we = y.we = reinterpret_cast<const double*>(base + WE[l]);
         x.BX = tiles_at<double>(base, to[l][0]);
         x.WX = tiles_at<double>(base, to[l][1]);
+        {
+            // W rows at each end whose band length differs from the middle row's, so
+            // that the x stage can give the uniform rows warps of their own
+            const Band1D& W = h->dir[l].W;
+            const int nr = W.rows, lm = nr > 0 ? W.len[nr / 2] : 0;
+            int nb = 0;
+            for (int i = 0; i < nr; ++i)
+                if (W.len[i] != lm) nb = std::max(nb, std::min(i + 1, nr - i));
+            x.wnb = y.wnb = 2 * nb < nr ? nb : 0;
+        }
         x.SX = detect_stencil(h->dir[l]);
         y.SX = stencil_as<float>(x.SX);
         y.BX = tiles_at<float>(base, to[l][0]);

@@ -112,6 +112,7 @@ struct DirD {
     BandD<T> E;       // B-spline values and derivatives at the error points
     TileD<T> BX, WX;  // B and W in two-row tiles (the tiled x stage)
     StencilD<T> SX;   // translation-invariant interior of B and W (the stencil x stage)
+    int wnb;          // W rows at each end whose band length differs from the middle row's (0: none split off)
     int ne;           // error points
     const double* xe; // error points and weights (always FP64)
     const double* we;

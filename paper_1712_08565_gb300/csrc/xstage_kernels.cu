@@ -164,10 +164,22 @@ __global__ void __launch_bounds__(kThreads) k_xstage_apply(XArgs<T> a, const T* 
         __syncthreads();
         // outputs; x-family (a1, b1) = ([alpha = 1], [beta = 1])
         if (MAP == 0) {
-            const int per = nl * n1;
-            for (int e = threadIdx.x; e < 3 * per; e += blockDim.x) {
-                const int al = e / per, rem = e - al * per;
-                const int l = rem / n1, i = rem - l * n1;
+            // items (alpha, line, i): first the rows of uniform band length (wnb <= i <
+            // n1 - wnb) of all (alpha, line), then the 2 wnb end rows of each, so that
+            // the warps walking the longer end bands are few and hold nothing else
+            const int nb = a.wnb, ni = n1 - 2 * nb, rows = 3 * nl;
+            for (int e = threadIdx.x; e < rows * n1; e += blockDim.x) {
+                int row, i;
+                if (e < rows * ni) {
+                    row = e / ni;
+                    i = nb + (e - row * ni);
+                } else {
+                    const int k = e - rows * ni;
+                    row = k / (2 * nb);
+                    const int j = k - row * 2 * nb;
+                    i = j < nb ? j : ni + j;
+                }
+                const int al = row / nl, l = row - al * nl;
                 const int fam = 2 * (al == 0 ? 1 : 0) + bfam;
                 const int s = a.W.start[i], L = a.W.len[i];
                 const T* H = sH + (al * LINES + l) * nq1 + s;
