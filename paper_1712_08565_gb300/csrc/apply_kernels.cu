@@ -358,8 +358,13 @@ __global__ void __launch_bounds__(kAuxMaxThreads) k_xstage_applyT(XArgs<T> a, Pt
         for (int k = 0; k < 9; ++k) sR[(k * kLines + l) * n1 + j] = rin.p[k][gi];
     }
     __syncthreads();
+    // points in parity order (even q, then odd q): the transposed W rows of
+    // interior points of one parity have one band length, so a warp's lanes
+    // leave the tap loop together
+    const int half = (nq1 + 1) >> 1;
     for (int e = threadIdx.x; e < nl * nq1; e += blockDim.x) {
-        const int l = e / nq1, q = e - l * nq1;
+        const int l = e / nq1, r = e - l * nq1;
+        const int q = r < half ? 2 * r : 2 * (r - half) + 1;
         const int s = a.WT.start[q], L = a.WT.len[q];
         const int fs = kLines * n1;
         const T* R = sR + l * n1 + s;
@@ -428,8 +433,11 @@ __global__ void __launch_bounds__(kAuxMaxThreads) k_xstage_grad(XArgs<T> a, cons
         for (int k = 0; k < 9; ++k) sR[(k * kLines + l) * n1 + j] = rin.p[k][gi];
     }
     __syncthreads();
+    // points in parity order, as in the transposed x stage
+    const int half = (nq1 + 1) >> 1;
     for (int e = threadIdx.x; e < nl * nq1; e += blockDim.x) {
-        const int l = e / nq1, q = e - l * nq1;
+        const int l = e / nq1, r = e - l * nq1;
+        const int q = r < half ? 2 * r : 2 * (r - half) + 1;
         const int fs = kLines * n1;
         T g1 = 0, g2 = 0, g3 = 0;
         {
