@@ -16,6 +16,10 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kRT = 4;  // output rows per thread (slow dims)
 constexpr int kAT = 4;  // output rows per thread (fast dim)
+// Threads per block of the two dense mode-product launches: finer than 256, so
+// the last blocks of a launch leave less of the FP64 pipe idle (FD at 130^3:
+// 1.72 -> 1.61 ms).
+constexpr int kDenseThreads = 128;
 
 __device__ __forceinline__ double fmaT(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a, b, c); }
@@ -132,11 +136,11 @@ template <typename T>
 cudaError_t dense_slow(const T* M, const T* in, T* out, int A, int ld, int nin, int nout, int inoff, int outoff, int C,
                        const T* l1, const T* l2, const T* l3, int n1, const int* skip, cudaStream_t s) {
     size_t AC = (size_t)A * C;
-    unsigned bx = (unsigned)((AC + kThreads - 1) / kThreads);
+    unsigned bx = (unsigned)((AC + kDenseThreads - 1) / kDenseThreads);
     if (bx > 65535u) bx = 65535u;
     dim3 grid(bx, (nout + kRT - 1) / kRT);
     launch_begin(S_FD_DIM23, s);
-    k_dense_slow<T><<<grid, kThreads, 0, s>>>(M, in, out, A, ld, nin, nout, inoff, outoff, C, l1, l2, l3, n1, skip);
+    k_dense_slow<T><<<grid, kDenseThreads, 0, s>>>(M, in, out, A, ld, nin, nout, inoff, outoff, C, l1, l2, l3, n1, skip);
     launch_end(S_FD_DIM23, s);
     return cudaGetLastError();
 }
@@ -145,10 +149,10 @@ template <typename T>
 cudaError_t dense_fast(const T* MT, const T* in, T* out, int A, int ld, int nin, int nout, int inoff, int outoff,
                        const int* skip, cudaStream_t s) {
     size_t total = (size_t)((A + kAT - 1) / kAT) * nout;
-    size_t blocks = (total + kThreads - 1) / kThreads;
+    size_t blocks = (total + kDenseThreads - 1) / kDenseThreads;
     if (blocks > 1u << 20) blocks = 1u << 20;
     launch_begin(S_FD_DIM1, s);
-    k_dense_fast<T><<<(unsigned)blocks, kThreads, 0, s>>>(MT, in, out, A, ld, nin, nout, inoff, outoff, skip);
+    k_dense_fast<T><<<(unsigned)blocks, kDenseThreads, 0, s>>>(MT, in, out, A, ld, nin, nout, inoff, outoff, skip);
     launch_end(S_FD_DIM1, s);
     return cudaGetLastError();
 }
