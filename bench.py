@@ -202,9 +202,12 @@ def profiled_traffic(kernel: str, workload: str):
     return None
 
 
-def xstage_kernel_name(code: int, elem: str) -> str:
-    """Kernel that runs the forward x stage for an autotune code."""
+def xstage_kernel_name(code: int, elem: str, p: int) -> str:
+    """Kernel that runs the forward x stage for an autotune code (degree p in
+    direction 1 names the stencil mapping's instance)."""
     L, mode, carve = code % 10, (code // 10) % 10, (code // 1000) % 10
+    if mode == 6:
+        return "k_xstage_stencil<%s, %d>" % (elem, p)
     if mode >= 4:
         return "k_xstage_tiled<%s, %d, %d>" % (elem, 4 if mode == 4 else 8, carve)
     return "k_xstage_apply<%s, %d, %d, %d>" % (elem, L, mode, carve)
@@ -634,7 +637,7 @@ def run_ours(args):
     dom_ms = stages[dom][0] / stages[dom][1]
     achieved = flops[dom] / (dom_ms * 1e-3) / 1e12
     peak = fp64_peak_tflops()
-    dom_kernel = xstage_kernel_name(op.tune_code, "double") if dom == "xstage" and op.tune_code else dom
+    dom_kernel = xstage_kernel_name(op.tune_code, "double", WORKLOAD["p"]) if dom == "xstage" and op.tune_code else dom
     roofline = {"bound": "alu", "kernel": dom, "kernel_function": dom_kernel, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": profiled_traffic(dom_kernel, WORKLOAD["name"]),
                 "peak_source": "FP64 pipe: 152 SMs x 2070 MHz x 4 flop/clk (1.25 TFLOP/s nominal); not in MEASURED_PEAKS.json",
