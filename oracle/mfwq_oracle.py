@@ -18,7 +18,7 @@ efficient isogeometric k-method"):
 * Section 3.2  -- the factorisation K~ = sum_ab W^(ab) D^(ab) B^(b), Algorithm 2.
 * Section 4    -- ring domain, Eq. (exact-solution), BiCGStab + FD preconditioner.
 
-Readings of passages the paper leaves open (each is listed in the design doc):
+Readings of passages the paper leaves open (both implementations follow each one):
 
 * R1  WQ points: all interior knots, the midpoints of the interior spans, and
       p+1 equispaced interior points in the first and in the last span
