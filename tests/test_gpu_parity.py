@@ -40,6 +40,7 @@ CASES = [
     ("ring-p6", (6, 6, 6), (7, 6, 8), "uniform", "ring", 2),
     ("jitter-p5", (5, 5, 5), (8, 9, 7), "jitter", "ring", 3),
     ("min-p4", (4, 4, 4), (2, 3, 2), "uniform", "ring", None),
+    ("min-p2", (2, 2, 2), (2, 2, 3), "uniform", "ring", 5),
     ("ring-p2-wide", (2, 2, 2), (40, 3, 4), "uniform", "ring", 4),
 ]
 
