@@ -260,6 +260,10 @@ int mfwq_sync(mfwq_handle h);
  * MFWQ_NOALLOC_MAX_N doubles (32 MB) that is part of the library's module, so
  * every GPU that loads the library holds it until the process exits.
  * - n1*n2*n3 > MFWQ_NOALLOC_MAX_N is rejected with MFWQ_EINVAL.
+ * - Every pointer (factors, r, z) must be device memory of the calling
+ *   thread's current device (or managed memory), and `stream` must belong to
+ *   that device: the scratch address is the current device's.  Host memory
+ *   and other devices' memory are rejected with MFWQ_EINVAL before any work.
  * - The first call on a device looks the array's address up
  *   (cudaGetSymbolAddress, which may load the module); make that first call
  *   before any stream capture.

@@ -44,8 +44,9 @@ Readings of passages the paper leaves open (both implementations follow each one
       is U diag(1/(l1+l2+l3+sigma)) U^T with the same U (sigma >= 0 chosen by
       the caller; the paper gives no preconditioner for alpha > 0).
 
-Parity unpinned (no value in the paper or in mathematics fixes them):
-boundary-row weight values beyond their exactness residual, BiCGStab
+Boundary-row weights are pinned by exactness, support and the minimum-norm
+property (w_i in range(A_i^T)); the paper prints no weight values.
+Parity unpinned (nothing in the paper or in mathematics fixes them): BiCGStab
 iteration counts.
 """
 from __future__ import annotations

@@ -56,6 +56,19 @@ int scratch_address(double** out) {
     return MFWQ_OK;
 }
 
+// True if p is device (or managed) memory that device dev can address as its
+// own: allocated on dev, or managed.  Host memory, pinned host memory and
+// other devices' memory are refused.
+bool on_device(const void* p, int dev) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
 }  // namespace
 
 extern "C" int mfwq_fd_precond_noalloc(const int n[3], const double* const U_dev[3], const double* const UT_dev[3],
@@ -70,11 +83,33 @@ extern "C" int mfwq_fd_precond_noalloc(const int n[3], const double* const U_dev
             mfwq::set_last_error("mfwq_fd_precond_noalloc: bad size or factor pointer in direction " + std::to_string(l + 1));
             return MFWQ_EINVAL;
         }
+        // reject before multiplying, so that no product can wrap around
+        if ((size_t)n[l] > kNoAllocMaxN / N) {
+            mfwq::set_last_error("mfwq_fd_precond_noalloc: n1*n2*n3 exceeds the fixed scratch of " +
+                                 std::to_string(kNoAllocMaxN) + " doubles");
+            return MFWQ_EINVAL;
+        }
         N *= (size_t)n[l];
     }
-    if (N > kNoAllocMaxN) {
-        mfwq::set_last_error("mfwq_fd_precond_noalloc: n1*n2*n3 = " + std::to_string(N) +
-                             " exceeds the fixed scratch of " + std::to_string(kNoAllocMaxN) + " doubles");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        mfwq::set_last_error("mfwq_fd_precond_noalloc: no usable current device");
+        return MFWQ_ECUDA;
+    }
+    // every buffer must be device memory of the current device: the scratch
+    // address below is this device's, and a kernel given another device's (or
+    // host) memory would fault or read the wrong memory
+    for (int l = 0; l < 3; ++l) {
+        if (!on_device(U_dev[l], dev) || !on_device(UT_dev[l], dev) || !on_device(lam_dev[l], dev)) {
+            mfwq::set_last_error("mfwq_fd_precond_noalloc: an FD factor of direction " + std::to_string(l + 1) +
+                                 " is not device memory of the current device " + std::to_string(dev));
+            return MFWQ_EINVAL;
+        }
+    }
+    if (!on_device(r_dev, dev) || !on_device(z_dev, dev)) {
+        mfwq::set_last_error("mfwq_fd_precond_noalloc: r or z is not device memory of the current device " +
+                             std::to_string(dev));
         return MFWQ_EINVAL;
     }
     double* scratch = nullptr;

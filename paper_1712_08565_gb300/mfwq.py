@@ -132,9 +132,12 @@ def fd_precond_noalloc(n, U, UT, lam, r, z, stream=None):
     Up = (ctypes.c_void_p * 3)(*[_ptr(U[l], torch.float64, nn[l] * nn[l], dev).value for l in range(3)])
     UTp = (ctypes.c_void_p * 3)(*[_ptr(UT[l], torch.float64, nn[l] * nn[l], dev).value for l in range(3)])
     Lp = (ctypes.c_void_p * 3)(*[_ptr(lam[l], torch.float64, nn[l], dev).value for l in range(3)])
-    s = stream if stream is not None else torch.cuda.current_stream(dev)
-    _check(lib().mfwq_fd_precond_noalloc(nn, Up, UTp, Lp, _ptr(r, torch.float64, N, dev), _ptr(z, torch.float64, N, dev),
-                                         ctypes.c_void_p(s.cuda_stream)))
+    # the library takes its scratch address from the current device, so make
+    # r's device current for the call
+    with torch.cuda.device(dev):
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        _check(lib().mfwq_fd_precond_noalloc(nn, Up, UTp, Lp, _ptr(r, torch.float64, N, dev),
+                                             _ptr(z, torch.float64, N, dev), ctypes.c_void_p(s.cuda_stream)))
     return z
 
 

@@ -8,6 +8,7 @@ import os
 
 import numpy as np
 import pytest
+import scipy.linalg
 import scipy.sparse.linalg as spla
 from scipy.interpolate import BSpline
 
@@ -103,6 +104,121 @@ def test_weights_exactness_and_support(p):
                 assert np.all(W[i, outside] == 0.0)
                 if p < i < tab.n - 1 - p:
                     assert np.count_nonzero(~outside) == 2 * p + 1
+
+
+def _mp_basis(t, p, x, deriv):
+    """B-spline values (deriv 0) or first derivatives (deriv 1) of all
+    functions at x by de Boor's recursion in mpmath (this test's own
+    evaluation, independent of the oracle's)."""
+    import mpmath as mp
+    m = len(t) - p - 1
+    nb = len(t) - 1
+    last = max(i for i in range(nb) if t[i] < t[i + 1])
+    N = [mp.mpf(1) if (t[i] <= x < t[i + 1]) or (i == last and x == t[i + 1]) else mp.mpf(0) for i in range(nb)]
+    for k in range(1, p + 1 - deriv):
+        M = []
+        for i in range(len(t) - k - 1):
+            v = mp.mpf(0)
+            if t[i + k] > t[i]:
+                v += (x - t[i]) / (t[i + k] - t[i]) * N[i]
+            if t[i + k + 1] > t[i + 1]:
+                v += (t[i + k + 1] - x) / (t[i + k + 1] - t[i + 1]) * N[i + 1]
+            M.append(v)
+        N = M
+    if not deriv:
+        return N[:m]
+    out = []
+    for i in range(m):
+        v = mp.mpf(0)
+        if t[i + p] > t[i]:
+            v += p * N[i] / (t[i + p] - t[i])
+        if t[i + p + 1] > t[i + 1]:
+            v -= p * N[i + 1] / (t[i + p + 1] - t[i + 1])
+        out.append(v)
+    return out
+
+
+def _weight_systems(tab, knots, p):
+    """(a, b, i, S, T) of every weight system: the row i's points S (open
+    support, Eq. (weights-support)) and test functions T (|j - i| <= p)."""
+    for (a, b) in tab.W:
+        for i in range(tab.n):
+            gi = i + 1
+            S = np.nonzero((tab.xq > knots[gi]) & (tab.xq < knots[gi + p + 1]))[0]
+            T = np.array([j for j in range(tab.n) if abs(j - i) <= p])
+            yield a, b, i, S, T
+
+
+def _nullspace_share_f64(A, w):
+    """|P_null(A) w| / |w| and the condition number of A (float64 SVD)."""
+    _, s, Vt = np.linalg.svd(A)
+    rank = int(np.sum(s > s[0] * 1e-13))
+    N = Vt[rank:]
+    share = np.linalg.norm(N @ w) / np.linalg.norm(w) if N.shape[0] else 0.0
+    return share, s[0] / s[rank - 1], rank
+
+
+@pytest.mark.parametrize("p", list(range(2, 8)))
+def test_weights_are_minimum_norm(p):
+    """Reading R2: the under-determined weight systems take their
+    minimum-2-norm solution, i.e. w_i lies in range(A_i^T), so its projection
+    onto null(A_i) vanishes.  A_i (rows j in T, columns q in S) from scipy's
+    B-splines; float64 resolves the null space to about eps * kappa(A_i), so
+    the bound is 1e-14 kappa(A_i) (kappa <= 4e11 for p <= 7), against an O(1)
+    share for any other solution (checked on a basic solution)."""
+    for knots in (O.uniform_knots(p, max(2 * p + 3, 8)), _nonuniform_knots(p, 2 * p + 4, seed=10 + p)):
+        tab = O.tables_1d(knots, p)
+        m = len(knots) - p - 1
+        F = {b: _scipy_basis(knots, p, tab.xq, b)[:, 1:m - 1] for b in (0, 1)}
+        under = 0
+        for a, b, i, S, T in _weight_systems(tab, knots, p):
+            A = F[b][np.ix_(S, T)].T
+            w = tab.W[(a, b)][i, S]
+            share, kappa, rank = _nullspace_share_f64(A, w)
+            if rank == len(S):
+                continue
+            under += 1
+            assert share <= 1e-14 * kappa, (a, b, i, share, kappa)
+            if under == 1:
+                # a basic solution of the same system (nonzero on `rank` points only) is not minimum-norm
+                piv = scipy.linalg.qr(A, pivoting=True)[2][:rank]
+                wb = np.zeros(len(S))
+                wb[piv] = np.linalg.lstsq(A[:, piv], A @ w, rcond=None)[0]
+                assert np.abs(A @ wb - A @ w).max() <= 1e-9 * np.abs(A @ w).max()
+                assert _nullspace_share_f64(A, wb)[0] > 1e-3
+        assert under >= 2 * p  # the first and last p rows at least
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("p,kind", [(8, "uniform"), (10, "jittered")])
+def test_weights_are_minimum_norm_high_degree(p, kind):
+    """As test_weights_are_minimum_norm for p = 8, 10, where kappa(A_i) reaches
+    1e13 and float64 cannot find null(A_i): A_i and its SVD in 50-digit
+    mpmath (this test's own de Boor recursion); the float64 weights (the
+    oracle's decimal solution rounded once) must then have a null-space share
+    of rounding size."""
+    import mpmath as mp
+    knots = O.uniform_knots(p, max(2 * p + 3, 8)) if kind == "uniform" else _nonuniform_knots(p, 2 * p + 4, seed=10 + p)
+    tab = O.tables_1d(knots, p)
+    with mp.workdps(50):
+        tm = [mp.mpf(float(v)) for v in knots]
+        xm = [mp.mpf(float(v)) for v in tab.xq]
+        vals = {b: [_mp_basis(tm, p, x, b) for x in xm] for b in (0, 1)}
+        under = 0
+        for a, b, i, S, T in _weight_systems(tab, knots, p):
+            if len(S) == len(T):
+                continue  # square systems of full rank have one solution
+            A = mp.matrix([[vals[b][q][j + 1] for q in S] for j in T])
+            _, s, V = mp.svd_r(A)
+            smax = max(abs(v) for v in s)
+            rank = sum(1 for v in s if abs(v) > smax * mp.mpf(10) ** -30)
+            if rank == len(S):
+                continue
+            under += 1
+            w = [mp.mpf(float(tab.W[(a, b)][i, q])) for q in S]
+            share = mp.sqrt(sum(sum(V[r, k] * w[k] for k in range(len(S))) ** 2 for r in range(rank, V.rows)))
+            assert float(share / mp.sqrt(sum(v * v for v in w))) <= 1e-14, (a, b, i)
+        assert under >= 2 * p
 
 
 def test_basis_tables_match_scipy():

@@ -84,4 +84,42 @@ def test_noalloc_binding_and_limits(mf):
     st = mf.lib().mfwq_fd_precond_noalloc((ctypes.c_int * 3)(*op.n), dummy, dummy, dummy,
                                           ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(r.data_ptr()), None)
     assert st == -1  # aliased input and output
+    # a size triple whose product wraps around 2^64 in size_t is rejected too
+    wrap = (ctypes.c_int * 3)(1 << 21, 1 << 21, 1 << 22)
+    st = mf.lib().mfwq_fd_precond_noalloc(wrap, dummy, dummy, dummy, ctypes.c_void_p(r.data_ptr()),
+                                          ctypes.c_void_p(z.data_ptr()), None)
+    assert st == -1 and b"exceeds" in mf.lib().mfwq_last_error()
+    # host memory (pageable or pinned) in place of r is rejected before any launch
+    n0 = mf.kernel_launches()
+    for host in (np.zeros(op.N), torch.zeros(op.N, dtype=torch.float64).pin_memory()):
+        hp = host.ctypes.data if isinstance(host, np.ndarray) else host.data_ptr()
+        Pd = lambda ts: (ctypes.c_void_p * 3)(*[t.data_ptr() for t in ts])
+        st = mf.lib().mfwq_fd_precond_noalloc((ctypes.c_int * 3)(*op.n), Pd(U), Pd(UT), Pd(lam), ctypes.c_void_p(hp),
+                                              ctypes.c_void_p(z.data_ptr()), None)
+        assert st == -1 and b"not device memory" in mf.lib().mfwq_last_error()
+    assert mf.kernel_launches() == n0
+    op.close()
+
+
+@pytest.mark.skipif(not torch.cuda.is_available() or torch.cuda.device_count() < 2, reason="needs two CUDA devices")
+def test_noalloc_on_second_device(mf):
+    """Tensors on cuda:1 while cuda:0 is current: the binding makes r's device
+    current, and the raw call with cuda:0 current refuses cuda:1 memory."""
+    ps, nel = (3, 3, 3), (6, 5, 7)
+    knots = [inputs.open_uniform_knots(ps[l], nel[l]) for l in range(3)]
+    dev1 = torch.device("cuda", 1)
+    op = mf.Operator(ps, knots, device=dev1)
+    U, UT, lam = _factors(mf, ps, knots)
+    U, UT, lam = [t.to(dev1) for t in U], [t.to(dev1) for t in UT], [t.to(dev1) for t in lam]
+    r = torch.from_numpy(inputs.uniform_vector(op.shape, 34)).to(dev1)
+    z = torch.empty_like(r)
+    with torch.cuda.device(0):
+        mf.fd_precond_noalloc(op.n, U, UT, lam, r, z)
+        ref = op.fd_precond(r)
+        torch.cuda.synchronize(dev1)
+        assert float((z - ref).abs().max()) <= TOL * float(ref.abs().max())
+        Pd = lambda ts: (ctypes.c_void_p * 3)(*[t.data_ptr() for t in ts])
+        st = mf.lib().mfwq_fd_precond_noalloc((ctypes.c_int * 3)(*op.n), Pd(U), Pd(UT), Pd(lam),
+                                              ctypes.c_void_p(r.data_ptr()), ctypes.c_void_p(z.data_ptr()), None)
+        assert st == -1 and b"current device" in mf.lib().mfwq_last_error()
     op.close()
