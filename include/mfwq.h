@@ -123,8 +123,26 @@ int mfwq_eval_coeff(mfwq_handle h, int geometry, const double* modes_host, int n
                     double kscale, double* C_dev);
 
 /* Copies C_dev[6][Nq] into the handle (and an FP32 copy when mixed).  The
- * caller's buffer may be reused afterwards.  Asynchronous. */
+ * caller's buffer may be reused afterwards.  Turns off a coefficient
+ * evaluated in the FP32 operator (mfwq_set_coeff_field).  Asynchronous. */
 int mfwq_set_coeff(mfwq_handle h, const double* C_dev);
+
+/* Sets the coefficient from its definition: C = |det J| J^-1 K J^-T (Eq. (C))
+ * for the given geometry and K(x) = exp(kscale g(x)) I, g as in
+ * mfwq_eval_coeff (modes_host: nmodes rows (a, k1, k2, k3, phi), nmodes <= 32).
+ * The FP64 coefficient is evaluated and stored as by mfwq_eval_coeff followed
+ * by mfwq_set_coeff.  With onthefly = 1 (mixed handles) the FP32 operator does
+ * not store C at all: its x stage evaluates C at every quadrature point from
+ * the map and the field, the memory-lean form of the paper's remark on
+ * storing the coefficient (Section 3.2), and the 6 Nq FP32 values are freed.
+ * Both geometries give C = kappa(x) G(xi1), with G = |det J| J^-1 J^-T a
+ * function of xi1 alone, so G is a table over the direction-1 points and
+ * kappa = exp(kscale g(F(xi))) is computed per point in FP32 (CUDA's cospif and
+ * expf, phase reduced modulo one period before rounding).  onthefly = 1 needs
+ * the stencil form of the x stage (p_1 <= 8) and makes the FP32 operator use
+ * it.  MFWQ_EINVAL on a bad argument or an unsupported handle.  Synchronous. */
+int mfwq_set_coeff_field(mfwq_handle h, int geometry, const double* modes_host, int nmodes, double kscale,
+                         int onthefly);
 
 /* ---- reaction (mass) term: alpha u in Eq. (poisson) ----------------------
  * The discrete operator becomes K~ + M~ with the WQ mass matrix of Eq. (Mwq),
@@ -186,6 +204,24 @@ int fd_precond(mfwq_handle h, const double* r_dev, double* z_dev);
 /* z = P^-1 r in the handle's low precision (TF32 or BF16 tensor-core mode
  * products, FP32 accumulate, FP32 in and out; needs mixed = 1). */
 int fd_precond_f32(mfwq_handle h, const float* r_dev, float* z_dev);
+
+/* The FP32 operator of a mixed handle runs in one of two kernel sequences
+ * that compute the same Algorithm 2 (results agree to FP32 rounding):
+ *  MFWQ_PATH_STAGED: five kernels, one banded contraction direction each (the
+ *    x stage fusing the trial x contraction, the coefficient product and the
+ *    test x contraction), partial tensors passed through device memory;
+ *  MFWQ_PATH_FUSED: trial z, then one kernel for the trial y contraction, the
+ *    x stage and the test y contraction per (q3 plane, run of q2 lines), with
+ *    the y partials kept on chip, then test z.  Available where the stencil
+ *    form of the x stage is (p_1 <= 8); not used while a reaction term is on.
+ * The staged path is the default; mfwq_autotune times both and keeps the faster.
+ * mfwq_set_fp32_path returns MFWQ_EINVAL (reason in mfwq_last_error) for
+ * MFWQ_PATH_FUSED where it is unavailable; mfwq_fp32_path returns the path in
+ * use.  Neither launches work. */
+#define MFWQ_PATH_STAGED 0
+#define MFWQ_PATH_FUSED 1
+int mfwq_set_fp32_path(mfwq_handle h, int path);
+int mfwq_fp32_path(mfwq_handle h);
 
 typedef struct {
     double rtol;           /* stop when ||f - K~ u||_2 <= rtol ||f||_2 */
@@ -289,7 +325,9 @@ int mfwq_fd_precond_noalloc(const int n[3], const double* const U_dev[3], const 
  * copies, where the slabs allow it; 4 and 5: 8 lines per block, a thread owns
  * a two-row tile and 4 or 8 lines; each with the default or a reduced
  * shared-memory carveout), then 1, 2 or 4 output rows per thread in the other
- * four stages.  *xlines_out (may be NULL) receives the FP64 choice as
+ * four stages, and for the FP32 operator the fused kernel sequence
+ * (MFWQ_PATH_FUSED, where available) against the best staged one (cached
+ * codes add 10000 when the fused one won).  *xlines_out (may be NULL) receives the FP64 choice as
  * 1000 * carveout + 100 * rows + 10 * mapping + lines.  cache_path (may be
  * NULL) is a file of JSON lines {"key": "...", "xstage": that code}: a hit
  * skips the timing, a miss appends the result (codes below 100 mean one row
@@ -337,7 +375,8 @@ int mfwq_selftest_bounded_wait(long long limit_cycles, void* stream);
  * xstage_T, trial_yT, trial_zT (the transpose), xstage_grad, fd_dim1,
  * fd_dim23, fd_tc (FD mode products), krylov (BiCGStab vector and scalar
  * kernels), setup, fd_fold (even/odd folding of the FP64 FD), mass (the
- * reaction-term passes), h1_error (mfwq_h1_error). */
+ * reaction-term passes), h1_error (mfwq_h1_error), fused_xy (the fused FP32
+ * trial-y / x / test-y kernel). */
 #define MFWQ_NSTAGES 24
 typedef struct {
     double ms[MFWQ_NSTAGES];           /* summed device time per stage (CUDA events) */

@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "apply_common.cuh"
+#include "fused_apply.h"
 #include "kernels.h"
 #include "prof.h"
 
@@ -769,6 +770,18 @@ int run_apply(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
     // trial z
     OpTrialZ<T> oz{d3.B, x, Z0, Z1};
     if ((e = launch_slow(S_TRIAL_Z, oz, 1, n3, q3, n2 * n1, skip, c.stream, c.srows)) != cudaSuccess) return MFWQ_ECUDA;
+    if constexpr (sizeof(T) == 4) {
+        if (c.fused && c.fused->ok && !c.cm) {
+            // trial y, x stage and test y in one kernel; U in the (unused) P region
+            if (launch_fused(c, *c.fused, Z0, Z1, P, SQ, skip) != cudaSuccess) return MFWQ_ECUDA;
+            OpTestZ<T> otz;
+            otz.band = d3.W;
+            for (int f = 0; f < 4; ++f) otz.in[f] = P + f * SQ;
+            otz.out = y;
+            if (launch_slow(S_TEST_Z, otz, 1, q3, n3, n2 * n1, skip, c.stream, c.srows) != cudaSuccess) return MFWQ_ECUDA;
+            return MFWQ_OK;
+        }
+    }
     // trial y
     OpTrialY<T> oy{d2.B, Z0, Z1, Y[0], Y[1], Y[2]};
     if ((e = launch_slow(S_TRIAL_Y, oy, q3, n2, q2, n1, skip, c.stream, c.srows)) != cudaSuccess) return MFWQ_ECUDA;

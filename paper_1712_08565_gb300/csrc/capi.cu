@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "fused_apply.h"
 #include "kernels.h"
 #include "krylov.h"
 #include "prof.h"
@@ -287,6 +288,11 @@ struct mfwq_handle_s {
     Profiler prof;
     double* hnorm = nullptr; // pinned, 2 doubles
     double* host_io = nullptr;  // device f/u buffers of mfwq_solve_host (2 N), lazily
+    FusedPlan fplan;            // fused FP32 apply (mixed handles with a stencil direction 1)
+    int fused32 = 0;            // 1: the FP32 apply runs the fused kernel
+    int onthefly = 0;           // 1: the FP32 operator evaluates C in its x stage (C32 freed)
+    CoeffField cf32;            // that coefficient field
+    float* cf_tab = nullptr;    // its direction-1 tables: G [6][nq1], s [2][nq1]
 };
 
 namespace {
@@ -322,6 +328,8 @@ OpCtx<float> ctx32(mfwq_handle h) {
     c.srows = h->srows32;
     c.xcarve = h->xcarve32;
     c.cm = h->Cm32;
+    c.fused = h->fused32 && h->fplan.ok ? &h->fplan : nullptr;
+    c.cf = h->onthefly ? &h->cf32 : nullptr;
     return c;
 }
 
@@ -342,6 +350,8 @@ void free_handle(mfwq_handle h) {
     cudaFree(h->derr);
     cudaFree(h->dsc);
     cudaFree(h->host_io);
+    fused_plan_free(h->fplan);
+    cudaFree(h->cf_tab);
     if (h->hsc) cudaFreeHost(h->hsc);
     if (h->hnorm) cudaFreeHost(h->hnorm);
     delete h;
@@ -518,6 +528,11 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
                 if (xstage_mode_valid(es, h->n[0], h->nq[0], L, mode))
                     smem = std::max(smem, xstage_smem_bytes(es, h->n[0], h->nq[0], L, mode));
     ST(configure_xstage_smem(smem));
+    if (h->mixed) {
+        ST(configure_xstage_otf_smem(xstage_otf_smem_bytes(h->n[0], h->nq[0])));
+        ST(fused_plan_build(h->dir[0], h->dir[1], h->d32[0].SX, h->d32[1].SX, h->nq[2], h->fplan));
+        h->fused32 = 0;  // the staged kernels unless mfwq_autotune or mfwq_set_fp32_path picks the fused one
+    }
     CU(cudaDeviceSynchronize());
     return MFWQ_OK;
 }
@@ -721,6 +736,8 @@ __global__ void k_fields_to_f32(const double* __restrict__ x, size_t n, float* _
 int mfwq_set_coeff(mfwq_handle h, const double* C_dev) {
     ProfScope _ps(h ? &h->prof : nullptr);
     if (!h || !C_dev) return fail(MFWQ_EINVAL, "bad argument");
+    h->onthefly = 0;
+    if (h->mixed && !h->C32) ST(dmalloc((void**)&h->C32, sizeof(float) * 6 * h->cs));
     CU(cudaMemcpy2DAsync(h->C64, sizeof(double) * h->cs, C_dev, sizeof(double) * h->Nq, sizeof(double) * h->Nq, 6,
                          cudaMemcpyDeviceToDevice, h->stream));
     if (h->mixed) {
@@ -729,6 +746,95 @@ int mfwq_set_coeff(mfwq_handle h, const double* C_dev) {
         launch_end(S_SETUP, h->stream);
         CU(cudaGetLastError());
     }
+    return MFWQ_OK;
+}
+
+namespace {
+// |det J| J^-1 J^-T of the geometry at (xi1, xi2), K = I (Eq. (C), J_ij = dF_i/dxi_j),
+// by the adjugate: J^-1 = adj(J) / det J, so the product is adj adj^T / |det|.
+void geom_factor(int geom, double xi1, double xi2, double G[6]) {
+    double J[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+    if (geom == MFWQ_GEOM_RING) {
+        const double hp = 1.5707963267948966, r = 1.0 + xi1;
+        const double sn = std::sin(hp * xi2), cs = std::cos(hp * xi2);
+        J[0][0] = cs;
+        J[1][0] = sn;
+        J[0][1] = -r * hp * sn;
+        J[1][1] = r * hp * cs;
+    }
+    double A[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            const int i1 = (j + 1) % 3, i2 = (j + 2) % 3, j1 = (i + 1) % 3, j2 = (i + 2) % 3;
+            A[i][j] = J[i1][j1] * J[i2][j2] - J[i1][j2] * J[i2][j1];  // cofactor of J[j][i]
+        }
+    const double det = J[0][0] * A[0][0] + J[0][1] * A[1][0] + J[0][2] * A[2][0];
+    const int pr[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+    for (int s = 0; s < 6; ++s) {
+        const int i = pr[s][0], j = pr[s][1];
+        G[s] = (A[i][0] * A[j][0] + A[i][1] * A[j][1] + A[i][2] * A[j][2]) / std::fabs(det);
+    }
+}
+}  // namespace
+
+int mfwq_set_coeff_field(mfwq_handle h, int geometry, const double* modes_host, int nmodes, double kscale, int onthefly) {
+    ProfScope _ps(h ? &h->prof : nullptr);
+    if (!h || nmodes < 0 || nmodes > kMaxModes || (nmodes > 0 && !modes_host) || !std::isfinite(kscale))
+        return fail(MFWQ_EINVAL, "bad argument");
+    if (geometry != MFWQ_GEOM_CUBE && geometry != MFWQ_GEOM_RING) return fail(MFWQ_EINVAL, "unknown geometry");
+    if (onthefly) {
+        if (!h->mixed) return fail(MFWQ_EINVAL, "the coefficient is evaluated in the FP32 operator: needs mixed = 1");
+        const StencilD<float>& S = h->d32[0].SX;
+        if (!S.ok || S.P < 2 || S.P > kStencilMaxP)
+            return fail(MFWQ_EINVAL, "evaluating the coefficient in the x stage needs the stencil form (p_1 <= 8)");
+    }
+    // the stored FP64 coefficient (the FP64 operator reads it) and, without on-the-fly, its FP32 copy
+    double* tmp = nullptr;
+    ST(dmalloc((void**)&tmp, sizeof(double) * 6 * h->Nq));
+    const double* xq[3] = {h->d64[0].xq, h->d64[1].xq, h->d64[2].xq};
+    int st = run_eval_coeff(h->nq, xq, geometry, modes_host, nmodes, kscale, tmp, h->stream);
+    if (st == MFWQ_OK) st = mfwq_set_coeff(h, tmp);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) st = fail(MFWQ_ECUDA, "evaluating the coefficient failed");
+    cudaFree(tmp);
+    if (st != MFWQ_OK) return st;
+    if (!onthefly) return MFWQ_OK;
+    // direction-1 tables: G(xi1) (checked to be independent of xi2) and s = r or xi1 as a float pair
+    const int nq1 = h->nq[0];
+    std::vector<float> tab((size_t)8 * nq1);
+    for (int q = 0; q < nq1; ++q) {
+        const double xi1 = h->dir[0].xq[q];
+        double G[6], G2[6];
+        geom_factor(geometry, xi1, 0.0, G);
+        for (double xi2 : {0.3, 0.7, 1.0}) {
+            geom_factor(geometry, xi1, xi2, G2);
+            for (int s = 0; s < 6; ++s)
+                if (std::fabs(G2[s] - G[s]) > 1e-13 * (std::fabs(G[0]) + std::fabs(G[1]) + std::fabs(G[2])))
+                    return fail(MFWQ_EINVAL, "the geometry factor of C depends on xi2: no direction-1 table");
+        }
+        for (int s = 0; s < 6; ++s) tab[(size_t)s * nq1 + q] = (float)G[s];
+        const double sv = geometry == MFWQ_GEOM_RING ? 1.0 + xi1 : xi1;
+        const float hi = (float)sv;
+        tab[(size_t)6 * nq1 + q] = hi;
+        tab[(size_t)7 * nq1 + q] = (float)(sv - (double)hi);
+    }
+    if (!h->cf_tab) ST(dmalloc((void**)&h->cf_tab, sizeof(float) * 8 * nq1));
+    CU(cudaMemcpy(h->cf_tab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice));
+    CoeffField& f = h->cf32;
+    f.geom = geometry;
+    f.nmodes = nmodes;
+    f.kscale = (float)kscale;
+    for (int m = 0; m < nmodes; ++m) {
+        f.a[m] = (float)modes_host[5 * m];
+        for (int d = 0; d < 3; ++d) f.k[m][d] = modes_host[5 * m + 1 + d];
+        f.phi_pi[m] = modes_host[5 * m + 4] / 3.141592653589793;
+    }
+    f.g6 = h->cf_tab;
+    f.s1 = h->cf_tab + (size_t)6 * nq1;
+    f.xq2 = h->d64[1].xq;
+    f.xq3 = h->d64[2].xq;
+    cudaFree(h->C32);  // the FP32 operator no longer reads a stored coefficient
+    h->C32 = nullptr;
+    h->onthefly = 1;
     return MFWQ_OK;
 }
 
@@ -889,7 +995,7 @@ int mfwq_grad_coeff(mfwq_handle h, const double* lambda_dev, const double* u_dev
 
 static const char* kStageNames[S_NTAGS] = {
     "trial_z", "trial_y", "xstage", "test_y", "test_z", "test_zT", "test_yT", "xstage_T", "trial_yT", "trial_zT",
-    "xstage_grad", "fd_dim1", "fd_dim23", "fd_tc", "krylov", "setup", "fd_fold", "mass", "h1_error"};
+    "xstage_grad", "fd_dim1", "fd_dim23", "fd_tc", "krylov", "setup", "fd_fold", "mass", "h1_error", "fused_xy"};
 
 const char* mfwq_stage_name(int stage) { return stage >= 0 && stage < S_NTAGS ? kStageNames[stage] : ""; }
 
@@ -917,6 +1023,20 @@ int mfwq_profile_read(mfwq_handle h, mfwq_profile_stats* out, int reset) {
 }
 
 long long mfwq_kernel_launches(void) { return total_launches(); }
+
+int mfwq_set_fp32_path(mfwq_handle h, int path) {
+    if (!h) return fail(MFWQ_EINVAL, "NULL handle");
+    if (path != MFWQ_PATH_STAGED && path != MFWQ_PATH_FUSED) return fail(MFWQ_EINVAL, "unknown FP32 apply path");
+    if (path == MFWQ_PATH_FUSED && !h->mixed) return fail(MFWQ_EINVAL, "handle was set up without mixed = 1");
+    if (path == MFWQ_PATH_FUSED && !h->fplan.ok) return fail(MFWQ_EINVAL, "fused FP32 apply unavailable: " + h->fplan.why);
+    h->fused32 = path == MFWQ_PATH_FUSED ? 1 : 0;
+    return MFWQ_OK;
+}
+
+int mfwq_fp32_path(mfwq_handle h) {
+    if (!h) return fail(MFWQ_EINVAL, "NULL handle");
+    return h->fused32 && h->fplan.ok ? MFWQ_PATH_FUSED : MFWQ_PATH_STAGED;
+}
 
 int mfwq_sync(mfwq_handle h) {
     if (!h) return fail(MFWQ_EINVAL, "NULL handle");
@@ -985,6 +1105,7 @@ int tune_xstage(mfwq_handle h, bool f32, int* err) {
     c.cs = h->cs;
     c.err = h->derr;
     c.cm = f32 ? (const T*)h->Cm32 : (const T*)h->Cm64;
+    c.cf = f32 && h->onthefly ? &h->cf32 : nullptr;
     c.scratch = static_cast<T*>(h->scratch);
     c.stream = h->stream;
     // one untimed apply, then three timed ones
@@ -1011,6 +1132,7 @@ int tune_xstage(mfwq_handle h, bool f32, int* err) {
                 if ((mode < 4 && L > h->max_xlines) || !xstage_mode_valid((int)sizeof(T), h->n[0], h->nq[0], Lv, mode))
                     continue;
                 if (mode == 6 && (carve || !(f32 ? h->d32[0].SX.ok : h->d64[0].SX.ok))) continue;
+                if (c.cf && (mode != 6 || L != 8)) continue;  // the evaluated coefficient runs the stencil form
                 c.xlines = L;
                 c.xmode = mode;
                 c.xcarve = carve;
@@ -1035,10 +1157,22 @@ int tune_xstage(mfwq_handle h, bool f32, int* err) {
             best_R = R;
         }
     }
+    // FP32: the fused trial-y / x / test-y kernel against the staged kernels
+    int best_fused = 0;
+    if (f32 && h->fplan.ok && !h->Cm32 && *err == MFWQ_OK) {
+        c.srows = best_R;
+        c.fused = &h->fplan;
+        const float ms = time_apply();
+        c.fused = nullptr;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_fused = 1;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (cudaGetLastError() != cudaSuccess) *err = MFWQ_ECUDA;
-    return 1000 * best_carve + 100 * best_R + 10 * best_mode + best_L;
+    return 10000 * best_fused + 1000 * best_carve + 100 * best_R + 10 * best_mode + best_L;
 }
 }  // namespace
 
@@ -1055,9 +1189,11 @@ extern "C" int mfwq_autotune(mfwq_handle h, const char* cache_path, int* xlines_
             cache_store(cache_path, key, code);
         }
         int L = code % 10, mode = (code / 10) % 10, R = (code / 100) % 10, carve = (code / 1000) % 10 ? 1 : 0;
+        const int fused = (code / 10000) % 10 ? 1 : 0;
         if (mode < 4 && L > h->max_xlines) L = h->max_xlines;
         if (R != 2 && R != 4) R = 1;
         if (prec) {
+            h->fused32 = fused && h->fplan.ok ? 1 : 0;
             h->xlines32 = L;
             h->xmode32 = mode;
             h->srows32 = R;

@@ -7,6 +7,33 @@
 
 namespace mfwq {
 
+struct FusedPlan;  // fused_apply.h
+
+// Coefficient evaluated at the quadrature points inside the FP32 x stage
+// instead of read from a stored copy (the memory-lean form of Section 3.2's
+// remark on storing C).  K(x) = exp(kscale g(x)) I with the Fourier field
+// g(x) = sum_m a_m cos(2 pi k_m . x + phi_m), x = F(xi) the exact map.  For
+// both geometries C = |det J| J^-1 K J^-T = kappa(x) G(xi1): G depends on xi1
+// only (ring: G = diag(pi r / 2, 2 / (pi r), pi r / 2), r = 1 + xi1; cube:
+// G = I), so G is a table over the direction-1 points and only kappa is
+// evaluated per point.  With s = r (ring) or xi1 (cube), the phase in
+// half-turns is 2 k.x + phi/pi = (2 A) s + B, where A and B depend on the
+// line (xi2, xi3) only: ring A = k1 cos(pi xi2 / 2) + k2 sin(pi xi2 / 2),
+// B = 2 k3 xi3 + phi/pi; cube A = k1, B = 2 (k2 xi2 + k3 xi3) + phi/pi.
+constexpr int kMaxModes = 32;
+struct CoeffField {
+    int geom = 0;          // MFWQ_GEOM_*
+    int nmodes = 0;
+    float kscale = 0.f;
+    float a[kMaxModes];            // amplitudes
+    double k[kMaxModes][3];        // wave vectors
+    double phi_pi[kMaxModes];      // phases / pi
+    const float* g6 = nullptr;     // [6][nq1]: G at the direction-1 points, fields 11, 22, 33, 12, 13, 23
+    const float* s1 = nullptr;     // [2][nq1]: s at the direction-1 points as an unevaluated sum hi + lo
+    const double* xq2 = nullptr;   // points of directions 2 and 3
+    const double* xq3 = nullptr;
+};
+
 // Everything one operator application needs, in one precision.
 template <typename T>
 struct OpCtx {
@@ -24,6 +51,8 @@ struct OpCtx {
     int srows = 1;     // output rows per thread of the slow-dimension stages: 1, 2 or 4
     int* err = nullptr;  // device error word: set when a bounded wait times out
     const T* cm = nullptr;  // reaction coefficient c = alpha det J at the WQ points [Nq], or none
+    const FusedPlan* fused = nullptr;  // FP32: plan of the fused apply (used when ok and no reaction term)
+    const CoeffField* cf = nullptr;    // FP32: coefficient evaluated in the x stage (C unused), or none
 };
 
 constexpr int kXstageSmemMax = 227 * 1024;
@@ -46,6 +75,8 @@ size_t rhs_scratch_elems(const int n[3], const int ng[3]);
 int xstage_smem_bytes(int elem_size, int n1, int nq1, int lines, int mode);  // forward x stage
 bool xstage_mode_valid(int elem_size, int n1, int nq1, int lines, int mode);
 int xstage_aux_smem_bytes(int elem_size, int n1, int nq1);         // transposed and gradient x stages
+int xstage_otf_smem_bytes(int n1, int nq1);                         // FP32 stencil x stage with the coefficient evaluated
+int configure_xstage_otf_smem(int bytes);
 int configure_xstage_smem(int bytes);
 
 int run_eval_coeff(const int nq[3], const double* const xq[3], int geom, const double* modes, int nmodes, double kscale,

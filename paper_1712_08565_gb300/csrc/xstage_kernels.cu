@@ -12,10 +12,18 @@
 
 #include "apply_common.cuh"
 #include "ptx_async.cuh"
+#include "stencil_x.cuh"
 
 namespace mfwq {
 
 namespace {
+
+using stx::kSeg;
+using stx::kStLines;
+using stx::st_load_y;
+using stx::st_stride;
+using stx::st_test;
+using stx::st_trial;
 
 // Forward x stage: Y (3 inputs [line][n1]) -> T (9 outputs [line][n1]).
 // The nine products are formed three at a time, one trial direction beta at a
@@ -417,199 +425,6 @@ __global__ void __launch_bounds__(kThreads) k_xstage_tiled(XArgs<T> a, const T* 
 }
 
 // ---- stencil forward x stage (mode 6): translation-invariant interiors
-// For uniform knots the interior rows of B (pairs of points) and W (outputs)
-// are one filter shifted along the line (StencilD); boundary rows use the
-// band tables.  A block owns 8 lines and takes the three trial gradients
-// beta in turn; the block's inputs are requested into L2 when it starts.
-//  trial: warp w = line w, lanes = consecutive pairs of points; the pair's
-//    window of P + 2 Y values gives G_b at both points (filter taps are kernel
-//    parameters), then the three H^(alpha b) = C_(alpha b) G_b with coalesced
-//    coefficient loads, stored to shared memory;
-//  test: lanes = (line, alpha), 24 of 32; a lane walks segments of 8 outputs
-//    of its own row with the window (2P + 15 values) in registers: 8(2P + 1)
-//    multiply-adds per window.  Row strides are 1 mod 32 and the alpha slabs
-//    8 rows apart, so the 24 lanes hit 24 different banks;
-//  outputs staged in shared memory and written out coalesced while the next
-//    beta's trial runs; the next beta's Y slab arrives by cp.async during the
-//    test, so each beta costs two barriers.
-constexpr int kStLines = 8;  // the (line, alpha) lane map and the copy-out assume 8
-constexpr int kSeg = 8;
-static_assert(kStLines == 8, "stencil x stage: 3 x 8 (line, alpha) lanes per warp");
-static_assert(kThreads / 32 == kStLines, "stencil x stage: one warp per line in the trial");
-
-// row stride >= n with stride = 1 (mod 32)
-__host__ __device__ inline int st_stride(int n) { return ((n + 30) / 32) * 32 + 1; }
-
-template <typename T, int P, int BF>
-__device__ __forceinline__ void st_pair(const StencilD<T>& st, const T* Y, T& g0, T& g1) {
-    constexpr int NB = P + 2;
-    T a = 0, b = 0;
-#pragma unroll
-    for (int t = 0; t < NB; ++t) {
-        const T y = Y[t];
-        a = fmaT(st.bf[BF][0][t], y, a);
-        b = fmaT(st.bf[BF][1][t], y, b);
-    }
-    g0 = a;
-    g1 = b;
-}
-
-template <typename T, int P>
-__device__ __forceinline__ void st_seg(const T* w, const T* H, T* To) {
-    constexpr int NW = 2 * P + 1, WIN = 2 * (kSeg - 1) + NW;
-    T h[WIN];
-#pragma unroll
-    for (int u = 0; u < WIN; ++u) h[u] = H[u];
-#pragma unroll
-    for (int r = 0; r < kSeg; ++r) {
-        T acc = 0;
-#pragma unroll
-        for (int t = 0; t < NW; ++t) acc = fmaT(w[t], h[2 * r + t], acc);
-        To[r] = acc;
-    }
-}
-
-// The Y slab of one beta for this block's lines: warp w copies line w's row
-// asynchronously (cp.async) into sY.
-template <typename T>
-__device__ __forceinline__ void st_load_y(const T* __restrict__ yb, int n1, int line0, int nl, T* sY) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (warp >= nl) return;
-    const T* src = yb + (size_t)(line0 + warp) * n1;
-    T* dst = sY + warp * st_stride(n1);
-    for (int j = lane; j < n1; j += 32) ptx::cp_async_elem(dst + j, src + j);
-}
-
-// Trial side of one beta: G_beta at every point of line w (warp w) from its Y
-// row, times the three coefficients C_(alpha beta), into the H rows.
-template <typename T, int P, int BETA>
-__device__ __forceinline__ void st_trial(const XArgs<T>& a, const StencilD<T>& st, int line0, int nl, const T* sY,
-                                         T* sH) {
-    constexpr int BF = BETA == 0 ? 1 : 0;  // trial family: derivative in direction 1 for beta = 1
-    const int n1 = a.n1, nq1 = a.nq1;
-    const int rY = st_stride(n1), rG = st_stride(nq1);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int c0 = BETA == 0 ? 0 : 2 + BETA, c1 = BETA == 1 ? 1 : 3 + BETA, c2 = BETA == 2 ? 2 : 4 + BETA;
-    if (warp >= nl) return;
-    const size_t lb = (size_t)(line0 + warp) * nq1;
-    const T* C0 = a.C + (size_t)c0 * a.cs + lb;
-    const T* C1 = a.C + (size_t)c1 * a.cs + lb;
-    const T* C2 = a.C + (size_t)c2 * a.cs + lb;
-    // boundary points of this line: their coefficients (first 32 points) are
-    // requested before the interior loop so that the latency overlaps it
-    const int nbq = st.q_lo + (nq1 - st.q_hi);
-    const int qb = lane < st.q_lo ? lane : st.q_hi + (lane - st.q_lo);
-    const bool bl = lane < nbq;
-    const T cb0 = bl ? C0[qb] : T(0), cb1 = bl ? C1[qb] : T(0), cb2 = bl ? C2[qb] : T(0);
-    // interior pairs: lane = pair k of a chunk of 32; two chunks per pass,
-    // the next pass's 12 coefficients loaded before this pass computes
-    const int npairs = (st.q_hi - st.q_lo) >> 1;
-    const T* Yl = sY + warp * rY + st.jb + lane;
-    T* Hl = sH + warp * rG + st.q_lo + 2 * lane;
-    const int qo = st.q_lo + 2 * lane;
-    auto load6 = [&](int k, T* c) {
-        const bool ok = k + lane < npairs;
-        const int o = qo + 2 * k;
-        c[0] = ok ? C0[o] : T(0);
-        c[1] = ok ? C0[o + 1] : T(0);
-        c[2] = ok ? C1[o] : T(0);
-        c[3] = ok ? C1[o + 1] : T(0);
-        c[4] = ok ? C2[o] : T(0);
-        c[5] = ok ? C2[o + 1] : T(0);
-    };
-    T cn[2][6];
-    load6(0, cn[0]);
-    load6(32, cn[1]);
-    for (int k0 = 0; k0 < npairs; k0 += 64) {
-        T c[2][6];
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int e = 0; e < 6; ++e) c[h][e] = cn[h][e];
-        if (k0 + 64 < npairs) {
-            load6(k0 + 64, cn[0]);
-            load6(k0 + 96, cn[1]);
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (k0 + 32 * h + lane >= npairs) break;
-            T g0, g1;
-            st_pair<T, P, BF>(st, Yl + k0 + 32 * h, g0, g1);
-            T* H = Hl + 2 * (k0 + 32 * h);
-            H[0] = c[h][0] * g0;
-            H[1] = c[h][1] * g1;
-            H[kStLines * rG] = c[h][2] * g0;
-            H[kStLines * rG + 1] = c[h][3] * g1;
-            H[2 * kStLines * rG] = c[h][4] * g0;
-            H[2 * kStLines * rG + 1] = c[h][5] * g1;
-        }
-    }
-    // boundary points (band tables)
-    for (int k = lane; k < nbq; k += 32) {
-        const int q = k < st.q_lo ? k : st.q_hi + (k - st.q_lo);
-        const int s0 = a.B.start[q], L = a.B.len[q];
-        const T* Y = sY + warp * rY + s0;
-        T g = 0;
-        for (int t = 0; t < L; ++t) g = fmaT(a.B.lane(BF, q, t), Y[t], g);
-        T* H = sH + warp * rG + q;
-        const bool first = k < 32;
-        H[0] = (first ? cb0 : C0[q]) * g;
-        H[kStLines * rG] = (first ? cb1 : C1[q]) * g;
-        H[2 * kStLines * rG] = (first ? cb2 : C2[q]) * g;
-    }
-}
-
-// Test side of one beta: the 24 rows (alpha, line) of H against the WQ
-// weights of their family, outputs into sT.
-template <typename T, int P, int BETA>
-__device__ __forceinline__ void st_test(const XArgs<T>& a, const StencilD<T>& st, const T* sH, T* sT) {
-    constexpr int BF = BETA == 0 ? 1 : 0;
-    constexpr int NW = 2 * P + 1;
-    const int n1 = a.n1, nq1 = a.nq1;
-    const int rT = st_stride(n1), rG = st_stride(nq1);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // interior segments of kSeg outputs with the window in registers
-    const int nseg = (st.i_hi - st.i_lo) / kSeg;
-    const int i_st = st.i_lo + nseg * kSeg;
-    const int nbi = st.i_lo + (n1 - i_st);
-    if (sizeof(T) == 8) {
-        // FP64 is bound by the FP64 pipe, not by shared-memory banks: all 32
-        // lanes work, as (line l, segment offset s4) for one alpha per warp pass
-        const int l = lane & 7, s4 = lane >> 3;
-        const int nm = (nseg + 3) >> 2;
-        for (int it = warp; it < 3 * nm; it += kStLines) {
-            const int al = it / nm, sg = 4 * (it - al * nm) + s4;
-            if (sg >= nseg) continue;
-            T w[NW];
-#pragma unroll
-            for (int t = 0; t < NW; ++t) w[t] = al == 0 ? st.wf[2 + BF][t] : st.wf[BF][t];
-            st_seg<T, P>(w, sH + (al * kStLines + l) * rG + st.qw + 2 * kSeg * sg,
-                         sT + (al * kStLines + l) * rT + st.i_lo + kSeg * sg);
-        }
-    } else if (lane < 3 * kStLines) {
-        // lane = (line l, alpha al): 24 rows 1 mod 32 apart, conflict-free
-        const int al = lane >> 3, l = lane & 7;
-        T w[NW];
-#pragma unroll
-        for (int t = 0; t < NW; ++t) w[t] = al == 0 ? st.wf[2 + BF][t] : st.wf[BF][t];
-        const T* Hl = sH + (al * kStLines + l) * rG + st.qw;
-        T* To = sT + (al * kStLines + l) * rT + st.i_lo;
-        for (int sg = warp; sg < nseg; sg += kStLines) st_seg<T, P>(w, Hl + 2 * kSeg * sg, To + kSeg * sg);
-    }
-    // boundary outputs: one (output, row) item per thread, rows fastest, handed
-    // out from the last warp down (the first warps take the extra interior segments)
-    for (int it = kThreads - 1 - threadIdx.x; it < nbi * 3 * kStLines; it += kThreads) {
-        const int k = it / (3 * kStLines), row = it - k * (3 * kStLines);
-        const int i = k < st.i_lo ? k : i_st + (k - st.i_lo);
-        const int fam = row < kStLines ? 2 + BF : BF;  // alpha = 1 tests the derivative
-        const int s0 = a.W.start[i], L = a.W.len[i];
-        const T* Hr = sH + row * rG + s0;
-        T acc = 0;
-        for (int t = 0; t < L; ++t) acc = fmaT(a.W.lane(fam, i, t), Hr[t], acc);
-        sT[row * rT + i] = acc;
-    }
-}
-
 // Staged outputs of one beta to T^(alpha beta): warp w copies rows w, w + 8, w + 16.
 template <typename T, int BETA>
 __device__ __forceinline__ void st_copy_out(int n1, int line0, int nl, const T* sT, T* __restrict__ tout,
@@ -646,34 +461,121 @@ __global__ void __launch_bounds__(kThreads) k_xstage_stencil(XArgs<T> a, Stencil
     T* sY = reinterpret_cast<T*>(smem_raw);             // [8][rY]: Y rows of one beta
     T* sT = sY + kStLines * st_stride(n1);              // [3 alpha][8][rT]: staged outputs of one beta
     T* sH = sT + 3 * kStLines * st_stride(n1);          // [3 alpha][8][rG]
-    st_load_y(y0, n1, line0, nl, sY);
+    const int rY = st_stride(n1), rT = st_stride(n1), rG = st_stride(a.nq1);
+    st_load_y(y0, n1, line0, nl, sY, rY);
     ptx::cp_async_commit();
     ptx::cp_async_wait_all();
     __syncthreads();
-    st_trial<T, P, 0>(a, st, line0, nl, sY, sH);
+    st_trial<T, P, 0>(a, st, line0, nl, sY, sH, rY, rG);
     __syncthreads();
-    st_load_y(y1, n1, line0, nl, sY);
+    st_load_y(y1, n1, line0, nl, sY, rY);
     ptx::cp_async_commit();
-    st_test<T, P, 0>(a, st, sH, sT);
+    st_test<T, P, 0>(a, st, sH, sT, rG, rT);
     ptx::cp_async_wait_all();
     __syncthreads();
     st_copy_out<T, 0>(n1, line0, nl, sT, tout, tstride);
-    st_trial<T, P, 1>(a, st, line0, nl, sY, sH);
+    st_trial<T, P, 1>(a, st, line0, nl, sY, sH, rY, rG);
     __syncthreads();
-    st_load_y(y2, n1, line0, nl, sY);
+    st_load_y(y2, n1, line0, nl, sY, rY);
     ptx::cp_async_commit();
-    st_test<T, P, 1>(a, st, sH, sT);
+    st_test<T, P, 1>(a, st, sH, sT, rG, rT);
     ptx::cp_async_wait_all();
     __syncthreads();
     st_copy_out<T, 1>(n1, line0, nl, sT, tout, tstride);
-    st_trial<T, P, 2>(a, st, line0, nl, sY, sH);
+    st_trial<T, P, 2>(a, st, line0, nl, sY, sH, rY, rG);
     __syncthreads();
-    st_test<T, P, 2>(a, st, sH, sT);
+    st_test<T, P, 2>(a, st, sH, sT, rG, rT);
     __syncthreads();
     st_copy_out<T, 2>(n1, line0, nl, sT, tout, tstride);
 }
 
+// The same x stage with the coefficient evaluated in the block (CoeffField):
+// kappa of the block's 8 lines into shared memory first, then the three betas
+// with C = kappa G; nothing of C is read from HBM.
+template <int P>
+__global__ void __launch_bounds__(kThreads) k_xstage_stencil_otf(XArgs<float> a, StencilD<float> st, CoeffField cf,
+                                                                 const float* __restrict__ y0,
+                                                                 const float* __restrict__ y1,
+                                                                 const float* __restrict__ y2, float* __restrict__ tout,
+                                                                 size_t tstride, int nq2, const int* skip) {
+    if (skip && *skip) return;
+    const int line0 = blockIdx.x * kStLines;
+    const int nl = min(kStLines, a.nlines - line0);
+    const int n1 = a.n1;
+    if (threadIdx.x < 3) {
+        const int f = threadIdx.x;
+        ptx::prefetch_l2_range((f == 0 ? y0 : f == 1 ? y1 : y2) + (size_t)line0 * n1, sizeof(float) * (size_t)nl * n1);
+    }
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* sY = reinterpret_cast<float*>(smem_raw);
+    const int rY = st_stride(n1), rT = st_stride(n1), rG = st_stride(a.nq1);
+    float* sT = sY + kStLines * rY;
+    float* sH = sT + 3 * kStLines * rT;
+    float* sK = sH + 3 * kStLines * rG;      // [8][rG]: kappa of the block's lines
+    float* sAB = sK + kStLines * rG;         // [8][kMaxModes][3]
+    st_load_y(y0, n1, line0, nl, sY, rY);
+    ptx::cp_async_commit();
+    stx::st_kappa(cf, line0, nl, a.nq1, nq2, sK, rG, sAB);
+    ptx::cp_async_wait_all();
+    __syncthreads();
+    stx::st_trial_otf<P, 0>(a, st, nl, sY, sH, rY, rG, sK, rG, cf.g6);
+    __syncthreads();
+    st_load_y(y1, n1, line0, nl, sY, rY);
+    ptx::cp_async_commit();
+    st_test<float, P, 0>(a, st, sH, sT, rG, rT);
+    ptx::cp_async_wait_all();
+    __syncthreads();
+    st_copy_out<float, 0>(n1, line0, nl, sT, tout, tstride);
+    stx::st_trial_otf<P, 1>(a, st, nl, sY, sH, rY, rG, sK, rG, cf.g6);
+    __syncthreads();
+    st_load_y(y2, n1, line0, nl, sY, rY);
+    ptx::cp_async_commit();
+    st_test<float, P, 1>(a, st, sH, sT, rG, rT);
+    ptx::cp_async_wait_all();
+    __syncthreads();
+    st_copy_out<float, 1>(n1, line0, nl, sT, tout, tstride);
+    stx::st_trial_otf<P, 2>(a, st, nl, sY, sH, rY, rG, sK, rG, cf.g6);
+    __syncthreads();
+    st_test<float, P, 2>(a, st, sH, sT, rG, rT);
+    __syncthreads();
+    st_copy_out<float, 2>(n1, line0, nl, sT, tout, tstride);
+}
+
 }  // namespace
+
+int xstage_otf_smem_bytes(int n1, int nq1) {
+    return (int)(((size_t)kStLines * (4 * (size_t)st_stride(n1) + 4 * (size_t)st_stride(nq1)) +
+                  (size_t)kStLines * kMaxModes * 3) * sizeof(float));
+}
+
+static void launch_stencil_otf(const StencilD<float>& S, const CoeffField& cf, int nlines, int nq2, size_t sm,
+                               cudaStream_t st, const XArgs<float>& a, const float* y0, const float* y1,
+                               const float* y2, float* tout, size_t tstride, const int* skip) {
+    const dim3 grid((nlines + kStLines - 1) / kStLines);
+    switch (S.P) {
+        case 2: k_xstage_stencil_otf<2><<<grid, kThreads, sm, st>>>(a, S, cf, y0, y1, y2, tout, tstride, nq2, skip); break;
+        case 3: k_xstage_stencil_otf<3><<<grid, kThreads, sm, st>>>(a, S, cf, y0, y1, y2, tout, tstride, nq2, skip); break;
+        case 4: k_xstage_stencil_otf<4><<<grid, kThreads, sm, st>>>(a, S, cf, y0, y1, y2, tout, tstride, nq2, skip); break;
+        case 5: k_xstage_stencil_otf<5><<<grid, kThreads, sm, st>>>(a, S, cf, y0, y1, y2, tout, tstride, nq2, skip); break;
+        case 6: k_xstage_stencil_otf<6><<<grid, kThreads, sm, st>>>(a, S, cf, y0, y1, y2, tout, tstride, nq2, skip); break;
+        case 7: k_xstage_stencil_otf<7><<<grid, kThreads, sm, st>>>(a, S, cf, y0, y1, y2, tout, tstride, nq2, skip); break;
+        case 8: k_xstage_stencil_otf<8><<<grid, kThreads, sm, st>>>(a, S, cf, y0, y1, y2, tout, tstride, nq2, skip); break;
+        default: break;  // unreachable: the field path needs the stencil tables (P <= kStencilMaxP), checked when set
+    }
+}
+
+int configure_xstage_otf_smem(int bytes) {
+    cudaError_t e = cudaSuccess;
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    e = cudaFuncSetAttribute(k_xstage_stencil_otf<2>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_stencil_otf<3>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_stencil_otf<4>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_stencil_otf<5>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_stencil_otf<6>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_stencil_otf<7>, A, bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_stencil_otf<8>, A, bytes);
+    return e == cudaSuccess ? MFWQ_OK : MFWQ_ECUDA;
+}
 
 template <typename T>
 void launch_stencil(const StencilD<T>& S, int nlines, size_t sm, cudaStream_t st, const XArgs<T>& a, const T* y0,
@@ -715,6 +617,14 @@ cudaError_t launch_forward_xstage(const OpCtx<T>& c, const XArgs<T>& a, const T*
             (mode == 6 && (!d1.SX.ok || d1.SX.P < 2 || d1.SX.P > kStencilMaxP))) {
             mode = 0;
             L = 4;
+        }
+        if constexpr (sizeof(T) == 4) {
+            if (c.cf) {  // coefficient evaluated in the x stage: the stencil form only
+                if (!d1.SX.ok || d1.SX.P < 2 || d1.SX.P > kStencilMaxP) return cudaErrorInvalidValue;
+                launch_stencil_otf(d1.SX, *c.cf, nlines, c.d[1].nq, (size_t)xstage_otf_smem_bytes(n1, q1), c.stream, a,
+                                   y0, y1, y2, tout, tstride, skip);
+                return cudaGetLastError();
+            }
         }
         const size_t sm = (size_t)xstage_smem_bytes((int)sizeof(T), n1, q1, L, mode);
         dim3 grid((nlines + L - 1) / L);

@@ -107,6 +107,10 @@ _SIGS = [
     ("mfwq_stage_name", ctypes.c_char_p, [ctypes.c_int]),
     ("mfwq_kernel_launches", ctypes.c_longlong, []),
     ("mfwq_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]),
+    ("mfwq_set_fp32_path", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("mfwq_set_coeff_field", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                            ctypes.c_double, ctypes.c_int]),
+    ("mfwq_fp32_path", ctypes.c_int, [ctypes.c_void_p]),
     ("mfwq_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p)]),
     ("mfwq_batch_destroy", None, [ctypes.c_void_p]),
     ("mfwq_batch_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
@@ -274,6 +278,14 @@ class Operator:
                                      float(kscale), _ptr(out, torch.float64, 6 * self.Nq, self.device)))
         return out
 
+    def set_coeff_field(self, geometry: str = "ring", modes=None, kscale: float = 0.0, onthefly: bool = True):
+        """Coefficient from its definition (mfwq_set_coeff_field): the FP64
+        fields stored; with onthefly the FP32 operator evaluates C in its x
+        stage instead of storing an FP32 copy."""
+        m = np.ascontiguousarray(modes if modes is not None else np.zeros((0, 5)), dtype=np.float64)
+        _check(lib().mfwq_set_coeff_field(self._h, GEOMETRY[geometry], m.ctypes.data if m.size else None,
+                                          int(m.shape[0]), float(kscale), 1 if onthefly else 0))
+
     def set_coeff(self, C):
         import torch
         _check(lib().mfwq_set_coeff(self._h, _ptr(C, torch.float64, 6 * self.Nq, self.device)))
@@ -426,6 +438,18 @@ class Operator:
         v = ctypes.c_int()
         _check(lib().mfwq_autotune(self._h, cache_path.encode() if cache_path else None, ctypes.byref(v)))
         return v.value
+
+    @property
+    def fp32_path(self) -> str:
+        """Kernel sequence of the FP32 operator: 'staged' or 'fused' (mfwq_fp32_path)."""
+        v = lib().mfwq_fp32_path(self._h)
+        if v < 0:
+            _check(v)
+        return "fused" if v == 1 else "staged"
+
+    @fp32_path.setter
+    def fp32_path(self, path: str):
+        _check(lib().mfwq_set_fp32_path(self._h, {"staged": 0, "fused": 1}[path]))
 
     def profile(self, on: bool = True):
         """Bracket every later kernel launch with CUDA events (per-stage timing)."""
