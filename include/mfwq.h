@@ -344,20 +344,37 @@ int mfwq_batch_create(int count, const mfwq_handle* patches, mfwq_batch* out);
 void mfwq_batch_destroy(mfwq_batch b);
 
 /* Solves K~_i u_i = f_i for every patch.  FP64 form (force_fp64, or any patch
- * without mixed = 1): FD-preconditioned BiCGStab as mfwq_solve; one BiCGStab
- * iteration of all patches is captured into a single CUDA graph (each patch
- * on its own stream) and launched once per sweep; every patch keeps its own
- * device-resident scalars, and the kernels of a converged patch return at
- * once; outer_iterations holds the number of sweeps.  Mixed form (every patch
- * mixed = 1): FP64 refinement steps in lockstep over the patches still above
- * rtol, each inner FP32 solve of all of them one graph launch per sweep;
- * iterations sums a patch's inner iterations, outer_iterations counts its
- * refinement steps.  f_dev[i], u_dev[i]: device vectors of patch i.  infos
- * (count entries, may be NULL) receive each patch's status, iterations and
- * FP64 relative residual.  Returns the first failing patch status (MFWQ_OK if
- * all converged).  Synchronous. */
+ * without mixed = 1): FD-preconditioned BiCGStab as mfwq_solve, one sweep (a
+ * BiCGStab iteration of every patch) per CUDA graph launch; every patch keeps
+ * its own device-resident scalars, and a converged patch's work is skipped on
+ * the device; outer_iterations holds the number of sweeps.  Two sweep forms
+ * (mfwq_batch_set_grouped), with the same results bit for bit:
+ *  - per-patch streams (the default): each patch's kernels on a stream of its
+ *    own inside the graph, so the patches' stages overlap freely;
+ *  - grouped: one persistent launch per kernel stage for a group of patches
+ *    (about 55 launches per sweep and group, groups on concurrent streams),
+ *    whose blocks walk a device table of the group's work items -- built from
+ *    each patch's own launch sequence with its arguments -- and skip converged
+ *    patches; the x stage runs in mapping 0 with 4 lines per block.  Needs no
+ *    reaction term and the same FD form (even/odd split or not) in every patch;
+ *    otherwise the per-patch streams run.
+ * Mixed form (every patch mixed = 1): FP64 refinement steps in lockstep over
+ * the patches still above rtol, each inner FP32 solve of all of them one graph
+ * launch per sweep on per-patch streams; iterations sums a patch's inner
+ * iterations, outer_iterations counts its refinement steps.  f_dev[i],
+ * u_dev[i]: device vectors of patch i.  infos (count entries, may be NULL)
+ * receive each patch's status, iterations and FP64 relative residual.  Returns
+ * the first failing patch status (MFWQ_OK if all converged).  Synchronous. */
 int mfwq_batch_solve(mfwq_batch b, const double* const* f_dev, double* const* u_dev, const mfwq_solve_opts* opts,
                      mfwq_solve_info* infos);
+
+/* grouped = G > 0 makes the FP64 batched solve run grouped sweeps in G
+ * concurrent groups of patches (balanced by size) where they apply; 0 (the
+ * default) keeps the per-patch streams.  mfwq_batch_last_grouped returns 1 if
+ * the last FP64 batched solve ran grouped sweeps, else 0.  Neither launches
+ * work; MFWQ_EINVAL for G < 0. */
+int mfwq_batch_set_grouped(mfwq_batch b, int grouped);
+int mfwq_batch_last_grouped(mfwq_batch b);
 
 /* ---- self-test of the bounded device waits (no counterpart in the paper) ---
  * Every wait of the library's kernels on an asynchronous copy or MMA is

@@ -21,10 +21,12 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "apply_common.cuh"
 #include "fused_apply.h"
+#include "grouped.h"
 #include "kernels.h"
 #include "prof.h"
 
@@ -45,14 +47,13 @@ struct SlowGeom {
     int A, Rin, Rout, C;
 };
 
+// One block (bx, by) of gx column blocks; sb: the block's band rows.
 template <class Op, int R>
-__global__ void __launch_bounds__(kThreads) k_slow(Op op, SlowGeom g, const int* skip) {
+__device__ __forceinline__ void slow_body(const Op& op, const SlowGeom& g, int bx, int by, int gx,
+                                          typename Op::Elem* sb) {
     using T = typename Op::Elem;
     constexpr int NF = Op::NF, NIN = Op::NIN, NACC = Op::NACC;
-    if (skip && *skip) return;
-    extern __shared__ __align__(16) unsigned char slow_smem[];
-    T* sb = reinterpret_cast<T*>(slow_smem);
-    const int r0 = blockIdx.y * R;
+    const int r0 = by * R;
     const int nr = min(R, g.Rout - r0);
     const int W = op.band.width;
     int s[R], len[R];
@@ -76,7 +77,7 @@ __global__ void __launch_bounds__(kThreads) k_slow(Op op, SlowGeom g, const int*
     }
     __syncthreads();
     const size_t AC = (size_t)g.A * g.C;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < AC; e += (size_t)gridDim.x * blockDim.x) {
+    for (size_t e = (size_t)bx * blockDim.x + threadIdx.x; e < AC; e += (size_t)gx * blockDim.x) {
         const size_t a = e / g.C, c = e - a * g.C;
         T acc[R][NACC];
 #pragma unroll
@@ -97,6 +98,30 @@ __global__ void __launch_bounds__(kThreads) k_slow(Op op, SlowGeom g, const int*
         for (int k = 0; k < R; ++k)
             if (k < nr) op.store((a * g.Rout + r0 + k) * (size_t)g.C + c, acc[k]);
     }
+}
+
+template <class Op, int R>
+__global__ void __launch_bounds__(kThreads) k_slow(Op op, SlowGeom g, const int* skip) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char slow_smem[];
+    slow_body<Op, R>(op, g, blockIdx.x, blockIdx.y, gridDim.x, reinterpret_cast<typename Op::Elem*>(slow_smem));
+}
+
+// Grouped form (batched FP64 solve): one R = 1 launch per stage over every patch.
+template <class Op>
+struct SlowG {
+    Op op;
+    SlowGeom g;
+    int gx;
+};
+
+template <class Op>
+__global__ void __launch_bounds__(kThreads) k_slow_grouped(const unsigned char* __restrict__ tab, int stride, int npatch) {
+    extern __shared__ __align__(16) unsigned char slow_smem[];
+    grouped_for<SlowG<Op>, true>(tab, stride, npatch, [&](const SlowG<Op>& p, int item) {
+        const int by = item / p.gx;
+        slow_body<Op, 1>(p.op, p.g, item - by * p.gx, by, p.gx, reinterpret_cast<typename Op::Elem*>(slow_smem));
+    });
 }
 
 // The ops: NIN inputs loaded per row, NACC accumulators per output row, NF
@@ -307,9 +332,33 @@ struct OpSingle {  // out = band(fam 0) applied to one input (load-vector stages
 
 // rows: output rows per thread (1, 2 or 4)
 template <class Op>
+constexpr int slow_kind() {
+    using T = typename Op::Elem;
+    if constexpr (sizeof(T) != 8) return GK_NONE;
+    else if constexpr (std::is_same<Op, OpTrialZ<T>>::value) return GK_SLOW_TRIAL_Z;
+    else if constexpr (std::is_same<Op, OpTrialY<T>>::value) return GK_SLOW_TRIAL_Y;
+    else if constexpr (std::is_same<Op, OpTestY<T>>::value) return GK_SLOW_TEST_Y;
+    else if constexpr (std::is_same<Op, OpTestZ<T>>::value) return GK_SLOW_TEST_Z;
+    else return GK_NONE;
+}
+
+template <class Op>
 cudaError_t launch_slow(int tag, const Op& op, int A, int Rin, int Rout, int C, const int* skip, cudaStream_t s,
                         int rows = 1) {
     SlowGeom g{A, Rin, Rout, C};
+    if (g_rec) {  // recorded with one row per thread (the rows per thread do not change any sum)
+        constexpr int kind = slow_kind<Op>();
+        if (kind == GK_NONE) {
+            g_rec->unsupported = true;
+            return cudaSuccess;
+        }
+        size_t AC = (size_t)A * C;
+        unsigned bx = (unsigned)((AC + kThreads - 1) / kThreads);
+        if (bx > 65535u) bx = 65535u;
+        SlowG<Op> p{op, g, (int)bx};
+        record_launch(kind, p, (int)bx * Rout, kThreads, (int)(sizeof(typename Op::Elem) * op.band.width * Op::NF), skip);
+        return cudaSuccess;
+    }
     const int R = rows == 2 || rows == 4 ? rows : 1;
     size_t AC = (size_t)A * C;
     unsigned bx = (unsigned)((AC + kThreads - 1) / kThreads);
@@ -793,7 +842,9 @@ int run_apply(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
         launch_end(S_XSTAGE, c.stream);
         if (cudaGetLastError() != cudaSuccess) return MFWQ_ECUDA;
     }
-    if (c.cm) {  // reaction term into T^(11)
+    if (c.cm && g_rec) {  // the reaction term has no grouped form
+        g_rec->unsupported = true;
+    } else if (c.cm) {  // reaction term into T^(11)
         XArgs<T> a = xargs(d1, q3 * q2, c.cs, c.C);
         launch_begin(S_MASS, c.stream);
         k_mass_x<T><<<(q3 * q2 + kLines - 1) / kLines, kThreads, mass_smem_bytes((int)sizeof(T), n1, q1), c.stream>>>(
@@ -954,6 +1005,19 @@ int xstage_aux_smem_bytes(int elem_size, int n1, int nq1) {
 
 // The dynamic shared-memory limit is a per-kernel attribute shared by all
 // handles on a device, so it only ever grows (one record per device).
+int configure_grouped_smem(int bytes) { return configure_xstage_smem(bytes); }
+
+bool grouped_launch_apply(int kind, const unsigned char* tab, int stride, int npatch, int grid, int smem,
+                          cudaStream_t s) {
+    switch (kind) {
+        case GK_SLOW_TRIAL_Z: k_slow_grouped<OpTrialZ<double>><<<grid, kThreads, smem, s>>>(tab, stride, npatch); return true;
+        case GK_SLOW_TRIAL_Y: k_slow_grouped<OpTrialY<double>><<<grid, kThreads, smem, s>>>(tab, stride, npatch); return true;
+        case GK_SLOW_TEST_Y: k_slow_grouped<OpTestY<double>><<<grid, kThreads, smem, s>>>(tab, stride, npatch); return true;
+        case GK_SLOW_TEST_Z: k_slow_grouped<OpTestZ<double>><<<grid, kThreads, smem, s>>>(tab, stride, npatch); return true;
+        default: return false;
+    }
+}
+
 int configure_xstage_smem(int bytes) {
     static std::mutex mu;
     static int configured[64] = {};

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "fused_apply.h"
+#include "grouped.h"
 #include "kernels.h"
 #include "krylov.h"
 #include "prof.h"
@@ -1211,6 +1212,9 @@ extern "C" int mfwq_autotune(mfwq_handle h, const char* cache_path, int* xlines_
 
 // ---------------------------------------------------------------- batched solve
 struct mfwq_batch_s {
+    int grouped = 0;       // 1: FP64 sweeps as grouped launches where the patches allow it
+    int groups = 4;        // concurrent groups (streams) of the grouped sweep
+    int last_grouped = 0;  // the last FP64 solve ran grouped sweeps
     std::vector<mfwq_handle> h;
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> join;
@@ -1275,6 +1279,18 @@ extern "C" int mfwq_batch_create(int count, const mfwq_handle* patches, mfwq_bat
     }
     *out = b;
     return MFWQ_OK;
+}
+
+extern "C" int mfwq_batch_set_grouped(mfwq_batch b, int grouped) {
+    if (!b || grouped < 0) return fail(MFWQ_EINVAL, "bad argument");
+    b->grouped = grouped ? 1 : 0;
+    if (grouped > 0) b->groups = grouped;
+    return MFWQ_OK;
+}
+
+extern "C" int mfwq_batch_last_grouped(mfwq_batch b) {
+    if (!b) return fail(MFWQ_EINVAL, "NULL batch");
+    return b->last_grouped;
 }
 
 extern "C" void mfwq_batch_destroy(mfwq_batch b) {
@@ -1459,6 +1475,124 @@ int batch_solve_mixed(mfwq_batch b, const double* const* f_dev, double* const* u
 }
 }  // namespace
 
+namespace {
+// One BiCGStab iteration of every patch as grouped launches: each patch's
+// iteration is recorded (the kernels a separate solve launches, with its
+// arguments), stage k of all patches becomes one launch over a device table.
+// Returns MFWQ_OK with *exec = NULL when the patches' sequences differ or a
+// kernel has no grouped form (the caller then captures per-patch streams).
+struct GroupedSweep {
+    void* dmem = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int stages = 0;
+    ~GroupedSweep() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (dmem) cudaFree(dmem);
+    }
+};
+
+int build_grouped_sweep(mfwq_batch b, const std::vector<PatchOps>& ops, const double* const* f_dev,
+                        double* const* u_dev, GroupedSweep& gs) {
+    const int count = (int)b->h.size();
+    std::vector<Recorder> rec(count);
+    for (int i = 0; i < count; ++i) {
+        mfwq_handle h = b->h[i];
+        RecScope rs(&rec[i]);
+        const int st = krylov_enqueue_iter<double>(ops[i].A, ops[i].P, f_dev[i], u_dev[i], bufs64(h), &b->dsc[i],
+                                                   h->part, h->N, b->streams[i]);
+        if (st != MFWQ_OK || rec[i].unsupported) return MFWQ_OK;
+    }
+    const size_t nst = rec[0].recs.size();
+    for (int i = 1; i < count; ++i) {
+        if (rec[i].recs.size() != nst) return MFWQ_OK;
+        for (size_t k = 0; k < nst; ++k)
+            if (rec[i].recs[k].kind != rec[0].recs[k].kind || rec[i].recs[k].threads != rec[0].recs[k].threads)
+                return MFWQ_OK;
+    }
+    // groups of patches (largest first, each to the group with the least work), one stream each
+    const int G = std::max(1, std::min(b->groups, count));
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int x, int y) { return b->h[x]->N > b->h[y]->N; });
+    std::vector<std::vector<int>> grp(G);
+    std::vector<double> load(G, 0.0);
+    for (int i : order) {
+        const int g = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        grp[g].push_back(i);
+        load[g] += (double)b->h[i]->N;
+    }
+    // tables: stage k of group g at off[g][k], slots of stride[k] bytes
+    std::vector<int> stride(nst), smem(nst);
+    for (size_t k = 0; k < nst; ++k) {
+        size_t amax = 0;
+        int sm = 0;
+        for (int i = 0; i < count; ++i) {
+            amax = std::max(amax, rec[i].recs[k].args.size());
+            sm = std::max(sm, rec[i].recs[k].smem);
+        }
+        stride[k] = (int)((kSlotHeader + amax + 15) / 16 * 16);
+        smem[k] = sm;
+    }
+    std::vector<std::vector<size_t>> off(G, std::vector<size_t>(nst));
+    std::vector<std::vector<int>> grid(G, std::vector<int>(nst));
+    size_t total = 0;
+    for (int g = 0; g < G; ++g)
+        for (size_t k = 0; k < nst; ++k) {
+            long long items = 0;
+            for (int i : grp[g]) items += rec[i].recs[k].items;
+            grid[g][k] = (int)std::max<long long>(1, std::min<long long>(items, 152LL * 32 / G + 1));
+            off[g][k] = total;
+            total = (total + (size_t)stride[k] * grp[g].size() + 255) / 256 * 256;
+        }
+    std::vector<unsigned char> host(total, 0);
+    for (int g = 0; g < G; ++g)
+        for (size_t k = 0; k < nst; ++k)
+            for (size_t q = 0; q < grp[g].size(); ++q) {
+                const LaunchRec& r = rec[grp[g][q]].recs[k];
+                unsigned char* slot = host.data() + off[g][k] + (size_t)stride[k] * q;
+                std::memcpy(slot, &r.items, sizeof(int));
+                std::memcpy(slot + 8, &r.skip, sizeof(const int*));
+                std::memcpy(slot + kSlotHeader, r.args.data(), r.args.size());
+            }
+    ST(dmalloc(&gs.dmem, total));
+    CU(cudaMemcpy(gs.dmem, host.data(), total, cudaMemcpyHostToDevice));
+    int smax = 0;
+    for (size_t k = 0; k < nst; ++k) smax = std::max(smax, smem[k]);
+    if (smax > 48 * 1024) ST(configure_grouped_smem(smax));
+    cudaGraph_t graph = nullptr;
+    CU(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+    bool ok = cudaEventRecord(b->fork, b->origin) == cudaSuccess;
+    for (int g = 0; g < G && ok; ++g) {
+        cudaStream_t sg = b->streams[g];
+        ok = cudaStreamWaitEvent(sg, b->fork, 0) == cudaSuccess;
+        for (size_t k = 0; k < nst && ok; ++k) {
+            const unsigned char* tab = static_cast<const unsigned char*>(gs.dmem) + off[g][k];
+            const int kind = rec[0].recs[k].kind, n = (int)grp[g].size();
+            ok = grouped_launch_krylov(kind, tab, stride[k], n, grid[g][k], smem[k], sg) ||
+                 grouped_launch_fd(kind, tab, stride[k], n, grid[g][k], smem[k], sg) ||
+                 grouped_launch_apply(kind, tab, stride[k], n, grid[g][k], smem[k], sg) ||
+                 grouped_launch_xstage(kind, tab, stride[k], n, grid[g][k], smem[k], sg);
+        }
+        if (ok) ok = cudaEventRecord(b->join[g], sg) == cudaSuccess && cudaStreamWaitEvent(b->origin, b->join[g], 0) == cudaSuccess;
+    }
+    cudaError_t ce = cudaStreamEndCapture(b->origin, &graph);
+    if (!ok || ce != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return fail(MFWQ_ECUDA, "capture of the grouped sweep failed");
+    }
+    cudaError_t ie = cudaGraphInstantiate(&gs.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+        gs.exec = nullptr;
+        cudaGetLastError();
+        return fail(MFWQ_ECUDA, "cudaGraphInstantiate of the grouped sweep failed");
+    }
+    gs.stages = (int)nst;
+    return MFWQ_OK;
+}
+}  // namespace
+
 extern "C" int mfwq_batch_solve(mfwq_batch b, const double* const* f_dev, double* const* u_dev, const mfwq_solve_opts* opts,
                                 mfwq_solve_info* infos) {
     if (!b || !f_dev || !u_dev) return fail(MFWQ_EINVAL, "bad argument");
@@ -1494,7 +1628,26 @@ extern "C" int mfwq_batch_solve(mfwq_batch b, const double* const* f_dev, double
         return true;
     };
     int sweeps = 0;
-    if (!all_done() && o.maxit > 0) {
+    GroupedSweep gs;
+    if (!all_done() && o.maxit > 0 && b->grouped && count <= 1024) ST(build_grouped_sweep(b, ops, f_dev, u_dev, gs));
+    b->last_grouped = gs.exec ? 1 : 0;
+    if (!all_done() && o.maxit > 0 && gs.exec) {
+        // the grouped sweep: one launch per stage over every patch, one stream
+        int st = MFWQ_OK;
+        for (sweeps = 0; sweeps < o.maxit; ++sweeps) {
+            if (cudaGraphLaunch(gs.exec, b->origin) != cudaSuccess ||
+                cudaMemcpyAsync(b->hsc, b->dsc, sizeof(KScal) * count, cudaMemcpyDeviceToHost, b->origin) != cudaSuccess ||
+                cudaStreamSynchronize(b->origin) != cudaSuccess) {
+                st = fail(MFWQ_ECUDA, "grouped sweep failed");
+                break;
+            }
+            if (all_done()) {
+                ++sweeps;
+                break;
+            }
+        }
+        if (st != MFWQ_OK) return st;
+    } else if (!all_done() && o.maxit > 0) {
         // one BiCGStab iteration of every patch, captured once into a graph
         cudaGraph_t graph = nullptr;
         cudaGraphExec_t exec = nullptr;

@@ -7,6 +7,7 @@
 // FP32 one); the tensor-core TF32/BF16 version is in fd_tc.cu.
 #include <cuda_runtime.h>
 
+#include "grouped.h"
 #include "kernels.h"
 #include "prof.h"
 
@@ -29,15 +30,32 @@ __device__ __forceinline__ float fmaT(float a, float b, float c) { return fmaf(a
 // (M row-major nout x nin).  With l3 != NULL (forward pass along dimension 3,
 // A = 1): out /= l3[outoff + r] + l2[j] + l1[i], c = j n1 + i.
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_dense_slow(const T* __restrict__ M, const T* __restrict__ in, T* __restrict__ out,
-                                                         int A, int ld, int nin, int nout, int inoff, int outoff, int C,
-                                                         const T* __restrict__ l1, const T* __restrict__ l2,
-                                                         const T* __restrict__ l3, int n1, const int* skip) {
-    if (skip && *skip) return;
-    const int r0 = blockIdx.y * kRT;
+struct DenseSlowArgs {
+    const T* M;
+    const T* in;
+    T* out;
+    int A, ld, nin, nout, inoff, outoff, C;
+    const T* l1;
+    const T* l2;
+    const T* l3;
+    int n1;
+    int gx;  // blocks along the columns
+};
+
+// One block (bx, by) of gx column blocks.
+template <typename T>
+__device__ __forceinline__ void dense_slow_body(const DenseSlowArgs<T>& p, int bx, int by) {
+    const T* __restrict__ M = p.M;
+    const T* __restrict__ in = p.in;
+    T* __restrict__ out = p.out;
+    const int A = p.A, ld = p.ld, nin = p.nin, nout = p.nout, inoff = p.inoff, outoff = p.outoff, C = p.C, n1 = p.n1;
+    const T* __restrict__ l1 = p.l1;
+    const T* __restrict__ l2 = p.l2;
+    const T* __restrict__ l3 = p.l3;
+    const int r0 = by * kRT;
     const int nr = min(kRT, nout - r0);
     const size_t AC = (size_t)A * C;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < AC; e += (size_t)gridDim.x * blockDim.x) {
+    for (size_t e = (size_t)bx * blockDim.x + threadIdx.x; e < AC; e += (size_t)p.gx * blockDim.x) {
         const size_t a = e / C, c = e - a * C;
         const T* x = in + (a * ld + inoff) * (size_t)C + c;
         T acc[kRT];
@@ -66,17 +84,33 @@ __global__ void __launch_bounds__(kThreads) k_dense_slow(const T* __restrict__ M
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_dense_slow(DenseSlowArgs<T> p, const int* skip) {
+    if (skip && *skip) return;
+    dense_slow_body<T>(p, blockIdx.x, blockIdx.y);
+}
+
 // Mode product along the fastest dimension of extent ld:
 // out[a][outoff + r] = sum_{t < nin} MT[t][r] in[a][inoff + t], r < nout
 // (MT row-major nin x nout, i.e. M transposed, so lanes read it coalesced).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_dense_fast(const T* __restrict__ MT, const T* __restrict__ in, T* __restrict__ out,
-                                                         int A, int ld, int nin, int nout, int inoff, int outoff,
-                                                         const int* skip) {
-    if (skip && *skip) return;
+struct DenseFastArgs {
+    const T* MT;
+    const T* in;
+    T* out;
+    int A, ld, nin, nout, inoff, outoff;
+    int gx;  // blocks
+};
+
+template <typename T>
+__device__ __forceinline__ void dense_fast_body(const DenseFastArgs<T>& p, int bx) {
+    const T* __restrict__ MT = p.MT;
+    const T* __restrict__ in = p.in;
+    T* __restrict__ out = p.out;
+    const int A = p.A, ld = p.ld, nin = p.nin, nout = p.nout, inoff = p.inoff, outoff = p.outoff;
     const int groups = (A + kAT - 1) / kAT;
     const size_t total = (size_t)groups * nout;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    for (size_t e = (size_t)bx * blockDim.x + threadIdx.x; e < total; e += (size_t)p.gx * blockDim.x) {
         const int g = (int)(e / nout), r = (int)(e - (size_t)g * nout);
         const int a0 = g * kAT;
         const int na = min(kAT, A - a0);
@@ -100,17 +134,31 @@ __global__ void __launch_bounds__(kThreads) k_dense_fast(const T* __restrict__ M
     }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_dense_fast(DenseFastArgs<T> p, const int* skip) {
+    if (skip && *skip) return;
+    dense_fast_body<T>(p, blockIdx.x);
+}
+
 // Even/odd folding along a dimension of extent n (h = n/2, he = n - h):
 // out[j] = in[j] + in[n-1-j] (j < h), out[h] = in[h] (odd n),
 // out[he + j] = in[j] - in[n-1-j] (j < h); and its inverse-type unfold
 // out[j] = in[j] + in[he+j], out[n-1-j] = in[j] - in[he+j], out[h] = in[h].
+struct FoldArgs {
+    const double* in;
+    double* out;
+    int A, n, C;
+    int gx;  // blocks
+};
+
 template <bool UNFOLD>
-__global__ void __launch_bounds__(kThreads) k_fold(const double* __restrict__ in, double* __restrict__ out, int A, int n,
-                                                   int C, const int* skip) {
-    if (skip && *skip) return;
+__device__ __forceinline__ void fold_body(const FoldArgs& p, int bx) {
+    const double* __restrict__ in = p.in;
+    double* __restrict__ out = p.out;
+    const int A = p.A, n = p.n, C = p.C;
     const int h = n / 2, he = n - h;
     const size_t total = (size_t)A * n * C;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    for (size_t e = (size_t)bx * blockDim.x + threadIdx.x; e < total; e += (size_t)p.gx * blockDim.x) {
         const size_t c = e % C;
         const size_t aj = e / C;
         const int j = (int)(aj % n);
@@ -132,6 +180,30 @@ __global__ void __launch_bounds__(kThreads) k_fold(const double* __restrict__ in
     }
 }
 
+template <bool UNFOLD>
+__global__ void __launch_bounds__(kThreads) k_fold(FoldArgs p, const int* skip) {
+    if (skip && *skip) return;
+    fold_body<UNFOLD>(p, blockIdx.x);
+}
+
+// ---- grouped forms (batched FP64 solve)
+__global__ void __launch_bounds__(kThreads) k_dense_slow_grouped(const unsigned char* __restrict__ tab, int stride,
+                                                                 int npatch) {
+    grouped_for<DenseSlowArgs<double>, false>(tab, stride, npatch, [&](const DenseSlowArgs<double>& p, int item) {
+        const int by = item / p.gx;
+        dense_slow_body<double>(p, item - by * p.gx, by);
+    });
+}
+__global__ void __launch_bounds__(kThreads) k_dense_fast_grouped(const unsigned char* __restrict__ tab, int stride,
+                                                                 int npatch) {
+    grouped_for<DenseFastArgs<double>, false>(tab, stride, npatch,
+                                       [&](const DenseFastArgs<double>& p, int item) { dense_fast_body<double>(p, item); });
+}
+template <bool UNFOLD>
+__global__ void __launch_bounds__(kThreads) k_fold_grouped(const unsigned char* __restrict__ tab, int stride, int npatch) {
+    grouped_for<FoldArgs, false>(tab, stride, npatch, [&](const FoldArgs& p, int item) { fold_body<UNFOLD>(p, item); });
+}
+
 template <typename T>
 cudaError_t dense_slow(const T* M, const T* in, T* out, int A, int ld, int nin, int nout, int inoff, int outoff, int C,
                        const T* l1, const T* l2, const T* l3, int n1, const int* skip, cudaStream_t s) {
@@ -139,8 +211,14 @@ cudaError_t dense_slow(const T* M, const T* in, T* out, int A, int ld, int nin, 
     unsigned bx = (unsigned)((AC + kDenseThreads - 1) / kDenseThreads);
     if (bx > 65535u) bx = 65535u;
     dim3 grid(bx, (nout + kRT - 1) / kRT);
+    DenseSlowArgs<T> p{M, in, out, A, ld, nin, nout, inoff, outoff, C, l1, l2, l3, n1, (int)bx};
+    if (g_rec) {
+        if (sizeof(T) != 8) g_rec->unsupported = true;
+        else record_launch(GK_DENSE_SLOW, p, (int)(grid.x * grid.y), kDenseThreads, 0, skip);
+        return cudaSuccess;
+    }
     launch_begin(S_FD_DIM23, s);
-    k_dense_slow<T><<<grid, kDenseThreads, 0, s>>>(M, in, out, A, ld, nin, nout, inoff, outoff, C, l1, l2, l3, n1, skip);
+    k_dense_slow<T><<<grid, kDenseThreads, 0, s>>>(p, skip);
     launch_end(S_FD_DIM23, s);
     return cudaGetLastError();
 }
@@ -151,8 +229,14 @@ cudaError_t dense_fast(const T* MT, const T* in, T* out, int A, int ld, int nin,
     size_t total = (size_t)((A + kAT - 1) / kAT) * nout;
     size_t blocks = (total + kDenseThreads - 1) / kDenseThreads;
     if (blocks > 1u << 20) blocks = 1u << 20;
+    DenseFastArgs<T> p{MT, in, out, A, ld, nin, nout, inoff, outoff, (int)blocks};
+    if (g_rec) {
+        if (sizeof(T) != 8) g_rec->unsupported = true;
+        else record_launch(GK_DENSE_FAST, p, (int)blocks, kDenseThreads, 0, skip);
+        return cudaSuccess;
+    }
     launch_begin(S_FD_DIM1, s);
-    k_dense_fast<T><<<(unsigned)blocks, kDenseThreads, 0, s>>>(MT, in, out, A, ld, nin, nout, inoff, outoff, skip);
+    k_dense_fast<T><<<(unsigned)blocks, kDenseThreads, 0, s>>>(p, skip);
     launch_end(S_FD_DIM1, s);
     return cudaGetLastError();
 }
@@ -162,8 +246,13 @@ cudaError_t fold(const double* in, double* out, int A, int n, int C, const int* 
     size_t total = (size_t)A * n * C;
     size_t blocks = (total + kThreads - 1) / kThreads;
     if (blocks > 1u << 20) blocks = 1u << 20;
+    FoldArgs p{in, out, A, n, C, (int)blocks};
+    if (g_rec) {
+        record_launch(UNFOLD ? GK_UNFOLD : GK_FOLD, p, (int)blocks, kThreads, 0, skip);
+        return cudaSuccess;
+    }
     launch_begin(S_FD_FOLD, s);
-    k_fold<UNFOLD><<<(unsigned)blocks, kThreads, 0, s>>>(in, out, A, n, C, skip);
+    k_fold<UNFOLD><<<(unsigned)blocks, kThreads, 0, s>>>(p, skip);
     launch_end(S_FD_FOLD, s);
     return cudaGetLastError();
 }
@@ -234,6 +323,17 @@ int run_fd_split(const DirD<double> d[3], const double* r, double* z, double* tm
 }
 
 }  // namespace
+
+bool grouped_launch_fd(int kind, const unsigned char* tab, int stride, int npatch, int grid, int smem, cudaStream_t s) {
+    (void)smem;
+    switch (kind) {
+        case GK_DENSE_SLOW: k_dense_slow_grouped<<<grid, kDenseThreads, 0, s>>>(tab, stride, npatch); return true;
+        case GK_DENSE_FAST: k_dense_fast_grouped<<<grid, kDenseThreads, 0, s>>>(tab, stride, npatch); return true;
+        case GK_FOLD: k_fold_grouped<false><<<grid, kThreads, 0, s>>>(tab, stride, npatch); return true;
+        case GK_UNFOLD: k_fold_grouped<true><<<grid, kThreads, 0, s>>>(tab, stride, npatch); return true;
+        default: return false;
+    }
+}
 
 int run_fd64(const DirD<double> d[3], const double* r, double* z, double* tmp, const int* skip, cudaStream_t s) {
     if (d[0].sym && d[1].sym && d[2].sym) return run_fd_split(d, r, z, tmp, skip, s);

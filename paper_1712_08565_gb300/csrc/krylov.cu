@@ -15,6 +15,7 @@
 #include <cmath>
 #include <cuda_runtime.h>
 
+#include "grouped.h"
 #include "krylov.h"
 #include "prof.h"
 
@@ -93,11 +94,12 @@ struct Dot2F {
 // conversions and arithmetic per element would make these memory-streaming
 // kernels FP64-pipe bound on this part.)
 template <int OP>
-__device__ __forceinline__ void vec_f32(const VArgs<float>& a, const KScal* __restrict__ sc, double& s0, double& s1) {
+__device__ __forceinline__ void vec_f32(const VArgs<float>& a, const KScal* __restrict__ sc, double& s0, double& s1,
+                                        int bx, int gdx) {
     const float beta = (float)sc->beta, omega = (float)sc->omega, alpha = (float)sc->alpha;
     const int half = sc->half;
     Dot2F k0, k1;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += (size_t)gridDim.x * blockDim.x) {
+    for (size_t i = (size_t)bx * blockDim.x + threadIdx.x; i < a.N; i += (size_t)gdx * blockDim.x) {
         if (OP == V_INIT) {
             const float fi = a.f[i];
             const float ri = a.x_given ? a.r[i] : fi;
@@ -136,17 +138,18 @@ __device__ __forceinline__ void vec_f32(const VArgs<float>& a, const KScal* __re
     s1 = k1.value();
 }
 
+// One block (virtual index bx of gdx) of a vector kernel; sh: 64 doubles of
+// shared memory.  Every block writes its two partial sums.
 template <typename T, int OP>
-__global__ void __launch_bounds__(kRedThreads) k_vec(VArgs<T> a, const KScal* __restrict__ sc, double* __restrict__ part) {
-    if (OP == V_DOT_TS ? sc->skip2 : sc->skip1) return;
-    __shared__ double sh[64];
+__device__ __forceinline__ void vec_body(const VArgs<T>& a, const KScal* __restrict__ sc, double* __restrict__ part,
+                                         int bx, int gdx, double* sh) {
     double s0 = 0.0, s1 = 0.0;
     const double beta = sc->beta, omega = sc->omega, alpha = sc->alpha;
     const int half = sc->half;
     if constexpr (sizeof(T) == 4) {
-        vec_f32<OP>(a, sc, s0, s1);
+        vec_f32<OP>(a, sc, s0, s1, bx, gdx);
     } else {
-        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += (size_t)gridDim.x * blockDim.x) {
+        for (size_t i = (size_t)bx * blockDim.x + threadIdx.x; i < a.N; i += (size_t)gdx * blockDim.x) {
             if (OP == V_INIT) {
                 T ri = a.x_given ? a.r[i] : a.f[i];
                 if (!a.x_given) a.x[i] = 0;
@@ -183,9 +186,16 @@ __global__ void __launch_bounds__(kRedThreads) k_vec(VArgs<T> a, const KScal* __
     if (OP == V_P) return;
     block_sum2(s0, s1, sh);
     if (threadIdx.x == 0) {
-        part[2 * blockIdx.x] = s0;
-        part[2 * blockIdx.x + 1] = s1;
+        part[2 * bx] = s0;
+        part[2 * bx + 1] = s1;
     }
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(kRedThreads) k_vec(VArgs<T> a, const KScal* __restrict__ sc, double* __restrict__ part) {
+    if (OP == V_DOT_TS ? sc->skip2 : sc->skip1) return;
+    __shared__ double sh[64];
+    vec_body<T, OP>(a, sc, part, blockIdx.x, gridDim.x, sh);
 }
 
 __device__ bool finite(double x) { return isfinite(x); }
@@ -193,13 +203,7 @@ __device__ bool finite(double x) { return isfinite(x); }
 // Finishing kernels: one block sums the partials in a fixed order, then one
 // thread updates the scalars.
 template <int OP>
-__global__ void __launch_bounds__(kRedThreads) k_finish(KScal* __restrict__ sc, const double* __restrict__ part, int nblk) {
-    if (OP == V_INIT) {
-        // always runs
-    } else if (OP == V_DOT_TS ? sc->skip2 : sc->skip1) {
-        return;
-    }
-    __shared__ double sh[64];
+__device__ __forceinline__ void finish_body(KScal* __restrict__ sc, const double* __restrict__ part, int nblk, double* sh) {
     double s0 = 0.0, s1 = 0.0;
     for (int i = threadIdx.x; i < nblk; i += blockDim.x) {
         s0 += part[2 * i];
@@ -278,18 +282,83 @@ __global__ void __launch_bounds__(kRedThreads) k_finish(KScal* __restrict__ sc, 
     }
 }
 
+template <int OP>
+__global__ void __launch_bounds__(kRedThreads) k_finish(KScal* __restrict__ sc, const double* __restrict__ part, int nblk) {
+    if (OP == V_INIT) {
+        // always runs
+    } else if (OP == V_DOT_TS ? sc->skip2 : sc->skip1) {
+        return;
+    }
+    __shared__ double sh[64];
+    finish_body<OP>(sc, part, nblk, sh);
+}
+
+// ---- grouped forms (batched FP64 solve)
+struct VecG {
+    VArgs<double> a;
+    const KScal* sc;
+    double* part;
+    int nblk;
+};
+struct FinG {
+    KScal* sc;
+    const double* part;
+    int nblk;
+};
+
+template <int OP>
+__global__ void __launch_bounds__(kRedThreads) k_vec_grouped(const unsigned char* __restrict__ tab, int stride, int npatch) {
+    __shared__ double sh[64];
+    grouped_for<VecG, true>(tab, stride, npatch, [&](const VecG& g, int item) { vec_body<double, OP>(g.a, g.sc, g.part, item, g.nblk, sh); });
+}
+
+template <int OP>
+__global__ void __launch_bounds__(kRedThreads) k_finish_grouped(const unsigned char* __restrict__ tab, int stride, int npatch) {
+    __shared__ double sh[64];
+    grouped_for<FinG, true>(tab, stride, npatch, [&](const FinG& g, int) { finish_body<OP>(g.sc, g.part, g.nblk, sh); });
+}
+
+constexpr int vec_kind(int op) {
+    return op == V_P ? GK_VEC_P : op == V_DOT_RV ? GK_VEC_DOT_RV : op == V_S ? GK_VEC_S : op == V_DOT_TS ? GK_VEC_DOT_TS
+         : op == V_XR ? GK_VEC_XR : GK_NONE;
+}
+constexpr int fin_kind(int op) {
+    return op == V_DOT_RV ? GK_FIN_DOT_RV : op == V_S ? GK_FIN_S : op == V_DOT_TS ? GK_FIN_DOT_TS : op == V_XR ? GK_FIN_XR
+         : GK_NONE;
+}
+
 template <typename T, int OP>
 cudaError_t vec(const VArgs<T>& a, const KScal* sc, double* part, cudaStream_t s) {
+    const int nblk = red_blocks(a.N);
+    if (g_rec) {
+        if (sizeof(T) != 8 || vec_kind(OP) == GK_NONE) {
+            g_rec->unsupported = true;
+            return cudaSuccess;
+        }
+        VecG g{*reinterpret_cast<const VArgs<double>*>(&a), sc, part, nblk};
+        record_launch(vec_kind(OP), g, nblk, kRedThreads, 0, OP == V_DOT_TS ? &sc->skip2 : &sc->skip1);
+        return cudaSuccess;
+    }
     launch_begin(S_KRYLOV, s);
-    k_vec<T, OP><<<kRedBlocks, kRedThreads, 0, s>>>(a, sc, part);
+    k_vec<T, OP><<<nblk, kRedThreads, 0, s>>>(a, sc, part);
     launch_end(S_KRYLOV, s);
     return cudaGetLastError();
 }
 
 template <int OP>
-cudaError_t fin(KScal* sc, const double* part, cudaStream_t s) {
+cudaError_t fin(KScal* sc, const double* part, size_t N, cudaStream_t s) {
+    const int nblk = red_blocks(N);
+    if (g_rec) {
+        if (fin_kind(OP) == GK_NONE) {
+            g_rec->unsupported = true;
+            return cudaSuccess;
+        }
+        FinG g{sc, part, nblk};
+        record_launch(fin_kind(OP), g, 1, kRedThreads, 0, OP == V_DOT_TS ? &sc->skip2 : &sc->skip1);
+        return cudaSuccess;
+    }
     launch_begin(S_KRYLOV, s);
-    k_finish<OP><<<1, kRedThreads, 0, s>>>(sc, part, kRedBlocks);
+    k_finish<OP><<<1, kRedThreads, 0, s>>>(sc, part, nblk);
     launch_end(S_KRYLOV, s);
     return cudaGetLastError();
 }
@@ -336,7 +405,7 @@ int krylov_enqueue_init(const LinOp<T>& A, const T* f, T* x, bool x_given, doubl
         STRY(axpby_into(f, b.v, b.r, N, s));
     }
     KTRY((vec<T, V_INIT>(a, dsc, part, s)));
-    KTRY(fin<V_INIT>(dsc, part, s));
+    KTRY(fin<V_INIT>(dsc, part, N, s));
     return MFWQ_OK;
 }
 
@@ -350,15 +419,15 @@ int krylov_enqueue_iter(const LinOp<T>& A, const LinOp<T>& P, const T* f, T* x, 
     STRY(P(b.p, b.ph, skip1));
     STRY(A(b.ph, b.v, skip1));
     KTRY((vec<T, V_DOT_RV>(a, dsc, part, s)));
-    KTRY(fin<V_DOT_RV>(dsc, part, s));
+    KTRY(fin<V_DOT_RV>(dsc, part, N, s));
     KTRY((vec<T, V_S>(a, dsc, part, s)));
-    KTRY(fin<V_S>(dsc, part, s));
+    KTRY(fin<V_S>(dsc, part, N, s));
     STRY(P(b.s, b.sh, skip2));
     STRY(A(b.sh, b.t, skip2));
     KTRY((vec<T, V_DOT_TS>(a, dsc, part, s)));
-    KTRY(fin<V_DOT_TS>(dsc, part, s));
+    KTRY(fin<V_DOT_TS>(dsc, part, N, s));
     KTRY((vec<T, V_XR>(a, dsc, part, s)));
-    KTRY(fin<V_XR>(dsc, part, s));
+    KTRY(fin<V_XR>(dsc, part, N, s));
     return MFWQ_OK;
 }
 
@@ -474,6 +543,23 @@ int add_f32_scaled(double* u, const float* d, const double* nrm2, size_t N, cuda
     k_add_f32_scaled<<<kRedBlocks, kRedThreads, 0, s>>>(u, d, nrm2, N);
     launch_end(S_KRYLOV, s);
     return cudaGetLastError() == cudaSuccess ? MFWQ_OK : MFWQ_ECUDA;
+}
+
+bool grouped_launch_krylov(int kind, const unsigned char* tab, int stride, int npatch, int grid, int smem,
+                           cudaStream_t s) {
+    (void)smem;
+    switch (kind) {
+        case GK_VEC_P: k_vec_grouped<V_P><<<grid, kRedThreads, 0, s>>>(tab, stride, npatch); return true;
+        case GK_VEC_DOT_RV: k_vec_grouped<V_DOT_RV><<<grid, kRedThreads, 0, s>>>(tab, stride, npatch); return true;
+        case GK_VEC_S: k_vec_grouped<V_S><<<grid, kRedThreads, 0, s>>>(tab, stride, npatch); return true;
+        case GK_VEC_DOT_TS: k_vec_grouped<V_DOT_TS><<<grid, kRedThreads, 0, s>>>(tab, stride, npatch); return true;
+        case GK_VEC_XR: k_vec_grouped<V_XR><<<grid, kRedThreads, 0, s>>>(tab, stride, npatch); return true;
+        case GK_FIN_DOT_RV: k_finish_grouped<V_DOT_RV><<<grid, kRedThreads, 0, s>>>(tab, stride, npatch); return true;
+        case GK_FIN_S: k_finish_grouped<V_S><<<grid, kRedThreads, 0, s>>>(tab, stride, npatch); return true;
+        case GK_FIN_DOT_TS: k_finish_grouped<V_DOT_TS><<<grid, kRedThreads, 0, s>>>(tab, stride, npatch); return true;
+        case GK_FIN_XR: k_finish_grouped<V_XR><<<grid, kRedThreads, 0, s>>>(tab, stride, npatch); return true;
+        default: return false;
+    }
 }
 
 template int axpby_into<double>(const double*, const double*, double*, size_t, cudaStream_t);

@@ -9,7 +9,15 @@
 
 namespace mfwq {
 
-constexpr int kRedBlocks = 1024;  // fixed reduction grid (deterministic sums)
+constexpr int kRedBlocks = 1024;  // largest reduction grid (deterministic sums)
+
+// Blocks of the reductions of a solve of N unknowns: one per 2048 entries, at
+// most kRedBlocks.  A fixed function of N, so a patch's sums are formed the
+// same way in a separate and in a batched solve.
+inline int red_blocks(size_t N) {
+    const size_t b = (N + 2047) / 2048;
+    return (int)(b < 1 ? 1 : (b > (size_t)kRedBlocks ? (size_t)kRedBlocks : b));
+}
 
 // Scalars of one BiCGStab solve, resident in device memory.
 struct KScal {

@@ -1,11 +1,13 @@
 // Launch counting and per-stage CUDA-event timing.
 #include <atomic>
 
+#include "grouped.h"
 #include "prof.h"
 
 namespace mfwq {
 
 thread_local Profiler* g_prof = nullptr;
+thread_local Recorder* g_rec = nullptr;
 std::atomic<long long> g_launches{0};
 namespace {
 thread_local cudaEvent_t t_begin = nullptr;
@@ -28,6 +30,7 @@ static cudaEvent_t take_event(Profiler* p) {
 
 void launch_begin(int tag, cudaStream_t s) {
     (void)tag;
+    if (g_rec) return;  // recording: nothing is launched
     g_launches.fetch_add(1, std::memory_order_relaxed);
     Profiler* p = g_prof;
     t_open = false;
@@ -39,7 +42,7 @@ void launch_begin(int tag, cudaStream_t s) {
 
 void launch_end(int tag, cudaStream_t s) {
     Profiler* p = g_prof;
-    if (!p || !p->on) return;
+    if (g_rec || !p || !p->on) return;
     p->launches[tag] += 1;
     if (!t_open) return;
     t_open = false;

@@ -11,6 +11,7 @@
 #include <cstdint>
 
 #include "apply_common.cuh"
+#include "grouped.h"
 #include "ptx_async.cuh"
 #include "stencil_x.cuh"
 
@@ -88,19 +89,18 @@ __device__ bool xstage_prefetch(const XArgs<T>& a, const T* __restrict__ y0, con
 // CARVE (0 or 1) only makes a separate function: CARVE = 1 copies are given a
 // smaller preferred shared-memory carveout, so fewer blocks share an SM and
 // the band tables they all read stay in a larger L1.
-template <typename T, int LINES, int MODE, int CARVE>
-__global__ void __launch_bounds__(kThreads) k_xstage_apply(XArgs<T> a, const T* __restrict__ y0, const T* __restrict__ y1,
-                                                           const T* __restrict__ y2, T* __restrict__ tout, size_t tstride,
-                                                           const int* skip, int* err) {
+// One block (virtual index bx) of the x stage; smem_raw: its shared memory.
+template <typename T, int LINES, int MODE>
+__device__ __forceinline__ void xstage_apply_body(const XArgs<T>& a, const T* __restrict__ y0, const T* __restrict__ y1,
+                                                  const T* __restrict__ y2, T* __restrict__ tout, size_t tstride, int* err,
+                                                  int bx, unsigned char* smem_raw) {
     constexpr bool PF = MODE >= 2;
     constexpr int MAP = MODE & 1;
-    if (skip && *skip) return;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     // [mbarrier, 16 B if PF][Y: 3][LINES][n1][H: 3][LINES][nq1][C (PF): 6][LINES][nq1]
     T* sY = reinterpret_cast<T*>(smem_raw + (PF ? 16 : 0));
     T* sH = sY + 3 * LINES * a.n1;
     T* sC = sH + 3 * LINES * a.nq1;
-    const int line0 = blockIdx.x * LINES;
+    const int line0 = bx * LINES;
     const int nl = min(LINES, a.nlines - line0);
     const int n1 = a.n1, nq1 = a.nq1;
     const int hs = LINES * nq1;
@@ -218,6 +218,33 @@ __global__ void __launch_bounds__(kThreads) k_xstage_apply(XArgs<T> a, const T* 
             }
         }
     }
+}
+
+template <typename T, int LINES, int MODE, int CARVE>
+__global__ void __launch_bounds__(kThreads) k_xstage_apply(XArgs<T> a, const T* __restrict__ y0, const T* __restrict__ y1,
+                                                           const T* __restrict__ y2, T* __restrict__ tout, size_t tstride,
+                                                           const int* skip, int* err) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    xstage_apply_body<T, LINES, MODE>(a, y0, y1, y2, tout, tstride, err, blockIdx.x, smem_raw);
+}
+
+// Grouped form (batched FP64 solve): mapping 0, 4 lines per block, every patch.
+struct XstageG {
+    XArgs<double> a;
+    const double* y0;
+    const double* y1;
+    const double* y2;
+    double* tout;
+    size_t tstride;
+    int* err;
+};
+
+__global__ void __launch_bounds__(kThreads) k_xstage_grouped(const unsigned char* __restrict__ tab, int stride, int npatch) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    grouped_for<XstageG, true>(tab, stride, npatch, [&](const XstageG& p, int item) {
+        xstage_apply_body<double, 4, 0>(p.a, p.y0, p.y1, p.y2, p.tout, p.tstride, p.err, item, smem_raw);
+    });
 }
 
 template <typename T, int MODE, int CARVE>
@@ -610,6 +637,15 @@ cudaError_t launch_forward_xstage(const OpCtx<T>& c, const XArgs<T>& a, const T*
     const DirD<T>& d1 = c.d[0];
     const int n1 = d1.n, q1 = d1.nq;
     const int nlines = a.nlines;
+    if (g_rec) {  // recorded as mapping 0 with 4 lines per block, the form every patch can share
+        if constexpr (sizeof(T) == 8) {
+            XstageG p{a, y0, y1, y2, tout, tstride, c.err};
+            record_launch(GK_XSTAGE0, p, (nlines + 3) / 4, kThreads, xstage_smem_bytes(8, n1, q1, 4, 0), skip);
+        } else {
+            g_rec->unsupported = true;
+        }
+        return cudaSuccess;
+    }
         int L = c.xlines == 2 || c.xlines == 8 ? c.xlines : 4;
         int mode = c.xmode >= 0 && c.xmode <= 6 ? c.xmode : 0;
         if (mode >= 4) L = mode == 6 ? kStLines : kTileLines;
@@ -701,8 +737,16 @@ static cudaError_t set_stencil_smem(int bytes) {
     return e;
 }
 
+bool grouped_launch_xstage(int kind, const unsigned char* tab, int stride, int npatch, int grid, int smem,
+                           cudaStream_t s) {
+    if (kind != GK_XSTAGE0) return false;
+    k_xstage_grouped<<<grid, kThreads, smem, s>>>(tab, stride, npatch);
+    return true;
+}
+
 cudaError_t configure_forward_xstage_smem(int bytes) {
     cudaError_t e = set_xstage_smem_all<0>(bytes);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) e = set_xstage_smem_all<1>(bytes);
     if (e == cudaSuccess) e = set_stencil_smem<float>(bytes);
     if (e == cudaSuccess) e = set_stencil_smem<double>(bytes);

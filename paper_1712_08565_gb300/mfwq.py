@@ -113,6 +113,8 @@ _SIGS = [
     ("mfwq_fp32_path", ctypes.c_int, [ctypes.c_void_p]),
     ("mfwq_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p)]),
     ("mfwq_batch_destroy", None, [ctypes.c_void_p]),
+    ("mfwq_batch_set_grouped", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("mfwq_batch_last_grouped", ctypes.c_int, [ctypes.c_void_p]),
     ("mfwq_batch_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfoC)]),
     ("mfwq_selftest_bounded_wait", ctypes.c_int, [ctypes.c_longlong, ctypes.c_void_p]),
@@ -521,6 +523,16 @@ class Batch:
         h = ctypes.c_void_p()
         _check(lib().mfwq_batch_create(len(self.ops), arr, ctypes.byref(h)))
         self._h = h
+
+    @property
+    def grouped(self) -> bool:
+        """True if the last FP64 solve ran grouped sweeps (mfwq_batch_last_grouped)."""
+        return bool(lib().mfwq_batch_last_grouped(self._h))
+
+    def set_grouped(self, groups: int):
+        """FP64 sweeps as grouped launches in `groups` concurrent groups of
+        patches (0: per-patch streams, the default) (mfwq_batch_set_grouped)."""
+        _check(lib().mfwq_batch_set_grouped(self._h, int(groups)))
 
     def close(self):
         if getattr(self, "_h", None):

@@ -40,7 +40,9 @@ def test_batch_equals_separate_solves(mf):
     fs = [op.load_vector("ring", "sines") for op in ops]
     ref = [op.solve(f, rtol=1e-8, force_fp64=True) for op, f in zip(ops, fs)]
     b = mf.Batch(ops)
+    b.set_grouped(1)  # one grouped launch per kernel stage over all patches
     us, infos = b.solve(fs, rtol=1e-8, maxit=500)
+    assert b.grouped
     for (u0, i0), u, i in zip(ref, us, infos):
         assert i.converged and i0.converged
         assert i.iterations == i0.iterations
@@ -55,6 +57,33 @@ def test_batch_equals_separate_solves(mf):
         fn = f.cpu().numpy().ravel()
         res = np.linalg.norm(fn - K @ u.cpu().numpy().ravel()) / np.linalg.norm(fn)
         assert res <= 2e-8
+        op.close()
+
+
+def test_grouped_sweep_equals_per_stream_sweep(mf):
+    """The grouped FP64 sweep and the per-patch-stream sweep give the same
+    bits; a patch with a reaction term (no grouped form) makes the batch fall
+    back to per-patch streams, still matching its separate solve."""
+    specs = inputs.batch_patches(count=5, seed=11, nel_range=(3, 10))
+    ops = [_patch(mf, p, nel, 40 + i) for i, (p, nel) in enumerate(specs)]
+    fs = [op.load_vector("ring", "sines") for op in ops]
+    b = mf.Batch(ops)
+    us, i_s = b.solve(fs, rtol=1e-9)  # per-patch streams (the default)
+    assert not b.grouped
+    for groups in (1, 2, 3):
+        b.set_grouped(groups)
+        ug, ig = b.solve(fs, rtol=1e-9)
+        assert b.grouped
+        for u1, u2, a, c in zip(ug, us, ig, i_s):
+            assert a.converged and c.converged and a.iterations == c.iterations
+            assert torch.equal(u1, u2)
+    ops[2].set_mass_coeff(ops[2].eval_mass_coeff("ring", 3.0), fd_shift=3.0)
+    ur, ir = b.solve(fs, rtol=1e-9)
+    assert not b.grouped
+    u_sep, i_sep = ops[2].solve(fs[2], rtol=1e-9, force_fp64=True)
+    assert ir[2].iterations == i_sep.iterations and torch.equal(ur[2], u_sep)
+    b.close()
+    for op in ops:
         op.close()
 
 

@@ -177,6 +177,11 @@ def test_batched_64_patches(mf):
     assert all(i.converged and i.rel_residual <= 1e-8 for i in infos)
     um, minfos = b.solve(fs, [torch.empty_like(f) for f in fs], rtol=1e-8)
     assert all(i.converged and i.rel_residual <= 1e-8 for i in minfos)
+    b.set_grouped(4)  # the grouped sweep (4 concurrent groups): the same bits as the per-patch streams
+    ug, ginfos = b.solve(fs, [torch.empty_like(f) for f in fs], rtol=1e-8, force_fp64=True)
+    assert b.grouped
+    assert all(a.iterations == c.iterations for a, c in zip(ginfos, infos))
+    assert all(torch.equal(x, y) for x, y in zip(ug, us))
     for i in range(6):  # the oracle checks the residual of a few patches, FP64 and mixed
         box = O.coefficient_box_fn(tabs[i], "ring", inputs.fourier_modes(1000 + i), 0.3)
         rows = _rows(ops[i].shape, 8, i)
