@@ -18,7 +18,14 @@ solve time and iteration count, the isolated apply and FD times, the apply
 DoF/s for p = 2..6 at 128 elements, the mixed-precision versus FP64 solve to
 1e-8 on the p = 6, 192-element ring, the 64-patch batched solves, the
 reaction term, and the transposed apply / coefficient gradient on the
-adjoint workload (ring p = 3, 64 elements, K = exp(0.3 g) I).
+adjoint workload (ring p = 3, 64 elements, K = exp(0.3 g) I), the FP32 apply
+in its two kernel sequences (staged, fused), the FP32 apply and mixed solve
+with the coefficient stored or evaluated in the x stage, and the grouped
+form of the batched FP64 sweep.
+
+Timing: the headline solves run with CUDA events around the dominant
+kernel's launches only (its per-launch time for the roofline); the per-stage
+breakdown comes from one fully profiled solve outside the timed region.
 """
 from __future__ import annotations
 
@@ -167,13 +174,25 @@ def stage_flops(mf, p, knots):
     }, n, nq
 
 
-def csrc_digest() -> str:
-    """sha256 over the library's CUDA/C++ sources (names and contents): the
-    identity of the kernels a profile's counters were taken on."""
+# Sources that define each profiled kernel (its body, the device helpers and
+# the argument types it includes): a profile's counters stay valid while these
+# files are unchanged.
+KERNEL_SOURCES = {
+    "k_xstage_apply": ["xstage_kernels.cu", "apply_common.cuh", "stencil_x.cuh", "kernels.h", "mfwq_internal.h",
+                       "ptx_async.cuh", "grouped.h", "../../include/mfwq.h"],
+}
+
+
+def csrc_digest(kernel: str | None = None) -> str:
+    """sha256 over the sources of a kernel (KERNEL_SOURCES), or over all the
+    library's CUDA/C++ sources (names and contents): the identity of the code
+    a profile's counters were taken on."""
     import hashlib
     d = os.path.join(ROOT, "paper_1712_08565_gb300", "csrc")
     h = hashlib.sha256()
-    for name in sorted(os.listdir(d)):
+    key = next((k for k in KERNEL_SOURCES if kernel and kernel.startswith(k)), None)
+    names = KERNEL_SOURCES[key] if key else sorted(os.listdir(d))
+    for name in names:
         if name.endswith((".cu", ".cuh", ".h", ".cpp")):
             h.update(name.encode())
             with open(os.path.join(d, name), "rb") as fh:
@@ -190,7 +209,7 @@ def profiled_traffic(kernel: str, workload: str):
     d = os.path.join(ROOT, "profiles")
     if not os.path.isdir(d):
         return None
-    digest = csrc_digest()
+    digest = csrc_digest(kernel)
     pat = re.compile(r'<!-- traffic kernel="([^"]+)" workload="([^"]+)" bytes_per_launch=(\d+) csrc_sha256=([0-9a-f]+) -->')
     for name in sorted(os.listdir(d)):
         if not name.endswith(".md"):
@@ -504,6 +523,69 @@ def mixed_vs_fp64(mf, device):
                     "apply_f32": event_time(op.stream, lambda: op.apply_f32(x32, y32), 10),
                     "fd_f64": event_time(op.stream, lambda: op.fd_precond(x, y), 5),
                     "fd_tf32": event_time(op.stream, lambda: op.fd_precond_f32(x32, y32), 10)}
+    # the two FP32 kernel sequences (the autotuned one is used by the solves above)
+    res["fp32_path_autotuned"] = op.fp32_path
+    chosen = op.fp32_path
+    paths = {}
+    for path in ("staged", "fused"):
+        try:
+            op.fp32_path = path
+        except Exception:
+            continue
+        op.apply_f32(x32, y32)
+        paths[path] = event_time(op.stream, lambda: op.apply_f32(x32, y32), 10)
+    op.fp32_path = chosen
+    res["op_ms"]["apply_f32_by_path"] = paths
+    op.close()
+    torch.cuda.empty_cache()
+    return res
+
+
+def coeff_onthefly(mf, device):
+    """Section 3.2's remark on storing the coefficient, measured: the FP32
+    operator of the p = 6, 192-element ring with C read from the stored FP32
+    copy (1.48 GB) against C evaluated in the x stage (mfwq_set_coeff_field),
+    for K = I and for the 8-mode field of the adjoint workload, each on the
+    faster FP32 kernel sequence; and the mixed solve to 1e-8 with each."""
+    import torch
+    from paper_1712_08565_gb300 import inputs
+    op, _ = make_op(mf, MIXED["p"], MIXED["nel"], mixed=True, fd="tf32", device=device)
+    x32 = torch.from_numpy(inputs.uniform_vector(op.shape, 1)).float().to(device)
+    y32 = torch.empty_like(x32)
+    res = {"workload": MIXED["name"], "fp32_coefficient_bytes_saved": 6 * op.Nq * 4}
+
+    def best_apply():
+        out = {}
+        for path in ("staged", "fused"):
+            try:
+                op.fp32_path = path
+            except Exception:
+                continue
+            op.apply_f32(x32, y32)
+            out[path] = event_time(op.stream, lambda: op.apply_f32(x32, y32), 10)
+        best = min(out, key=out.get)
+        op.fp32_path = best
+        return out, best
+
+    def mixed_solve(f):
+        op.solve(f, rtol=MIXED["rtol"], maxit=2000)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, info = op.solve(f, rtol=MIXED["rtol"], maxit=2000)
+        torch.cuda.synchronize()
+        return {"time_s": time.perf_counter() - t0, "iterations": info.iterations, "outer": info.outer_iterations,
+                "rel_residual": info.rel_residual, "converged": info.converged}
+
+    f = op.load_vector("ring", "sines")
+    for field, modes, ks in (("K=I", None, 0.0), ("fourier8_k0.3", inputs.fourier_modes(ADJOINT["modes_seed"]), 0.3)):
+        entry = {}
+        for form, otf in (("stored", False), ("onthefly", True)):
+            op.set_coeff_field("ring", modes, ks, onthefly=otf)
+            times, best = best_apply()
+            entry[form] = {"apply_f32_ms": times, "best_path": best, "mixed_solve": mixed_solve(f)}
+        entry["onthefly_over_stored_apply"] = (min(entry["onthefly"]["apply_f32_ms"].values()) /
+                                               min(entry["stored"]["apply_f32_ms"].values()))
+        res[field] = entry
     op.close()
     torch.cuda.empty_cache()
     return res
@@ -547,6 +629,19 @@ def batched(mf, device):
     torch.cuda.synchronize()
     tm = time.perf_counter() - t0
     merr = max(float(torch.linalg.vector_norm(u - v) / torch.linalg.vector_norm(v)) for u, v in zip(us, u64))
+    # the grouped FP64 sweep: one launch per kernel stage over each of 4 groups of patches
+    b.set_grouped(4)
+    ug = [torch.empty_like(f) for f in fs]
+    b.solve(fs, ug, rtol=BATCH["rtol"], force_fp64=True)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, ginfos = b.solve(fs, ug, rtol=BATCH["rtol"], force_fp64=True)
+    torch.cuda.synchronize()
+    tg = time.perf_counter() - t0
+    g_ran = b.grouped
+    g_equal = all(torch.equal(a, c) for a, c in zip(ug, u64))
+    b.set_grouped(0)
+    del ug
     t0 = time.perf_counter()
     seq_iters = []
     for op, f, u in zip(ops, fs, us):
@@ -563,7 +658,9 @@ def batched(mf, device):
            "sweeps": max(i.outer_iterations for i in infos), "iterations_min_max": [min(i.iterations for i in infos), max(i.iterations for i in infos)],
            "all_converged": all(i.converged for i in infos),
            "apply_dof_per_s": sum(2 * i.iterations * op.N for i, op in zip(infos, ops)) / tb,
-           "autotuned_xstage": {str(k): v for k, v in sorted(lines.items())}}
+           "autotuned_xstage": {str(k): v for k, v in sorted(lines.items())},
+           "grouped_4_s": tg, "grouped_ran": g_ran, "grouped_bitwise_equal_to_streams": g_equal,
+           "grouped_all_converged": all(i.converged for i in ginfos)}
     b.close()
     for op in ops:
         op.close()
@@ -596,14 +693,22 @@ def run_ours(args):
 
     for _ in range(max(args.warmup, 3)):
         _, info = step()
-    # timed region
+    # stage breakdown: one more solve with every launch bracketed by CUDA
+    # events, outside the timed region
+    op.profile(True)
+    op.profile_read(reset=True)
+    step()
+    stages = op.profile_read(reset=True)
+    flops, n, nq = stage_flops(mf, p, knots)
+    dom = max((k for k in stages if k in flops), key=lambda k: stages[k][0])
+    # timed region: events bracket only the dominant kernel's launches (its
+    # per-launch time for the roofline, measured live at negligible cost)
+    op.profile_stages([dom])
     uuid = None
     try:
         uuid = "GPU-" + str(torch.cuda.get_device_properties(device).uuid)
     except Exception:
         uuid = None
-    op.profile(True)
-    op.profile_read(reset=True)
     iters = []
     with ClockSampler(uuid) as clk:
         if ws > 1:
@@ -624,23 +729,29 @@ def run_ours(args):
         launches = mf.kernel_launches() - launches0
         ms_total = e0.elapsed_time(e1)
     clocks = clk.summary()
-    stages = op.profile_read(reset=True)
+    dom_stat = op.profile_read(reset=True)[dom]
     op.profile(False)
+    op.profile_stages(None)
     ms_step = ms_total / args.steps
     applies_per_solve = 2 * statistics.mean(iters)
     ms_step, units = reduce_over_ranks(ms_step, op.N * applies_per_solve, device)
     value = units / (ms_step * 1e-3)
 
-    # roofline of the dominant kernel (largest share of the timed region)
-    flops, n, nq = stage_flops(mf, p, knots)
-    dom = max((k for k in stages if k in flops), key=lambda k: stages[k][0])
-    dom_ms = stages[dom][0] / stages[dom][1]
+    # roofline of the dominant kernel (largest share of the profiled solve),
+    # its per-launch time from the events around its launches in the timed region
+    dom_ms = dom_stat[0] / dom_stat[1]
     achieved = flops[dom] / (dom_ms * 1e-3) / 1e12
     peak = fp64_peak_tflops()
+    peak_probe = mf.probe_fma_rate(True)
     dom_kernel = xstage_kernel_name(op.tune_code, "double", WORKLOAD["p"]) if dom == "xstage" and op.tune_code else dom
     roofline = {"bound": "alu", "kernel": dom, "kernel_function": dom_kernel, "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": achieved / peak, "traffic": profiled_traffic(dom_kernel, WORKLOAD["name"]),
-                "peak_source": "FP64 pipe: 152 SMs x 2070 MHz x 4 flop/clk (1.25 TFLOP/s nominal); not in MEASURED_PEAKS.json",
+                "peak_source": "FP64 pipe: 152 SMs x 2070 MHz x 4 flop/clk (1.25 TFLOP/s, unit counts and clock; "
+                               "MEASURED_PEAKS.json holds no FP64 figure)",
+                "peak_measured": peak_probe, "frac_of_measured": achieved / peak_probe,
+                "peak_measured_source": "in-process FP64 FMA-chain probe on this GPU (mfwq_probe_fma_rate), plain "
+                                        "CUDA-event timing, no setting changed",
+                "launches_timed": dom_stat[1],
                 "algorithmic_flops_per_launch": flops[dom], "ms_per_launch": dom_ms}
 
     # isolated apply and FD (same launch configuration)
@@ -675,6 +786,7 @@ def run_ours(args):
     if not args.no_extras:
         extras["p_sweep_nel128"] = p_sweep(mf, device)
         extras["mixed_vs_fp64"] = mixed_vs_fp64(mf, device)
+        extras["coeff_onthefly"] = coeff_onthefly(mf, device)
         extras["batched_64"] = batched(mf, device)
         extras["reaction"] = reaction(mf, device)
         extras["fp64_solve_low_fd"] = fp64_low_fd(mf, device)
@@ -691,6 +803,8 @@ def run_ours(args):
         "fd_precond_ms": fd_ms,
         "stages_ms_per_launch": {k: v[0] / v[1] for k, v in stages.items()},
         "stages_share": {k: v[0] / sum(s[0] for s in stages.values()) for k, v in stages.items()},
+        "stages_source": "one profiled solve after the warm-up, every launch bracketed by CUDA events (outside the "
+                         "timed region, whose solves bracket only the dominant kernel)",
         "roofline": roofline,
         "e2e": e2e,
         "gpu_launches": launches,

@@ -238,6 +238,12 @@ typedef struct {
                               operator and the residual stay FP64, so the tolerance is met in
                               FP64; only the preconditioner is inexact.  MFWQ_EINVAL on a
                               handle without mixed = 1 and in mfwq_batch_solve. */
+    int graph_chunk;       /* FP64 single-patch solves: > 1 captures that many BiCGStab iterations
+                              into one CUDA graph, launched between two host checks of the
+                              device-resident scalars (iterations after convergence are skipped
+                              on the device); 0 or 1: one check per iteration.  Ignored with
+                              res_hist, while profiling, on the legacy stream, and when the
+                              capture fails (the iterations then run uncaptured). */
 } mfwq_solve_opts;
 
 typedef struct {
@@ -386,6 +392,16 @@ int mfwq_batch_last_grouped(mfwq_batch b);
  * context stays usable), MFWQ_EINTERNAL if it did not.  Synchronous. */
 int mfwq_selftest_bounded_wait(long long limit_cycles, void* stream);
 
+/* ---- arithmetic-throughput probe (no counterpart in the paper) ------------
+ * *tflops = the fused multiply-add throughput of the current device in FP64
+ * (fp64 = 1) or FP32 (fp64 = 0), in TFLOP/s (an FMA counts 2): every thread
+ * runs independent FMA chains in registers; the best rate over three timed
+ * launches (after one warm-up) at each of 4, 8 and 16 blocks per SM (CUDA
+ * events on `stream`, may be NULL).  The measured
+ * denominator of the FP64- and FP32-pipe rooflines.  Allocates a small
+ * output buffer; changes no device setting.  Synchronous. */
+int mfwq_probe_fma_rate(int fp64, void* stream, double* tflops);
+
 /* ---- instrumentation (no counterpart in the paper) -------------------------
  * Kernel stages, in the index order of mfwq_profile_stats: trial_z, trial_y,
  * xstage, test_y, test_z (the five stages of the apply), test_zT, test_yT,
@@ -403,6 +419,11 @@ typedef struct {
 /* With on = 1, every kernel the handle launches afterwards is bracketed by
  * CUDA events on the handle's stream (a few microseconds per launch). */
 int mfwq_profile_enable(mfwq_handle h, int on);
+
+/* Restricts the event bracketing of mfwq_profile_enable to the stages whose
+ * bit (1 << stage index) is set in mask (default: all).  Launches of other
+ * stages are still counted.  Launches no work. */
+int mfwq_profile_stage_mask(mfwq_handle h, unsigned long long mask);
 
 /* Waits for the recorded events and sums them per stage; reset = 1 clears the
  * totals afterwards.  Synchronous. */

@@ -587,8 +587,9 @@ int solve64(mfwq_handle h, const double* f, double* u, const mfwq_solve_opts& o,
     }
     int iters = 0, status = MFWQ_OK;
     double rel = 0.0;
+    const int chunk = h->prof.on ? 0 : o.graph_chunk;  // profiling events cannot be captured
     ST(bicgstab<double>(A, P, f, u, o.use_initial_guess != 0, o.rtol, o.maxit, bufs64(h), h->dsc, h->hsc, h->part, h->N, s,
-                        1, o.res_hist, &iters, &rel, &status));
+                        1, o.res_hist, &iters, &rel, &status, chunk));
     if (info) {
         info->status = status;
         info->iterations = iters;
@@ -1003,6 +1004,12 @@ const char* mfwq_stage_name(int stage) { return stage >= 0 && stage < S_NTAGS ? 
 int mfwq_profile_enable(mfwq_handle h, int on) {
     if (!h) return fail(MFWQ_EINVAL, "NULL handle");
     h->prof.on = on != 0;
+    return MFWQ_OK;
+}
+
+int mfwq_profile_stage_mask(mfwq_handle h, unsigned long long mask) {
+    if (!h) return fail(MFWQ_EINVAL, "NULL handle");
+    h->prof.mask = mask;
     return MFWQ_OK;
 }
 

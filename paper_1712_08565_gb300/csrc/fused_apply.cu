@@ -437,7 +437,7 @@ __global__ void __launch_bounds__(kFusedThreads, 2) k_apply_fused(FusedArgs a) {
     float* sZ = sT + 3 * kFusedLines * a.rT;                     // [2][RZ][n1]
     float* sU = sZ + 2 * a.RZ * n1;                              // [4][RU][n1]
     float* sK = sU + 4 * a.RU * n1;                              // ONF: [8][rG] kappa of the batch's lines
-    float* sAB = sK + kFusedLines * a.rG;                        // ONF: [8][kMaxModes][3]
+    float* sAB = sK + kFusedLines * a.rG;                        // ONF: [8][kMaxModes][4]
     // both rings start at zero: zero taps of a uniform batch may read Z slots
     // no row was loaded into, and must not meet a NaN pattern there
     for (int i = threadIdx.x; i < n1; i += kFusedThreads) {
@@ -588,7 +588,7 @@ int fused_plan_build(const Dir1D& d1, const Dir1D& d2, const StencilD<float>& S1
         return MFWQ_OK;
     }
     pl.smem = (int)(floats * sizeof(float));
-    pl.smem_onf = (int)((floats + (size_t)kFusedLines * pl.rG + (size_t)kFusedLines * kMaxModes * 3) * sizeof(float));
+    pl.smem_onf = (int)((floats + (size_t)kFusedLines * pl.rG + (size_t)kFusedLines * kMaxModes * 4) * sizeof(float));
     int st = configure_fused_smem(std::min(pl.smem_onf, kXstageSmemMax));
     if (st != MFWQ_OK) return st;
     int dev = 0, sms = 0, bps = 0;

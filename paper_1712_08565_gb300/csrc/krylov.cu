@@ -442,14 +442,42 @@ void krylov_result(const KScal& h, int* iters, double* relres, int* status) {
 template <typename T>
 int bicgstab(const LinOp<T>& A, const LinOp<T>& P, const T* f, T* x, bool x_given, double rtol, int maxit,
              const KrylovBufs<T>& b, KScal* dsc, KScal* hsc, double* part, size_t N, cudaStream_t s, int check_every,
-             double* hist, int* iters, double* relres, int* status) {
+             double* hist, int* iters, double* relres, int* status, int graph_chunk) {
     STRY(krylov_enqueue_init<T>(A, f, x, x_given, rtol, b, dsc, part, N, s));
     KTRY(cudaMemcpyAsync(hsc, dsc, sizeof(KScal), cudaMemcpyDeviceToHost, s));
     KTRY(cudaStreamSynchronize(s));
     if (hist) hist[0] = hsc->f2 > 0 ? std::sqrt(hsc->r2 / hsc->f2) : 0.0;
     if (!hsc->skip1) {
         if (check_every < 1) check_every = 1;
-        for (int it = 0; it < maxit; ++it) {
+        // graph_chunk > 1: that many iterations captured once into a CUDA graph, launched
+        // between host checks (iterations after convergence are skipped on the device)
+        cudaGraphExec_t exec = nullptr;
+        if (graph_chunk > 1 && !hist && s != nullptr && maxit >= graph_chunk) {
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                int cst = MFWQ_OK;
+                for (int k = 0; k < graph_chunk && cst == MFWQ_OK; ++k)
+                    cst = krylov_enqueue_iter<T>(A, P, f, x, b, dsc, part, N, s);
+                const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+                if (cst != MFWQ_OK || ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+                    exec = nullptr;
+                if (graph) cudaGraphDestroy(graph);
+            }
+            cudaGetLastError();
+        }
+        int it = 0;
+        while (exec && it + graph_chunk <= maxit) {
+            if (cudaGraphLaunch(exec, s) != cudaSuccess) {
+                cudaGraphExecDestroy(exec);
+                return MFWQ_ECUDA;
+            }
+            it += graph_chunk;
+            KTRY(cudaMemcpyAsync(hsc, dsc, sizeof(KScal), cudaMemcpyDeviceToHost, s));
+            KTRY(cudaStreamSynchronize(s));
+            if (hsc->skip1) break;
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        for (; it < maxit && !hsc->skip1; ++it) {
             STRY(krylov_enqueue_iter<T>(A, P, f, x, b, dsc, part, N, s));
             if ((it + 1) % check_every == 0 || it + 1 == maxit || hist) {
                 KTRY(cudaMemcpyAsync(hsc, dsc, sizeof(KScal), cudaMemcpyDeviceToHost, s));
@@ -574,9 +602,9 @@ template int krylov_enqueue_iter<float>(const LinOp<float>&, const LinOp<float>&
                                          const KrylovBufs<float>&, KScal*, double*, size_t, cudaStream_t);
 template int bicgstab<double>(const LinOp<double>&, const LinOp<double>&, const double*, double*, bool, double, int,
                               const KrylovBufs<double>&, KScal*, KScal*, double*, size_t, cudaStream_t, int, double*, int*,
-                              double*, int*);
+                              double*, int*, int);
 template int bicgstab<float>(const LinOp<float>&, const LinOp<float>&, const float*, float*, bool, double, int,
                              const KrylovBufs<float>&, KScal*, KScal*, double*, size_t, cudaStream_t, int, double*, int*,
-                             double*, int*);
+                             double*, int*, int);
 
 }  // namespace mfwq

@@ -43,7 +43,7 @@ struct KrylovBufs {
 template <typename T>
 int bicgstab(const LinOp<T>& A, const LinOp<T>& P, const T* f, T* x, bool x_given, double rtol, int maxit,
              const KrylovBufs<T>& b, KScal* dsc, KScal* hsc, double* part, size_t N, cudaStream_t s, int check_every,
-             double* hist, int* iters, double* relres, int* status);
+             double* hist, int* iters, double* relres, int* status, int graph_chunk = 0);
 
 // Enqueue-only pieces of the same solver (no host synchronisation), for
 // callers that capture iterations into CUDA graphs: the init kernels, one

@@ -34,7 +34,7 @@ void launch_begin(int tag, cudaStream_t s) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     Profiler* p = g_prof;
     t_open = false;
-    if (!p || !p->on) return;
+    if (!p || !p->on || !((p->mask >> tag) & 1ull)) return;
     if (p->pending.size() >= 16384) p->drain();
     t_begin = take_event(p);
     if (t_begin && cudaEventRecord(t_begin, s) == cudaSuccess) t_open = true;
@@ -44,6 +44,7 @@ void launch_end(int tag, cudaStream_t s) {
     Profiler* p = g_prof;
     if (g_rec || !p || !p->on) return;
     p->launches[tag] += 1;
+    if (!((p->mask >> tag) & 1ull)) return;
     if (!t_open) return;
     t_open = false;
     cudaEvent_t e = take_event(p);

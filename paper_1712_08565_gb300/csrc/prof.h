@@ -16,6 +16,7 @@ enum StageTag {
 
 struct Profiler {
     bool on = false;
+    unsigned long long mask = ~0ull;  // stages bracketed by events while on (bit = stage tag)
     struct Pending {
         cudaEvent_t a, b;
         int tag;

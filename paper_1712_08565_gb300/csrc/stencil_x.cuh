@@ -159,12 +159,13 @@ __device__ __forceinline__ void st_trial(const XArgs<T>& a, const StencilD<T>& s
 // kappa(x) = exp(kscale g(x)) at every point of the block's lines line0 ..
 // line0 + nl - 1 (global line index q3 * nq2 + q2), into sK[l * rK + q1].  One
 // thread per (line, mode) first forms the line's phase coefficients in FP64
-// (2A as an unevaluated sum of two floats, B reduced to [-1, 1]) in sAB
-// [8][kMaxModes][3]; then one thread per point sums the modes in FP32 with
-// CUDA's cospif and expf.  The phase (2A) s is formed as a float pair and
-// reduced modulo 2 before rounding, so the argument of cospif carries an
-// absolute error near 1e-7 half-turns rather than ulp(|2 A s|).  Ends with a
-// barrier.
+// (2A and B, reduced to [-1, 1], each as an unevaluated sum of two floats) in
+// sAB [8][kMaxModes][4]; then one thread per point sums the modes in FP32
+// with CUDA's sincospif and expf.  The phase 2A s + B is carried as a float
+// pair through its reduction modulo 2, and the cosine of the pair is
+// cospi(hi) - pi lo sinpi(hi), so the cosine's error is that of sincospif
+// (about one FP32 ulp) instead of the rounding of a phase of up to 17
+// half-turns.  Ends with a barrier.
 __device__ __forceinline__ void st_kappa(const CoeffField& f, int line0, int nl, int nq1, int nq2, float* sK, int rK,
                                          float* sAB) {
     const int nm = f.nmodes;
@@ -185,27 +186,36 @@ __device__ __forceinline__ void st_kappa(const CoeffField& f, int line0, int nl,
         const double A2 = 2.0 * A;
         double B = 2.0 * C3 + f.phi_pi[m];
         B -= 2.0 * rint(0.5 * B);
-        const float hi = (float)A2;
-        float* o = sAB + (l * kMaxModes + m) * 3;
+        const float hi = (float)A2, bh = (float)B;
+        float* o = sAB + (l * kMaxModes + m) * 4;
         o[0] = hi;
         o[1] = (float)(A2 - (double)hi);
-        o[2] = (float)B;
+        o[2] = bh;
+        o[3] = (float)(B - (double)bh);
     }
     __syncthreads();
     for (int e = threadIdx.x; e < nl * nq1; e += blockDim.x) {
         const int l = e / nq1, q = e - l * nq1;
         const float sh = f.s1[q], sl = f.s1[nq1 + q];
-        const float* ab = sAB + l * kMaxModes * 3;
+        const float* ab = sAB + l * kMaxModes * 4;
         float g = 0.f;
         for (int m = 0; m < nm; ++m) {
-            const float ah = ab[3 * m], al = ab[3 * m + 1], b = ab[3 * m + 2];
+            const float ah = ab[4 * m], al = ab[4 * m + 1], bh = ab[4 * m + 2], bl = ab[4 * m + 3];
+            // phase (ah + al)(sh + sl) + (bh + bl) in half-turns as t + lo, |t| <= 2
             const float p = ah * sh;
             float err = fmaf(ah, sh, -p);  // exact error of the rounded product
             err = fmaf(ah, sl, err);
             err = fmaf(al, sh, err);
             const float n = rintf(0.5f * p);
             const float pr = fmaf(-2.f, n, p);  // p - 2n, exact
-            g = fmaf(f.a[m], cospif(pr + (err + b)), g);
+            const float t = __fadd_rn(pr, bh);  // TwoSum: t + e = pr + bh exactly
+            const float z = __fsub_rn(t, pr);
+            const float e = __fadd_rn(__fsub_rn(pr, __fsub_rn(t, z)), __fsub_rn(bh, z));
+            const float lo = e + (err + bl);
+            // cos(pi (t + lo)) = cospi(t) - pi lo sinpi(t) to first order in lo (|lo| < 1e-6)
+            float sn, cs;
+            sincospif(t, &sn, &cs);
+            g = fmaf(f.a[m], fmaf(-3.14159265f * lo, sn, cs), g);
         }
         sK[l * rK + q] = expf(f.kscale * g);
     }

@@ -539,7 +539,7 @@ __global__ void __launch_bounds__(kThreads) k_xstage_stencil_otf(XArgs<float> a,
     float* sT = sY + kStLines * rY;
     float* sH = sT + 3 * kStLines * rT;
     float* sK = sH + 3 * kStLines * rG;      // [8][rG]: kappa of the block's lines
-    float* sAB = sK + kStLines * rG;         // [8][kMaxModes][3]
+    float* sAB = sK + kStLines * rG;         // [8][kMaxModes][4]
     st_load_y(y0, n1, line0, nl, sY, rY);
     ptx::cp_async_commit();
     stx::st_kappa(cf, line0, nl, a.nq1, nq2, sK, rG, sAB);
@@ -572,7 +572,7 @@ __global__ void __launch_bounds__(kThreads) k_xstage_stencil_otf(XArgs<float> a,
 
 int xstage_otf_smem_bytes(int n1, int nq1) {
     return (int)(((size_t)kStLines * (4 * (size_t)st_stride(n1) + 4 * (size_t)st_stride(nq1)) +
-                  (size_t)kStLines * kMaxModes * 3) * sizeof(float));
+                  (size_t)kStLines * kMaxModes * 4) * sizeof(float));
 }
 
 static void launch_stencil_otf(const StencilD<float>& S, const CoeffField& cf, int nlines, int nq2, size_t sm,

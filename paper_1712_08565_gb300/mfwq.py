@@ -37,7 +37,7 @@ class SetupDesc(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int), ("inner_rtol", ctypes.c_double),
                 ("inner_maxit", ctypes.c_int), ("use_initial_guess", ctypes.c_int), ("force_fp64", ctypes.c_int),
-                ("res_hist", _c_dptr), ("fp64_low_fd", ctypes.c_int)]
+                ("res_hist", _c_dptr), ("fp64_low_fd", ctypes.c_int), ("graph_chunk", ctypes.c_int)]
 
 
 class ProfileStats(ctypes.Structure):
@@ -104,6 +104,7 @@ _SIGS = [
     ("mfwq_sync", ctypes.c_int, [ctypes.c_void_p]),
     ("mfwq_profile_enable", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     ("mfwq_profile_read", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ProfileStats), ctypes.c_int]),
+    ("mfwq_profile_stage_mask", ctypes.c_int, [ctypes.c_void_p, ctypes.c_ulonglong]),
     ("mfwq_stage_name", ctypes.c_char_p, [ctypes.c_int]),
     ("mfwq_kernel_launches", ctypes.c_longlong, []),
     ("mfwq_autotune", ctypes.c_int, [ctypes.c_void_p, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int)]),
@@ -118,6 +119,7 @@ _SIGS = [
     ("mfwq_batch_solve", ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                         ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfoC)]),
     ("mfwq_selftest_bounded_wait", ctypes.c_int, [ctypes.c_longlong, ctypes.c_void_p]),
+    ("mfwq_probe_fma_rate", ctypes.c_int, [ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)]),
     ("mfwq_fd_precond_noalloc", ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_void_p),
                                                ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
@@ -145,6 +147,14 @@ def fd_precond_noalloc(n, U, UT, lam, r, z, stream=None):
         _check(lib().mfwq_fd_precond_noalloc(nn, Up, UTp, Lp, _ptr(r, torch.float64, N, dev),
                                              _ptr(z, torch.float64, N, dev), ctypes.c_void_p(s.cuda_stream)))
     return z
+
+
+def probe_fma_rate(fp64: bool = True, stream=None) -> float:
+    """Measured FMA throughput of the current device in TFLOP/s (mfwq_probe_fma_rate)."""
+    v = ctypes.c_double()
+    _check(lib().mfwq_probe_fma_rate(1 if fp64 else 0, ctypes.c_void_p(stream.cuda_stream) if stream is not None else None,
+                                     ctypes.byref(v)))
+    return v.value
 
 
 def kernel_launches() -> int:
@@ -362,9 +372,10 @@ class Operator:
         _check(lib().fd_precond_f32(self._h, _ptr(r, torch.float32, self.N, self.device), _ptr(out, torch.float32, self.N, self.device)))
         return out
 
-    def _opts(self, rtol, maxit, inner_rtol, inner_maxit, x0, force_fp64, history, fp64_low_fd=False):
+    def _opts(self, rtol, maxit, inner_rtol, inner_maxit, x0, force_fp64, history, fp64_low_fd=False, graph_chunk=0):
         o = SolveOpts()
         o.fp64_low_fd = 1 if fp64_low_fd else 0
+        o.graph_chunk = int(graph_chunk)
         o.rtol = rtol
         o.maxit = maxit
         o.inner_rtol = inner_rtol
@@ -377,11 +388,12 @@ class Operator:
             o.res_hist = hist.ctypes.data_as(_c_dptr)
         return o, hist
 
-    def _solve(self, fn, f, u, rtol, maxit, inner_rtol, inner_maxit, force_fp64, history, check, fp64_low_fd=False):
+    def _solve(self, fn, f, u, rtol, maxit, inner_rtol, inner_maxit, force_fp64, history, check, fp64_low_fd=False,
+               graph_chunk=0):
         import torch
         x0 = u is not None
         u = u if u is not None else self._new(self.shape, torch.float64)
-        o, hist = self._opts(rtol, maxit, inner_rtol, inner_maxit, x0, force_fp64, history, fp64_low_fd)
+        o, hist = self._opts(rtol, maxit, inner_rtol, inner_maxit, x0, force_fp64, history, fp64_low_fd, graph_chunk)
         info = SolveInfoC()
         st = fn(self._h, _ptr(f, torch.float64, self.N, self.device), _ptr(u, torch.float64, self.N, self.device),
                 ctypes.byref(o), ctypes.byref(info))
@@ -394,13 +406,15 @@ class Operator:
         return u, SolveInfo(info.status, info.iterations, info.outer_iterations, info.rel_residual, h)
 
     def solve(self, f, u=None, rtol=1e-10, maxit=500, inner_rtol=0.0, inner_maxit=0, force_fp64=False,
-              history=False, check=False, fp64_low_fd=False):
+              history=False, check=False, fp64_low_fd=False, graph_chunk=0):
         """Solve K~ u = f (FP64 BiCGStab + FD, or mixed refinement on a mixed
         operator).  u, if given, is the initial guess and receives the result.
         fp64_low_fd (mixed operator): FP64 BiCGStab with the FD in the
-        operator's low precision (tensor cores); the tolerance is met in FP64."""
+        operator's low precision (tensor cores); the tolerance is met in FP64.
+        graph_chunk > 1: FP64 iterations captured that many to a CUDA graph
+        (needs an operator on a non-default stream)."""
         return self._solve(lib().mfwq_solve, f, u, rtol, maxit, inner_rtol, inner_maxit, force_fp64, history, check,
-                           fp64_low_fd)
+                           fp64_low_fd, graph_chunk)
 
     def solve_T(self, g, lam=None, rtol=1e-10, maxit=500, history=False, check=False, fp64_low_fd=False):
         """Solve the adjoint system K~^T lambda = g (FP64; fp64_low_fd as in solve)."""
@@ -456,6 +470,16 @@ class Operator:
     def profile(self, on: bool = True):
         """Bracket every later kernel launch with CUDA events (per-stage timing)."""
         _check(lib().mfwq_profile_enable(self._h, 1 if on else 0))
+
+    def profile_stages(self, names=None):
+        """Bracket only the named stages with events while profiling (None: all)."""
+        mask = (1 << 64) - 1
+        if names is not None:
+            idx = {lib().mfwq_stage_name(i).decode(): i for i in range(24)}
+            mask = 0
+            for n in names:
+                mask |= 1 << idx[n]
+        _check(lib().mfwq_profile_stage_mask(self._h, ctypes.c_ulonglong(mask)))
 
     def profile_read(self, reset: bool = True) -> dict:
         """{stage name: (device ms summed, launches)} since the last reset."""

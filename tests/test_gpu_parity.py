@@ -256,3 +256,23 @@ def test_autograd_function_gradient(mf):
         an = float((g * d).sum())
         assert abs(fd - an) <= 1e-5 * abs(an), (fd, an)
     c.op.close()
+
+
+def test_graph_chunk_solve_is_the_same_solve(mf):
+    """FP64 solve with BiCGStab iterations captured four at a time into a CUDA
+    graph (operator on a stream of its own): the same kernels in the same
+    order, so the same iterations and bits as the plain solve; a chunk larger
+    than maxit runs uncaptured, and maxit is honoured."""
+    p, nel = 3, (6, 7, 5)
+    knots = [inputs.open_uniform_knots(p, n) for n in nel]
+    s = torch.cuda.Stream()
+    op = mf.Operator(p, knots, device=DEV, stream=s)
+    op.set_coeff(op.eval_coeff("ring", inputs.fourier_modes(3), 0.3))
+    f = op.load_vector("ring", "sines")
+    u0, i0 = op.solve(f, rtol=1e-10)
+    u4, i4 = op.solve(f, rtol=1e-10, graph_chunk=4)
+    assert i0.converged and i4.converged and i4.iterations == i0.iterations
+    assert torch.equal(u0, u4)
+    u5, i5 = op.solve(f, rtol=1e-14, maxit=5, graph_chunk=4)
+    assert i5.iterations == 5 and i5.status == -6
+    op.close()
