@@ -66,6 +66,8 @@ def parse():
                     help="run the k-refinement experiment of Section 4 (Table 1) for the given comma-separated "
                          "elements per direction (e.g. 16,32,64,128,256), p = 2..10, and print its table as JSON")
     ap.add_argument("--table1-p", default="2,3,4,5,6,7,8,9,10", help="degrees for --table1")
+    ap.add_argument("--fp32-path", choices=["staged", "fused"], default=None,
+                    help="with --kernel-run apply32: force the FP32 kernel sequence")
     ap.add_argument("--kernel-run", choices=["apply", "apply_T", "grad", "fd64", "fdtc", "fdbf16", "apply32", "mixed_solve"],
                     default=None,
                     help="set up the workload, run one operator 3 times and exit (target for ncu captures)")
@@ -822,7 +824,7 @@ def run_ours(args):
     return 0
 
 
-def kernel_run(which, nel_override=None):
+def kernel_run(which, nel_override=None, fp32_path=None):
     """Setup + three launches of one operator on the bench workload (the
     p = 6, 192-element ring for the mixed-precision operators), or on the
     same degree with the elements per direction given (a smaller case with
@@ -841,6 +843,8 @@ def kernel_run(which, nel_override=None):
             raise SystemExit("--kernel-nel takes one value or three (per direction)")
         nel = vals[0] if len(vals) == 1 else vals
     op, _ = make_op(mf, p, nel, mixed=mixed, fd="bf16" if which == "fdbf16" else "tf32", device=dev)
+    if fp32_path:
+        op.fp32_path = fp32_path
     if which == "mixed_solve":  # one warm-up and one measured mixed-precision solve to 1e-8
         f = op.load_vector("ring", "sines")
         for _ in range(2):
@@ -927,7 +931,7 @@ def main():
     if args.table1:
         return table1(args)
     if args.kernel_run:
-        return kernel_run(args.kernel_run, args.kernel_nel)
+        return kernel_run(args.kernel_run, args.kernel_nel, args.fp32_path)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
