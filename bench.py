@@ -66,6 +66,7 @@ def parse():
                     help="run the k-refinement experiment of Section 4 (Table 1) for the given comma-separated "
                          "elements per direction (e.g. 16,32,64,128,256), p = 2..10, and print its table as JSON")
     ap.add_argument("--table1-p", default="2,3,4,5,6,7,8,9,10", help="degrees for --table1")
+    ap.add_argument("--kernel-p", type=int, default=None, help="with --kernel-run: degree (default: the workload's)")
     ap.add_argument("--fp32-path", choices=["staged", "fused"], default=None,
                     help="with --kernel-run apply32: force the FP32 kernel sequence")
     ap.add_argument("--kernel-run", choices=["apply", "apply_T", "grad", "fd64", "fdtc", "fdbf16", "apply32", "mixed_solve"],
@@ -824,7 +825,7 @@ def run_ours(args):
     return 0
 
 
-def kernel_run(which, nel_override=None, fp32_path=None):
+def kernel_run(which, nel_override=None, fp32_path=None, p_override=None):
     """Setup + three launches of one operator on the bench workload (the
     p = 6, 192-element ring for the mixed-precision operators), or on the
     same degree with the elements per direction given (a smaller case with
@@ -837,6 +838,8 @@ def kernel_run(which, nel_override=None, fp32_path=None):
     dev = torch.device("cuda", 0)
     mixed = which in ("fdtc", "fdbf16", "apply32", "mixed_solve")
     p, nel = (MIXED["p"], MIXED["nel"]) if mixed else (WORKLOAD["p"], WORKLOAD["nel"])
+    if p_override:
+        p = p_override
     if nel_override:
         vals = tuple(int(v) for v in nel_override.split(","))
         if len(vals) not in (1, 3):
@@ -931,7 +934,7 @@ def main():
     if args.table1:
         return table1(args)
     if args.kernel_run:
-        return kernel_run(args.kernel_run, args.kernel_nel, args.fp32_path)
+        return kernel_run(args.kernel_run, args.kernel_nel, args.fp32_path, args.kernel_p)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
