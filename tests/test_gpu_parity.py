@@ -130,12 +130,18 @@ def test_load_vector(case):
     assert _rel_max(f, ref) <= 1e-13, _rel_max(f, ref)
 
 
+# Cases whose WQ matrix is so ill-conditioned that a relative residual of 1e-10
+# bounds the solution error only to kappa_2 * 1e-10 > 1e-9 (kappa_2 measured by
+# a dense SVD of the oracle's K~): there the 1e-10 solve must be as close to the
+# direct solve as the oracle's own BiCGStab gets.  Every other case: 1e-9 flat.
+WIDE_SOLVE_BOUND = {"ring-p6": 1.94e7}
+
+
 def test_solve_matches_direct(case):
     """At rtol 1e-12 the solution is within 1e-9 of a direct sparse solve; at
-    rtol 1e-10 it is as close as the oracle's own BiCGStab gets at that
-    tolerance (the WQ matrix of a small high-degree patch has condition
-    numbers up to 1e7, so a 1e-10 residual bounds the error only to
-    kappa * 1e-10), and its true residual, measured by the oracle, is 1e-10."""
+    rtol 1e-10 too, except in the ill-conditioned cases listed above, where it
+    is as close as the oracle's own BiCGStab gets at that tolerance; its true
+    residual, measured by the oracle, is 1e-10."""
     import scipy.sparse.linalg as spla
     K = O.stiffness_wq(case.tabs, O.full_coeff(case.C6)).tocsc()
     F = O.load_vector(case.tabs, case.geom, O.forcing_sines)
@@ -148,7 +154,10 @@ def test_solve_matches_direct(case):
     assert info.rel_residual <= 1e-10
     un = u.cpu().numpy()
     err = np.linalg.norm(un - ref) / np.linalg.norm(ref)
-    assert err <= max(SOLVE_TOL, 5 * err_or), (err, err_or)
+    if case.name in WIDE_SOLVE_BOUND:
+        assert err <= max(SOLVE_TOL, 5 * err_or), (err, err_or)
+    else:
+        assert err <= SOLVE_TOL, (case.name, err, err_or)
     res = np.linalg.norm(F.ravel() - K @ un.ravel()) / np.linalg.norm(F)
     assert res <= 2e-10, res
     assert info.history is not None and abs(info.history[-1] - info.rel_residual) <= 1e-12 + 1e-6 * info.rel_residual
