@@ -223,6 +223,37 @@ int fd_precond_f32(mfwq_handle h, const float* r_dev, float* z_dev);
 int mfwq_set_fp32_path(mfwq_handle h, int path);
 int mfwq_fp32_path(mfwq_handle h);
 
+/* Kernels of the FP64 FD preconditioner (fd_precond and the FP64 solves):
+ *  MFWQ_FD64_PIPE: the mode products in FP64 on the FP64 pipe (even/odd
+ *    split where the knot vectors are symmetric); the default;
+ *  MFWQ_FD64_SPLIT: the mode products on the BF16 tensor cores, every FP64
+ *    operand split into 8 integer slices of 7 bits under a power-of-two scale
+ *    per row (Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012); the
+ *    slice products accumulate exactly, and the result keeps 56 bits below
+ *    each row's leading power of two, so it agrees with the FP64 products to
+ *    about 2^-55 of sum |U_ij| |x_j|.  Needs every n_l <= 256; the first
+ *    selection slices the mode matrices and allocates N doubles for the
+ *    eigenvalue scaling (synchronous).
+ * mfwq_set_fd64_path returns MFWQ_EINVAL for an unknown path or sizes above
+ * 256; mfwq_fd64_path returns the path in use. */
+#define MFWQ_FD64_PIPE 0
+#define MFWQ_FD64_SPLIT 1
+int mfwq_set_fd64_path(mfwq_handle h, int path);
+int mfwq_fd64_path(mfwq_handle h);
+
+/* Thread tiling of the four slow-dimension stages (the z and y contractions
+ * of Algorithm 2): each thread computes `rows` consecutive output rows (1, 2
+ * or 4) of `cols` consecutive columns (1, 2 or 4; FP32 forward stages only,
+ * loaded and stored as one 8- or 16-byte vector; a stage whose column count
+ * or buffers are not aligned to it runs one column per thread).  fp32 = 0
+ * sets the FP64 operator (cols must be 1), 1 the FP32 operator of a mixed
+ * handle.  Every output is summed in the same order under every tiling, so
+ * the results are bitwise the same; mfwq_autotune sets both by timing.
+ * Returns MFWQ_EINVAL for other values; launches no work.  mfwq_slow_tiling
+ * writes the tiling in use to *rows and *cols. */
+int mfwq_set_slow_tiling(mfwq_handle h, int fp32, int rows, int cols);
+int mfwq_slow_tiling(mfwq_handle h, int fp32, int* rows, int* cols);
+
 typedef struct {
     double rtol;           /* stop when ||f - K~ u||_2 <= rtol ||f||_2 */
     int maxit;             /* BiCGStab iterations (outer refinement steps when mixed) */
@@ -333,7 +364,8 @@ int mfwq_fd_precond_noalloc(const int n[3], const double* const U_dev[3], const 
  * shared-memory carveout), then 1, 2 or 4 output rows per thread in the other
  * four stages, and for the FP32 operator the fused kernel sequence
  * (MFWQ_PATH_FUSED, where available) against the best staged one (cached
- * codes add 10000 when the fused one won).  *xlines_out (may be NULL) receives the FP64 choice as
+ * codes add 10000 when the fused one won) and 1, 2 or 4 columns per thread
+ * in its slow stages (cached codes add 100000 times the columns).  *xlines_out (may be NULL) receives the FP64 choice as
  * 1000 * carveout + 100 * rows + 10 * mapping + lines.  cache_path (may be
  * NULL) is a file of JSON lines {"key": "...", "xstage": that code}: a hit
  * skips the timing, a miss appends the result (codes below 100 mean one row
@@ -409,7 +441,8 @@ int mfwq_probe_fma_rate(int fp64, void* stream, double* tflops);
  * fd_dim23, fd_tc (FD mode products), krylov (BiCGStab vector and scalar
  * kernels), setup, fd_fold (even/odd folding of the FP64 FD), mass (the
  * reaction-term passes), h1_error (mfwq_h1_error), fused_xy (the fused FP32
- * trial-y / x / test-y kernel). */
+ * trial-y / x / test-y kernel), fd_oz (FP64 FD mode products on the tensor
+ * cores by operand splitting). */
 #define MFWQ_NSTAGES 24
 typedef struct {
     double ms[MFWQ_NSTAGES];           /* summed device time per stage (CUDA events) */

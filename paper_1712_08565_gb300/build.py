@@ -12,7 +12,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmfwq.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["setup_host.cpp", "apply_kernels.cu", "xstage_kernels.cu", "fd_kernels.cu", "fd_tc.cu", "krylov.cu", "capi.cu", "prof.cu", "fd_noalloc.cu", "selftest.cu", "fused_apply.cu", "probe.cu"]
+SOURCES = ["setup_host.cpp", "apply_kernels.cu", "xstage_kernels.cu", "fd_kernels.cu", "fd_tc.cu", "krylov.cu", "capi.cu", "prof.cu", "fd_noalloc.cu", "selftest.cu", "fused_apply.cu", "probe.cu", "fd_oz.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I", INCLUDE]
 

@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <cstdint>
 #include <type_traits>
 #include <vector>
 
@@ -46,6 +47,109 @@ namespace {
 struct SlowGeom {
     int A, Rin, Rout, C;
 };
+
+// VW = 2 or 4 consecutive FP32 values (one 8- or 16-byte aligned vector) as
+// VW / 2 pairs.
+template <int VW>
+__device__ __forceinline__ void ld_pairs(const float* __restrict__ p, float2* v) {
+    if constexpr (VW == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4*>(p));
+        v[0] = make_float2(t.x, t.y);
+        v[1] = make_float2(t.z, t.w);
+    } else {
+        v[0] = __ldg(reinterpret_cast<const float2*>(p));
+    }
+}
+template <int VW>
+__device__ __forceinline__ void st_pairs(float* __restrict__ p, const float2* v) {
+    if constexpr (VW == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    else *reinterpret_cast<float2*>(p) = v[0];
+}
+
+// The same stage with a thread owning VW = 2 or 4 consecutive columns (FP32,
+// C a multiple of VW): one vector load per input row and tensor, and the
+// columns taken in pairs by the packed FP32 FMA (Op::fma2, each of its two
+// FMAs rounded as by fmaf).  The band weights sit in shared memory as
+// (w, w) pairs.  Every output is summed in the same order as by the
+// one-column form, so the results are bitwise the same.
+template <class Op, int R, int VW>
+__device__ __forceinline__ void slow_body_vec(const Op& op, const SlowGeom& g, int bx, int by, int gx, float2* sb) {
+    constexpr int NF = Op::NF, NIN = Op::NIN, NACC = Op::NACC, VP = VW / 2;
+    const int r0 = by * R;
+    const int nr = min(R, g.Rout - r0);
+    const int W = op.band.width;
+    int s[R], len[R];
+    int lo = 0x7fffffff, hi = 0;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        s[k] = 0;
+        len[k] = 0;
+        if (k < nr) {
+            s[k] = op.band.start[r0 + k];
+            len[k] = op.band.len[r0 + k];
+            if (len[k] > 0) {
+                lo = min(lo, s[k]);
+                hi = max(hi, s[k] + len[k]);
+            }
+        }
+    }
+    for (int e = threadIdx.x; e < nr * W * NF; e += blockDim.x) {
+        const int k = e / (W * NF), rem = e - k * W * NF, t = rem / NF, f = rem - t * NF;
+        const float v = op.band.row(f, r0 + k)[t];
+        sb[e] = make_float2(v, v);
+    }
+    __syncthreads();
+    const size_t CV = (size_t)g.C / VW, ACV = (size_t)g.A * CV;
+    for (size_t e = (size_t)bx * blockDim.x + threadIdx.x; e < ACV; e += (size_t)gx * blockDim.x) {
+        const size_t a = e / CV, c = (e - a * CV) * VW;
+        float2 acc[R][VP][NACC];
+#pragma unroll
+        for (int k = 0; k < R; ++k)
+#pragma unroll
+            for (int v = 0; v < VP; ++v)
+#pragma unroll
+                for (int m = 0; m < NACC; ++m) acc[k][v][m] = make_float2(0.f, 0.f);
+        const size_t ib = a * g.Rin * (size_t)g.C + c;
+        for (int q = lo; q < hi; ++q) {
+            float2 x[VP][NIN];
+#pragma unroll
+            for (int i = 0; i < NIN; ++i) {
+                float2 t[VP];
+                ld_pairs<VW>(op.in_ptr(i) + ib + (size_t)q * g.C, t);
+#pragma unroll
+                for (int v = 0; v < VP; ++v) x[v][i] = t[v];
+            }
+#pragma unroll
+            for (int k = 0; k < R; ++k) {
+                const int t = q - s[k];
+                if ((unsigned)t < (unsigned)len[k]) {
+                    const float2* w = sb + (k * W + t) * NF;
+#pragma unroll
+                    for (int v = 0; v < VP; ++v) op.fma2(w, x[v], acc[k][v]);
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if (k >= nr) continue;
+            const size_t o = (a * g.Rout + r0 + k) * (size_t)g.C + c;
+#pragma unroll
+            for (int m = 0; m < NACC; ++m) {
+                float2 t[VP];
+#pragma unroll
+                for (int v = 0; v < VP; ++v) t[v] = acc[k][v][m];
+                st_pairs<VW>(op.out_ptr(m) + o, t);
+            }
+        }
+    }
+}
+
+template <class Op, int R, int VW>
+__global__ void __launch_bounds__(kThreads) k_slow_vec(Op op, SlowGeom g, const int* skip) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char slow_smem[];
+    slow_body_vec<Op, R, VW>(op, g, blockIdx.x, blockIdx.y, gridDim.x, reinterpret_cast<float2*>(slow_smem));
+}
 
 // One block (bx, by) of gx column blocks; sb: the block's band rows.
 template <class Op, int R>
@@ -139,10 +243,17 @@ struct OpTrialZ {  // Z0 = B0 v, Z1 = B1 v
         u[0] = fmaT(w[0], x[0], u[0]);
         u[1] = fmaT(w[1], x[0], u[1]);
     }
+    __device__ void fma2(const float2* w, const float2* x, float2* u) const {
+        u[0] = __ffma2_rn(w[0], x[0], u[0]);
+        u[1] = __ffma2_rn(w[1], x[0], u[1]);
+    }
     __device__ void store(size_t o, const T* u) const {
         z0[o] = u[0];
         z1[o] = u[1];
     }
+    static constexpr bool kVec = true;
+    __host__ __device__ const T* in_ptr(int) const { return v; }
+    __host__ __device__ T* out_ptr(int m) const { return m == 0 ? z0 : z1; }
 };
 
 template <typename T>
@@ -164,11 +275,19 @@ struct OpTrialY {  // Y00 = B0 Z0, Y10 = B1 Z0, Y01 = B0 Z1
         u[1] = fmaT(w[1], x[0], u[1]);
         u[2] = fmaT(w[0], x[1], u[2]);
     }
+    __device__ void fma2(const float2* w, const float2* x, float2* u) const {
+        u[0] = __ffma2_rn(w[0], x[0], u[0]);
+        u[1] = __ffma2_rn(w[1], x[0], u[1]);
+        u[2] = __ffma2_rn(w[0], x[1], u[2]);
+    }
     __device__ void store(size_t o, const T* u) const {
         y00[o] = u[0];
         y10[o] = u[1];
         y01[o] = u[2];
     }
+    static constexpr bool kVec = true;
+    __host__ __device__ const T* in_ptr(int k) const { return k == 0 ? z0 : z1; }
+    __host__ __device__ T* out_ptr(int m) const { return m == 0 ? y00 : (m == 1 ? y10 : y01); }
 };
 
 template <typename T>
@@ -198,10 +317,24 @@ struct OpTestY {  // 9 x-contracted tensors -> 4 z-groups through W2
         // z-family (1,1): pair 33 (y 00)
         u[3] = fmaT(f00, x[8], u[3]);
     }
+    __device__ void fma2(const float2* w, const float2* x, float2* u) const {  // fma on column pairs
+        u[0] = __ffma2_rn(w[0], x[0], u[0]);
+        u[0] = __ffma2_rn(w[1], x[1], u[0]);
+        u[0] = __ffma2_rn(w[2], x[3], u[0]);
+        u[0] = __ffma2_rn(w[3], x[4], u[0]);
+        u[1] = __ffma2_rn(w[0], x[2], u[1]);
+        u[1] = __ffma2_rn(w[2], x[5], u[1]);
+        u[2] = __ffma2_rn(w[0], x[6], u[2]);
+        u[2] = __ffma2_rn(w[1], x[7], u[2]);
+        u[3] = __ffma2_rn(w[0], x[8], u[3]);
+    }
     __device__ void store(size_t o, const T* u) const {
 #pragma unroll
         for (int f = 0; f < 4; ++f) out[f][o] = u[f];
     }
+    static constexpr bool kVec = true;
+    __host__ __device__ const T* in_ptr(int k) const { return in[k]; }
+    __host__ __device__ T* out_ptr(int m) const { return out[m]; }
 };
 
 template <typename T>
@@ -221,7 +354,16 @@ struct OpTestZ {  // w = sum_f W3^f U_f
         u[0] = fmaT(w[2], x[2], u[0]);
         u[0] = fmaT(w[3], x[3], u[0]);
     }
+    __device__ void fma2(const float2* w, const float2* x, float2* u) const {
+        u[0] = __ffma2_rn(w[0], x[0], u[0]);
+        u[0] = __ffma2_rn(w[1], x[1], u[0]);
+        u[0] = __ffma2_rn(w[2], x[2], u[0]);
+        u[0] = __ffma2_rn(w[3], x[3], u[0]);
+    }
     __device__ void store(size_t o, const T* u) const { out[o] = u[0]; }
+    static constexpr bool kVec = true;
+    __host__ __device__ const T* in_ptr(int k) const { return in[k]; }
+    __host__ __device__ T* out_ptr(int) const { return out; }
 };
 
 // ---- transposed stages
@@ -342,9 +484,14 @@ constexpr int slow_kind() {
     else return GK_NONE;
 }
 
+template <class Op, class = void>
+struct HasVec : std::false_type {};
+template <class Op>
+struct HasVec<Op, std::void_t<decltype(Op::kVec)>> : std::true_type {};
+
 template <class Op>
 cudaError_t launch_slow(int tag, const Op& op, int A, int Rin, int Rout, int C, const int* skip, cudaStream_t s,
-                        int rows = 1) {
+                        int rows = 1, int vw = 1) {
     SlowGeom g{A, Rin, Rout, C};
     if (g_rec) {  // recorded with one row per thread (the rows per thread do not change any sum)
         constexpr int kind = slow_kind<Op>();
@@ -360,6 +507,30 @@ cudaError_t launch_slow(int tag, const Op& op, int A, int Rin, int Rout, int C, 
         return cudaSuccess;
     }
     const int R = rows == 2 || rows == 4 ? rows : 1;
+    if constexpr (sizeof(typename Op::Elem) == 4 && HasVec<Op>::value) {
+        bool aligned = (vw == 2 || vw == 4) && C % vw == 0;
+        for (int i = 0; aligned && i < Op::NIN; ++i) aligned = (reinterpret_cast<uintptr_t>(op.in_ptr(i)) % (4 * vw)) == 0;
+        for (int m = 0; aligned && m < Op::NACC; ++m) aligned = (reinterpret_cast<uintptr_t>(op.out_ptr(m)) % (4 * vw)) == 0;
+        if (aligned) {  // VW columns per thread, vector loads and stores
+            const size_t ACV = (size_t)A * C / vw;
+            unsigned bx = (unsigned)((ACV + kThreads - 1) / kThreads);
+            if (bx > 65535u) bx = 65535u;
+            dim3 grid(bx, (Rout + R - 1) / R);
+            const size_t sm = sizeof(float2) * (size_t)R * op.band.width * Op::NF;
+            launch_begin(tag, s);
+            if (vw == 4) {
+                if (R == 4) k_slow_vec<Op, 4, 4><<<grid, kThreads, sm, s>>>(op, g, skip);
+                else if (R == 2) k_slow_vec<Op, 2, 4><<<grid, kThreads, sm, s>>>(op, g, skip);
+                else k_slow_vec<Op, 1, 4><<<grid, kThreads, sm, s>>>(op, g, skip);
+            } else {
+                if (R == 4) k_slow_vec<Op, 4, 2><<<grid, kThreads, sm, s>>>(op, g, skip);
+                else if (R == 2) k_slow_vec<Op, 2, 2><<<grid, kThreads, sm, s>>>(op, g, skip);
+                else k_slow_vec<Op, 1, 2><<<grid, kThreads, sm, s>>>(op, g, skip);
+            }
+            launch_end(tag, s);
+            return cudaGetLastError();
+        }
+    }
     size_t AC = (size_t)A * C;
     unsigned bx = (unsigned)((AC + kThreads - 1) / kThreads);
     if (bx > 65535u) bx = 65535u;
@@ -818,7 +989,7 @@ int run_apply(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
     cudaError_t e;
     // trial z
     OpTrialZ<T> oz{d3.B, x, Z0, Z1};
-    if ((e = launch_slow(S_TRIAL_Z, oz, 1, n3, q3, n2 * n1, skip, c.stream, c.srows)) != cudaSuccess) return MFWQ_ECUDA;
+    if ((e = launch_slow(S_TRIAL_Z, oz, 1, n3, q3, n2 * n1, skip, c.stream, c.srows, c.svec)) != cudaSuccess) return MFWQ_ECUDA;
     if constexpr (sizeof(T) == 4) {
         if (c.fused && c.fused->ok && !c.cm) {
             // trial y, x stage and test y in one kernel; U in the (unused) P region
@@ -827,13 +998,14 @@ int run_apply(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
             otz.band = d3.W;
             for (int f = 0; f < 4; ++f) otz.in[f] = P + f * SQ;
             otz.out = y;
-            if (launch_slow(S_TEST_Z, otz, 1, q3, n3, n2 * n1, skip, c.stream, c.srows) != cudaSuccess) return MFWQ_ECUDA;
+            if (launch_slow(S_TEST_Z, otz, 1, q3, n3, n2 * n1, skip, c.stream, c.srows, c.svec) != cudaSuccess)
+                return MFWQ_ECUDA;
             return MFWQ_OK;
         }
     }
     // trial y
     OpTrialY<T> oy{d2.B, Z0, Z1, Y[0], Y[1], Y[2]};
-    if ((e = launch_slow(S_TRIAL_Y, oy, q3, n2, q2, n1, skip, c.stream, c.srows)) != cudaSuccess) return MFWQ_ECUDA;
+    if ((e = launch_slow(S_TRIAL_Y, oy, q3, n2, q2, n1, skip, c.stream, c.srows, c.svec)) != cudaSuccess) return MFWQ_ECUDA;
     // x stage (lines per block and work mapping chosen by the autotuner)
     {
         XArgs<T> a = xargs(d1, q3 * q2, c.cs, c.C);
@@ -857,13 +1029,13 @@ int run_apply(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
     oty.band = d2.W;
     for (int k = 0; k < 9; ++k) oty.in[k] = Tt[k];
     for (int f = 0; f < 4; ++f) oty.out[f] = Q + f * SQ;
-    if ((e = launch_slow(S_TEST_Y, oty, q3, q2, n2, n1, skip, c.stream, c.srows)) != cudaSuccess) return MFWQ_ECUDA;
+    if ((e = launch_slow(S_TEST_Y, oty, q3, q2, n2, n1, skip, c.stream, c.srows, c.svec)) != cudaSuccess) return MFWQ_ECUDA;
     // test z
     OpTestZ<T> otz;
     otz.band = d3.W;
     for (int f = 0; f < 4; ++f) otz.in[f] = Q + f * SQ;
     otz.out = y;
-    if ((e = launch_slow(S_TEST_Z, otz, 1, q3, n3, n2 * n1, skip, c.stream, c.srows)) != cudaSuccess) return MFWQ_ECUDA;
+    if ((e = launch_slow(S_TEST_Z, otz, 1, q3, n3, n2 * n1, skip, c.stream, c.srows, c.svec)) != cudaSuccess) return MFWQ_ECUDA;
     return MFWQ_OK;
 }
 

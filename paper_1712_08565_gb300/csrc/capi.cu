@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "fd_oz.h"
 #include "fused_apply.h"
 #include "grouped.h"
 #include "kernels.h"
@@ -283,12 +284,15 @@ struct mfwq_handle_s {
     int xmode = 0;                   // FP64 x-stage work mapping (autotuned)
     int xlines32 = 4, xmode32 = 1;   // the same for the FP32 operator
     int srows = 1, srows32 = 1;      // slow-dimension output rows per thread (autotuned)
+    int svec32 = 1;                  // FP32 slow-dimension columns per thread (autotuned)
     int xcarve = 0, xcarve32 = 0;    // x stage with the reduced shared-memory carveout (autotuned)
     KScal* dsc = nullptr;
     KScal* hsc = nullptr;    // pinned
     Profiler prof;
     double* hnorm = nullptr; // pinned, 2 doubles
     double* host_io = nullptr;  // device f/u buffers of mfwq_solve_host (2 N), lazily
+    OzPlan oz;                  // FP64 FD on the tensor cores by operand splitting (built on request)
+    int fd64_path = MFWQ_FD64_PIPE;
     FusedPlan fplan;            // fused FP32 apply (mixed handles with a stencil direction 1)
     int fused32 = 0;            // 1: the FP32 apply runs the fused kernel
     int onthefly = 0;           // 1: the FP32 operator evaluates C in its x stage (C32 freed)
@@ -327,11 +331,26 @@ OpCtx<float> ctx32(mfwq_handle h) {
     c.xlines = h->xlines32;
     c.xmode = h->xmode32;
     c.srows = h->srows32;
+    c.svec = h->svec32;
     c.xcarve = h->xcarve32;
     c.cm = h->Cm32;
     c.fused = h->fused32 && h->fplan.ok ? &h->fplan : nullptr;
     c.cf = h->onthefly ? &h->cf32 : nullptr;
     return c;
+}
+
+// The FP64 FD preconditioner of the handle's FP64 path on stream s.
+LinOp<double> fd64_linop(mfwq_handle h, cudaStream_t s) {
+    double* tmp = h->fd_tmp64;
+    if (h->fd64_path == MFWQ_FD64_SPLIT && h->oz.ok) {
+        const OzPlan* p = &h->oz;
+        int* err = h->derr;
+        return [p, tmp, err, s](const double* in, double* out, const int* skip) {
+            return run_fd_oz(*p, in, out, tmp, err, skip, s);
+        };
+    }
+    DirD<double> d[3] = {h->d64[0], h->d64[1], h->d64[2]};
+    return [d, tmp, s](const double* in, double* out, const int* skip) { return run_fd64(d, in, out, tmp, skip, s); };
 }
 
 void free_handle(mfwq_handle h) {
@@ -352,6 +371,7 @@ void free_handle(mfwq_handle h) {
     cudaFree(h->dsc);
     cudaFree(h->host_io);
     fused_plan_free(h->fplan);
+    oz_plan_free(h->oz);
     cudaFree(h->cf_tab);
     if (h->hsc) cudaFreeHost(h->hsc);
     if (h->hnorm) cudaFreeHost(h->hnorm);
@@ -563,10 +583,8 @@ int solve64(mfwq_handle h, const double* f, double* u, const mfwq_solve_opts& o,
     LinOp<double> A = [c, transpose](const double* in, double* out, const int* skip) {
         return transpose ? run_apply_T<double>(c, in, out, skip) : run_apply<double>(c, in, out, skip);
     };
-    DirD<double> d[3] = {h->d64[0], h->d64[1], h->d64[2]};
-    double* tmp = h->fd_tmp64;
     cudaStream_t s = h->stream;
-    LinOp<double> P = [d, tmp, s](const double* in, double* out, const int* skip) { return run_fd64(d, in, out, tmp, skip, s); };
+    LinOp<double> P = fd64_linop(h, s);
     if (o.fp64_low_fd) {
         // the FD in the handle's low precision: FP32 copies in the mixed refinement's
         // work vectors (unused by an FP64 solve), tensor-core mode products
@@ -866,6 +884,10 @@ int upload_fd_shift(mfwq_handle h, double shift) {
         CU(cudaMemcpy(const_cast<double*>(h->d64[2].lam_split), ls.data(), sizeof(double) * ls.size(),
                       cudaMemcpyHostToDevice));
     }
+    if (h->oz.ok) {
+        ST(oz_update_dinv(h->d64, h->oz, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+    }
     return MFWQ_OK;
 }
 }  // namespace
@@ -946,6 +968,8 @@ int mfwq_apply_f32(mfwq_handle h, const float* x_dev, float* y_dev) {
 int fd_precond(mfwq_handle h, const double* r_dev, double* z_dev) {
     ProfScope _ps(h ? &h->prof : nullptr);
     if (!h || !r_dev || !z_dev || r_dev == z_dev) return fail(MFWQ_EINVAL, "bad argument");
+    if (h->fd64_path == MFWQ_FD64_SPLIT && h->oz.ok)
+        return run_fd_oz(h->oz, r_dev, z_dev, h->fd_tmp64, h->derr, nullptr, h->stream);
     return run_fd64(h->d64, r_dev, z_dev, h->fd_tmp64, nullptr, h->stream);
 }
 
@@ -997,7 +1021,7 @@ int mfwq_grad_coeff(mfwq_handle h, const double* lambda_dev, const double* u_dev
 
 static const char* kStageNames[S_NTAGS] = {
     "trial_z", "trial_y", "xstage", "test_y", "test_z", "test_zT", "test_yT", "xstage_T", "trial_yT", "trial_zT",
-    "xstage_grad", "fd_dim1", "fd_dim23", "fd_tc", "krylov", "setup", "fd_fold", "mass", "h1_error", "fused_xy"};
+    "xstage_grad", "fd_dim1", "fd_dim23", "fd_tc", "krylov", "setup", "fd_fold", "mass", "h1_error", "fused_xy", "fd_oz"};
 
 const char* mfwq_stage_name(int stage) { return stage >= 0 && stage < S_NTAGS ? kStageNames[stage] : ""; }
 
@@ -1044,6 +1068,51 @@ int mfwq_set_fp32_path(mfwq_handle h, int path) {
 int mfwq_fp32_path(mfwq_handle h) {
     if (!h) return fail(MFWQ_EINVAL, "NULL handle");
     return h->fused32 && h->fplan.ok ? MFWQ_PATH_FUSED : MFWQ_PATH_STAGED;
+}
+
+int mfwq_set_fd64_path(mfwq_handle h, int path) {
+    if (!h) return fail(MFWQ_EINVAL, "NULL handle");
+    if (path != MFWQ_FD64_PIPE && path != MFWQ_FD64_SPLIT) return fail(MFWQ_EINVAL, "unknown FP64 FD path");
+    if (path == MFWQ_FD64_SPLIT && !h->oz.ok) {
+        for (int l = 0; l < 3; ++l)
+            if (h->n[l] > kOzMaxN) return fail(MFWQ_EINVAL, "the split FP64 FD needs at most 256 DoFs per direction");
+        static bool configured = false;
+        if (!configured) {
+            ST(configure_fd_oz());
+            configured = true;
+        }
+        CU(cudaStreamSynchronize(h->stream));
+        ST(oz_plan_build(h->dir, h->d64, h->stream, h->oz));
+        CU(cudaStreamSynchronize(h->stream));
+    }
+    h->fd64_path = path;
+    return MFWQ_OK;
+}
+
+int mfwq_fd64_path(mfwq_handle h) {
+    if (!h) return fail(MFWQ_EINVAL, "NULL handle");
+    return h->fd64_path == MFWQ_FD64_SPLIT && h->oz.ok ? MFWQ_FD64_SPLIT : MFWQ_FD64_PIPE;
+}
+
+int mfwq_set_slow_tiling(mfwq_handle h, int fp32, int rows, int cols) {
+    if (!h) return fail(MFWQ_EINVAL, "NULL handle");
+    if (fp32 && !h->mixed) return fail(MFWQ_EINVAL, "set_slow_tiling: the handle has no FP32 operator");
+    if ((rows != 1 && rows != 2 && rows != 4) || (cols != 1 && cols != 2 && cols != 4) || (!fp32 && cols != 1))
+        return fail(MFWQ_EINVAL, "set_slow_tiling: rows 1, 2 or 4; cols 1, 2 or 4 (FP32 only)");
+    if (fp32) {
+        h->srows32 = rows;
+        h->svec32 = cols;
+    } else {
+        h->srows = rows;
+    }
+    return MFWQ_OK;
+}
+
+int mfwq_slow_tiling(mfwq_handle h, int fp32, int* rows, int* cols) {
+    if (!h || !rows || !cols) return fail(MFWQ_EINVAL, "NULL argument");
+    *rows = fp32 ? h->srows32 : h->srows;
+    *cols = fp32 ? h->svec32 : 1;
+    return MFWQ_OK;
 }
 
 int mfwq_sync(mfwq_handle h) {
@@ -1156,15 +1225,24 @@ int tune_xstage(mfwq_handle h, bool f32, int* err) {
     c.xlines = best_L;
     c.xmode = best_mode;
     c.xcarve = best_carve;
-    for (int R : {2, 4}) {
-        if (*err != MFWQ_OK) break;
-        c.srows = R;
-        const float ms = time_apply();
-        if (ms < best_ms) {
-            best_ms = ms;
-            best_R = R;
+    // the slow stages: rows per thread, and for FP32 columns per thread
+    int best_V = 1;
+    c.svec = 1;
+    for (int V : {1, 2, 4}) {
+        if (V > 1 && !f32) break;
+        for (int R : {1, 2, 4}) {
+            if (*err != MFWQ_OK || (V == 1 && R == 1)) continue;
+            c.srows = R;
+            c.svec = V;
+            const float ms = time_apply();
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_R = R;
+                best_V = V;
+            }
         }
     }
+    c.svec = best_V;
     // FP32: the fused trial-y / x / test-y kernel against the staged kernels
     int best_fused = 0;
     if (f32 && h->fplan.ok && !h->Cm32 && *err == MFWQ_OK) {
@@ -1180,7 +1258,7 @@ int tune_xstage(mfwq_handle h, bool f32, int* err) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (cudaGetLastError() != cudaSuccess) *err = MFWQ_ECUDA;
-    return 10000 * best_fused + 1000 * best_carve + 100 * best_R + 10 * best_mode + best_L;
+    return 100000 * best_V + 10000 * best_fused + 1000 * best_carve + 100 * best_R + 10 * best_mode + best_L;
 }
 }  // namespace
 
@@ -1198,6 +1276,8 @@ extern "C" int mfwq_autotune(mfwq_handle h, const char* cache_path, int* xlines_
         }
         int L = code % 10, mode = (code / 10) % 10, R = (code / 100) % 10, carve = (code / 1000) % 10 ? 1 : 0;
         const int fused = (code / 10000) % 10 ? 1 : 0;
+        int V = (code / 100000) % 10;
+        if (V != 2 && V != 4) V = 1;
         if (mode < 4 && L > h->max_xlines) L = h->max_xlines;
         if (R != 2 && R != 4) R = 1;
         if (prec) {
@@ -1205,6 +1285,7 @@ extern "C" int mfwq_autotune(mfwq_handle h, const char* cache_path, int* xlines_
             h->xlines32 = L;
             h->xmode32 = mode;
             h->srows32 = R;
+            h->svec32 = V;
             h->xcarve32 = carve;
         } else {
             h->xlines = L;
@@ -1250,11 +1331,9 @@ struct PatchOps {
 PatchOps patch_ops(mfwq_handle h, cudaStream_t s) {
     OpCtx<double> c = ctx64(h);
     c.stream = s;
-    DirD<double> d[3] = {h->d64[0], h->d64[1], h->d64[2]};
-    double* tmp = h->fd_tmp64;
     PatchOps o;
     o.A = [c](const double* in, double* out, const int* skip) { return run_apply<double>(c, in, out, skip); };
-    o.P = [d, tmp, s](const double* in, double* out, const int* skip) { return run_fd64(d, in, out, tmp, skip, s); };
+    o.P = fd64_linop(h, s);
     return o;
 }
 }  // namespace

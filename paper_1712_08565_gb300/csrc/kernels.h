@@ -49,6 +49,7 @@ struct OpCtx {
                        // 4 and 5 two-row tiles over 4 or 8 lines (8 lines per block)
     int xcarve = 0;    // 1: forward x stage with the reduced shared-memory carveout (larger L1)
     int srows = 1;     // output rows per thread of the slow-dimension stages: 1, 2 or 4
+    int svec = 1;      // FP32 forward slow stages: columns per thread (1, 2 or 4; vector loads and stores)
     int* err = nullptr;  // device error word: set when a bounded wait times out
     const T* cm = nullptr;  // reaction coefficient c = alpha det J at the WQ points [Nq], or none
     const FusedPlan* fused = nullptr;  // FP32: plan of the fused apply (used when ok and no reaction term)

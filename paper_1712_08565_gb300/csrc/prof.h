@@ -11,7 +11,7 @@ namespace mfwq {
 enum StageTag {
     S_TRIAL_Z = 0, S_TRIAL_Y, S_XSTAGE, S_TEST_Y, S_TEST_Z,
     S_TEST_ZT, S_TEST_YT, S_XSTAGE_T, S_TRIAL_YT, S_TRIAL_ZT, S_XSTAGE_GRAD,
-    S_FD_DIM1, S_FD_DIM23, S_FD_TC, S_KRYLOV, S_SETUP, S_FD_FOLD, S_MASS, S_H1, S_FUSED, S_NTAGS
+    S_FD_DIM1, S_FD_DIM23, S_FD_TC, S_KRYLOV, S_SETUP, S_FD_FOLD, S_MASS, S_H1, S_FUSED, S_FD_OZ, S_NTAGS
 };
 
 struct Profiler {

@@ -35,6 +35,16 @@ constexpr int kSeg = 8;
 static_assert(kStLines == 8, "stencil x stage: 3 x 8 (line, alpha) lanes per warp");
 static_assert(kThreads / 32 == kStLines, "stencil x stage: one warp per line in the trial");
 
+// Longest boundary band rows of degree P (B: the P + 1 basis functions
+// nonzero at a point; W: the points in a function's support, at most 3P + 1
+// for the WQ rules here).  The boundary loops are unrolled to these lengths,
+// taps beyond the row's own length predicated off, and any longer row ends in
+// a plain loop; the taps are summed in ascending order either way.
+template <int P>
+constexpr int kBndB = P + 1;
+template <int P>
+constexpr int kBndW = 3 * P + 1;
+
 // row stride >= n with stride = 1 (mod 32)
 __host__ __device__ inline int st_stride(int n) { return ((n + 30) / 32) * 32 + 1; }
 
@@ -64,6 +74,33 @@ __device__ __forceinline__ void st_seg(const T* w, const T* H, T* To) {
 #pragma unroll
         for (int t = 0; t < NW; ++t) acc = fmaT(w[t], h[2 * r + t], acc);
         To[r] = acc;
+    }
+}
+
+// FP32: two segments of one row at once, segments A (window at H) and B
+// (window at H + 2 kSeg), paired in the packed FP32 FMA (two FMAs per
+// instruction, each rounded as by fmaf).  The window is streamed point by
+// point; output r takes its taps in ascending order, as in st_seg, so the
+// results are bitwise those of two st_seg calls.
+template <int P>
+__device__ __forceinline__ void st_seg2(const float2* w2, const float* H, float* To) {
+    constexpr int NW = 2 * P + 1, WIN = 2 * (kSeg - 1) + NW;
+    float2 acc[kSeg];
+#pragma unroll
+    for (int r = 0; r < kSeg; ++r) acc[r] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int u = 0; u < WIN; ++u) {
+        const float2 hh = make_float2(H[u], H[u + 2 * kSeg]);
+#pragma unroll
+        for (int r = 0; r < kSeg; ++r) {
+            const int t = u - 2 * r;
+            if (t >= 0 && t < NW) acc[r] = __ffma2_rn(w2[t], hh, acc[r]);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kSeg; ++r) {
+        To[r] = acc[r].x;
+        To[kSeg + r] = acc[r].y;
     }
 }
 
@@ -147,7 +184,10 @@ __device__ __forceinline__ void st_trial(const XArgs<T>& a, const StencilD<T>& s
         const int s0 = a.B.start[q], L = a.B.len[q];
         const T* Y = sY + warp * rY + s0;
         T g = 0;
-        for (int t = 0; t < L; ++t) g = fmaT(a.B.lane(BF, q, t), Y[t], g);
+#pragma unroll
+        for (int t = 0; t < kBndB<P>; ++t)
+            if (t < L) g = fmaT(a.B.lane(BF, q, t), Y[t], g);
+        for (int t = kBndB<P>; t < L; ++t) g = fmaT(a.B.lane(BF, q, t), Y[t], g);
         T* H = sH + warp * rG + q;
         const bool first = k < 32;
         H[0] = (first ? cb0 : C0[q]) * g;
@@ -259,7 +299,10 @@ __device__ __forceinline__ void st_trial_otf(const XArgs<float>& a, const Stenci
         const int s0 = a.B.start[q], L = a.B.len[q];
         const float* Y = sY + warp * rY + s0;
         float g = 0.f;
-        for (int t = 0; t < L; ++t) g = fmaf(a.B.lane(BF, q, t), Y[t], g);
+#pragma unroll
+        for (int t = 0; t < kBndB<P>; ++t)
+            if (t < L) g = fmaf(a.B.lane(BF, q, t), Y[t], g);
+        for (int t = kBndB<P>; t < L; ++t) g = fmaf(a.B.lane(BF, q, t), Y[t], g);
         g *= K[q];
         float* H = sH + warp * rG + q;
         H[0] = __ldg(G0 + q) * g;
@@ -297,12 +340,31 @@ __device__ __forceinline__ void st_test(const XArgs<T>& a, const StencilD<T>& st
     } else if (lane < 3 * kStLines) {
         // lane = (line l, alpha al): 24 rows 1 mod 32 apart, conflict-free
         const int al = lane >> 3, l = lane & 7;
-        T w[NW];
-#pragma unroll
-        for (int t = 0; t < NW; ++t) w[t] = al == 0 ? st.wf[2 + BF][t] : st.wf[BF][t];
         const T* Hl = sH + (al * kStLines + l) * rG + st.qw;
         T* To = sT + (al * kStLines + l) * rT + st.i_lo;
-        for (int sg = warp; sg < nseg; sg += kStLines) st_seg<T, P>(w, Hl + 2 * kSeg * sg, To + kSeg * sg);
+        if constexpr (sizeof(T) == 4) {
+            // segment pairs (2m, 2m + 1) in the packed FMA; an odd last segment alone
+            float2 w2[NW];
+#pragma unroll
+            for (int t = 0; t < NW; ++t) {
+                const float v = al == 0 ? st.wf[2 + BF][t] : st.wf[BF][t];
+                w2[t] = make_float2(v, v);
+            }
+            const int npr = nseg >> 1;
+            for (int sp = warp; sp < npr; sp += kStLines)
+                st_seg2<P>(w2, Hl + 4 * kSeg * sp, To + 2 * kSeg * sp);
+            if ((nseg & 1) && warp == npr % kStLines) {
+                T w[NW];
+#pragma unroll
+                for (int t = 0; t < NW; ++t) w[t] = w2[t].x;
+                st_seg<T, P>(w, Hl + 2 * kSeg * (nseg - 1), To + kSeg * (nseg - 1));
+            }
+        } else {
+            T w[NW];
+#pragma unroll
+            for (int t = 0; t < NW; ++t) w[t] = al == 0 ? st.wf[2 + BF][t] : st.wf[BF][t];
+            for (int sg = warp; sg < nseg; sg += kStLines) st_seg<T, P>(w, Hl + 2 * kSeg * sg, To + kSeg * sg);
+        }
     }
     // boundary outputs: one (output, row) item per thread, rows fastest, handed
     // out from the last warp down (the first warps take the extra interior segments)
@@ -313,7 +375,10 @@ __device__ __forceinline__ void st_test(const XArgs<T>& a, const StencilD<T>& st
         const int s0 = a.W.start[i], L = a.W.len[i];
         const T* Hr = sH + row * rG + s0;
         T acc = 0;
-        for (int t = 0; t < L; ++t) acc = fmaT(a.W.lane(fam, i, t), Hr[t], acc);
+#pragma unroll
+        for (int t = 0; t < kBndW<P>; ++t)
+            if (t < L) acc = fmaT(a.W.lane(fam, i, t), Hr[t], acc);
+        for (int t = kBndW<P>; t < L; ++t) acc = fmaT(a.W.lane(fam, i, t), Hr[t], acc);
         sT[row * rT + i] = acc;
     }
 }

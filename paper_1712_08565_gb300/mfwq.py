@@ -112,6 +112,11 @@ _SIGS = [
     ("mfwq_set_coeff_field", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                             ctypes.c_double, ctypes.c_int]),
     ("mfwq_fp32_path", ctypes.c_int, [ctypes.c_void_p]),
+    ("mfwq_set_fd64_path", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    ("mfwq_fd64_path", ctypes.c_int, [ctypes.c_void_p]),
+    ("mfwq_set_slow_tiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    ("mfwq_slow_tiling", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int)]),
     ("mfwq_batch_create", ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p)]),
     ("mfwq_batch_destroy", None, [ctypes.c_void_p]),
     ("mfwq_batch_set_grouped", ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
@@ -466,6 +471,29 @@ class Operator:
     @fp32_path.setter
     def fp32_path(self, path: str):
         _check(lib().mfwq_set_fp32_path(self._h, {"staged": 0, "fused": 1}[path]))
+
+    @property
+    def fd64_path(self) -> str:
+        """Kernels of the FP64 FD: 'pipe' (FP64 pipe) or 'split' (BF16 tensor
+        cores by operand splitting), mfwq_fd64_path."""
+        v = lib().mfwq_fd64_path(self._h)
+        if v < 0:
+            _check(v)
+        return "split" if v == 1 else "pipe"
+
+    @fd64_path.setter
+    def fd64_path(self, path: str):
+        _check(lib().mfwq_set_fd64_path(self._h, {"pipe": 0, "split": 1}[path]))
+
+    def slow_tiling(self, fp32: bool = False) -> tuple[int, int]:
+        """(rows, cols) per thread of the slow-dimension stages (mfwq_slow_tiling)."""
+        r, c = ctypes.c_int(), ctypes.c_int()
+        _check(lib().mfwq_slow_tiling(self._h, 1 if fp32 else 0, ctypes.byref(r), ctypes.byref(c)))
+        return r.value, c.value
+
+    def set_slow_tiling(self, rows: int, cols: int = 1, fp32: bool = False):
+        """Thread tiling of the slow-dimension stages (mfwq_set_slow_tiling)."""
+        _check(lib().mfwq_set_slow_tiling(self._h, 1 if fp32 else 0, rows, cols))
 
     def profile(self, on: bool = True):
         """Bracket every later kernel launch with CUDA events (per-stage timing)."""

@@ -39,13 +39,18 @@ def test_digest_follows_the_sources(tmp_path, monkeypatch):
 
 def test_traffic_only_on_the_sources_it_was_taken_on(tmp_path, monkeypatch):
     d = _tree(tmp_path)
+    (d / "other.cu").write_text("int w;")
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    (tmp_path / "profiles" / "x.md").write_text("summary\n" + LINE % bench.csrc_digest() + "\n")
-    assert bench.profiled_traffic("k_xstage_apply<double, 4, 0, 0>", "ring-p4-nel128") == 123
+    monkeypatch.setattr(bench, "KERNEL_SOURCES", {"k_xstage_apply": ["a.cu"]})
+    k = "k_xstage_apply<double, 4, 0, 0>"
+    (tmp_path / "profiles" / "x.md").write_text("summary\n" + LINE % bench.csrc_digest(k) + "\n")
+    assert bench.profiled_traffic(k, "ring-p4-nel128") == 123
     assert bench.profiled_traffic("k_xstage_apply<double, 2, 0, 0>", "ring-p4-nel128") is None
-    assert bench.profiled_traffic("k_xstage_apply<double, 4, 0, 0>", "ring-p6-nel192") is None
-    (d / "a.cu").write_text("int z;")  # a source changed after the capture
-    assert bench.profiled_traffic("k_xstage_apply<double, 4, 0, 0>", "ring-p4-nel128") is None
+    assert bench.profiled_traffic(k, "ring-p6-nel192") is None
+    (d / "other.cu").write_text("int v;")  # a file the kernel is not built from
+    assert bench.profiled_traffic(k, "ring-p4-nel128") == 123
+    (d / "a.cu").write_text("int z;")  # one of its sources changed after the capture
+    assert bench.profiled_traffic(k, "ring-p4-nel128") is None
 
 
 @pytest.mark.parametrize("code,elem,p,name", [

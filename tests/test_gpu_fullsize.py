@@ -79,6 +79,9 @@ def test_fd_full_at_130_cubed(mf):
     z = op.fd_precond(torch.from_numpy(r).to(DEV)).cpu().numpy()
     ref = O.fd_apply(O.fd_setup(tabs), r)
     assert np.abs(z - ref).max() <= 1e-12 * np.abs(ref).max()
+    op.fd64_path = "split"  # the same products on the BF16 tensor cores by operand splitting
+    zs = op.fd_precond(torch.from_numpy(r).to(DEV)).cpu().numpy()
+    assert np.abs(zs - ref).max() <= 1e-12 * np.abs(ref).max()
     op.close()
 
 
@@ -105,6 +108,10 @@ def test_mixed_196_cubed(mf):
     z64 = op.fd_precond(torch.from_numpy(r).to(DEV)).cpu().numpy()
     ref = O.fd_apply(O.fd_setup(tabs), r)
     assert np.abs(z64 - ref).max() <= 1e-12 * np.abs(ref).max()
+    op.fd64_path = "split"
+    zs = op.fd_precond(torch.from_numpy(r).to(DEV)).cpu().numpy()
+    assert np.abs(zs - ref).max() <= 1e-12 * np.abs(ref).max()
+    op.fd64_path = "pipe"
     z32 = op.fd_precond_f32(torch.from_numpy(r).float().to(DEV)).double().cpu().numpy()
     assert np.linalg.norm(z32 - ref) <= 1e-2 * np.linalg.norm(ref)
     # the FP32 operator in its autotuned launch shape, sampled rows computed one by one

@@ -136,8 +136,35 @@ def test_autotune_picks_a_path_and_keeps_parity(mf, tmp_path):
     op.autotune(cache)
     assert op.fp32_path in ("staged", "fused")
     codes = [json.loads(l)["xstage"] for l in open(cache) if "fp32" in l]
-    assert len(codes) == 1 and (codes[0] // 10000 == 1) == (op.fp32_path == "fused")
+    assert len(codes) == 1 and ((codes[0] // 10000) % 10 == 1) == (op.fp32_path == "fused")
     x = inputs.uniform_vector(op.shape, 6)
     ref = O.apply_alg2(tabs, O.full_coeff(C6), x)
     assert np.abs(_apply32(op, x) - ref).max() <= TOL * np.abs(ref).max()
+    op.close()
+
+
+@pytest.mark.parametrize("ps,nel", [((4, 4, 4), (14, 20, 9)), ((3, 2, 5), (11, 7, 6)), ((2, 3, 2), (9, 13, 10))])
+def test_slow_tiling_is_bitwise_the_same(mf, ps, nel):
+    """Every (rows, cols) tiling of the FP32 slow stages sums each output in the
+    same order: bitwise equal results on both FP32 paths.  (3, 2, 5) with 11
+    elements gives an odd column count n1 = 14 for the y stages (n1 even: 2 columns
+    run, 4 fall back to one column per thread), (2, 3, 2) n1 = 11 (all one column)."""
+    knots = [inputs.open_uniform_knots(ps[l], nel[l]) for l in range(3)]
+    op, tabs, C6 = _patch(mf, ps, knots, 11)
+    x = inputs.uniform_vector(op.shape, 12)
+    ref = O.apply_alg2(tabs, O.full_coeff(C6), x)
+    for path in ("staged", "fused"):
+        op.fp32_path = path
+        op.set_slow_tiling(1, 1, fp32=True)
+        base = _apply32(op, x)
+        assert np.abs(base - ref).max() <= TOL * np.abs(ref).max()
+        for rows in (1, 2, 4):
+            for cols in (1, 2, 4):
+                op.set_slow_tiling(rows, cols, fp32=True)
+                assert op.slow_tiling(fp32=True) == (rows, cols)
+                assert np.array_equal(_apply32(op, x), base), (path, rows, cols)
+    with pytest.raises(mf.MfwqError):
+        op.set_slow_tiling(2, 2, fp32=False)  # FP64 stages take one column per thread
+    with pytest.raises(mf.MfwqError):
+        op.set_slow_tiling(3, 1, fp32=True)
     op.close()
