@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--kernel-p", type=int, default=None, help="with --kernel-run: degree (default: the workload's)")
     ap.add_argument("--fp32-path", choices=["staged", "fused"], default=None,
                     help="with --kernel-run apply32: force the FP32 kernel sequence")
+    ap.add_argument("--fd64-path", choices=["pipe", "split"], default=None,
+                    help="with --kernel-run fd64 / apply / mixed_solve: kernels of the FP64 FD")
     ap.add_argument("--kernel-run", choices=["apply", "apply_T", "grad", "fd64", "fdtc", "fdbf16", "apply32", "mixed_solve"],
                     default=None,
                     help="set up the workload, run one operator 3 times and exit (target for ncu captures)")
@@ -382,11 +384,18 @@ def reaction(mf, device, alpha=10.0):
     return out
 
 
+def inputs_uniform(shape):
+    from paper_1712_08565_gb300 import inputs
+    return inputs.uniform_vector(shape, 1)
+
+
 def fp64_low_fd(mf, device):
     """The bench solve (ring, p = 4, 128 elements, FP64 BiCGStab to 1e-10) with
     the FD applied on the tensor cores (TF32, then BF16) instead of in FP64:
     the iterate, operator and residual stay FP64, only the preconditioner is
-    inexact.  Times against the plain FP64 solve on the same handle."""
+    inexact.  Times against the plain FP64 solve on the same handle, whose FD
+    runs in both FP64 forms (FP64 pipe; BF16 tensor cores by operand
+    splitting, the default)."""
     import torch
     op, _ = make_op(mf, WORKLOAD["p"], WORKLOAD["nel"], mixed=True, fd="tf32", device=device)
     f = op.load_vector(WORKLOAD["geometry"], WORKLOAD["forcing"])
@@ -401,9 +410,19 @@ def fp64_low_fd(mf, device):
         e1.synchronize()
         return u, info, e0.elapsed_time(e1) / 1e3
 
+    # the FP64 FD in its two kernel forms: FP64 pipe, and BF16 tensor cores by operand splitting (the default)
+    x = torch.from_numpy(inputs_uniform(op.shape)).to(device)
+    y = torch.empty_like(x)
+    out = {"workload": WORKLOAD["name"], "rtol": WORKLOAD["rtol"]}
+    for path in ("pipe", "split"):
+        op.fd64_path = path
+        u_, i_, t_ = timed(force_fp64=True)
+        out["fp64_fd_" + path] = {"solve_s": t_, "iterations": i_.iterations, "rel_residual": i_.rel_residual,
+                                  "fd_precond_ms": event_time(op.stream, lambda: op.fd_precond(x, y), 10)}
+    out["fp64_fd_split"]["speedup_vs_pipe"] = out["fp64_fd_pipe"]["solve_s"] / out["fp64_fd_split"]["solve_s"]
     u64, i64, t64 = timed(force_fp64=True)
-    out = {"workload": WORKLOAD["name"], "rtol": WORKLOAD["rtol"],
-           "fp64_fd": {"solve_s": t64, "iterations": i64.iterations, "rel_residual": i64.rel_residual}}
+    out["fp64_fd"] = {"solve_s": t64, "iterations": i64.iterations, "rel_residual": i64.rel_residual,
+                      "path": op.fd64_path}
     u, info, t = timed(fp64_low_fd=True)
     out["tf32_fd"] = {"solve_s": t, "iterations": info.iterations, "rel_residual": info.rel_residual,
                       "converged": info.converged, "speedup": t64 / t,
@@ -632,7 +651,17 @@ def batched(mf, device):
     torch.cuda.synchronize()
     tm = time.perf_counter() - t0
     merr = max(float(torch.linalg.vector_norm(u - v) / torch.linalg.vector_norm(v)) for u, v in zip(us, u64))
-    # the grouped FP64 sweep: one launch per kernel stage over each of 4 groups of patches
+    # the grouped FP64 sweep: one launch per kernel stage over each of 4 groups of patches; its kernels
+    # are the FP64-pipe FD's, so it is compared with the per-patch streams on that FD
+    for op in ops:
+        op.fd64_path = "pipe"
+    b.solve(fs, us, rtol=BATCH["rtol"], force_fp64=True)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, pinfos = b.solve(fs, us, rtol=BATCH["rtol"], force_fp64=True)
+    torch.cuda.synchronize()
+    tp = time.perf_counter() - t0
+    up = [u.clone() for u in us]
     b.set_grouped(4)
     ug = [torch.empty_like(f) for f in fs]
     b.solve(fs, ug, rtol=BATCH["rtol"], force_fp64=True)  # warm-up
@@ -642,9 +671,11 @@ def batched(mf, device):
     torch.cuda.synchronize()
     tg = time.perf_counter() - t0
     g_ran = b.grouped
-    g_equal = all(torch.equal(a, c) for a, c in zip(ug, u64))
+    g_equal = all(torch.equal(a, c) for a, c in zip(ug, up))
     b.set_grouped(0)
-    del ug
+    for op in ops:
+        op.fd64_path = "split"
+    del ug, up
     t0 = time.perf_counter()
     seq_iters = []
     for op, f, u in zip(ops, fs, us):
@@ -662,7 +693,8 @@ def batched(mf, device):
            "all_converged": all(i.converged for i in infos),
            "apply_dof_per_s": sum(2 * i.iterations * op.N for i, op in zip(infos, ops)) / tb,
            "autotuned_xstage": {str(k): v for k, v in sorted(lines.items())},
-           "grouped_4_s": tg, "grouped_ran": g_ran, "grouped_bitwise_equal_to_streams": g_equal,
+           "fd64_path": "split", "batched_s_pipe_fd": tp,
+           "grouped_4_s_pipe_fd": tg, "grouped_ran": g_ran, "grouped_bitwise_equal_to_streams": g_equal,
            "grouped_all_converged": all(i.converged for i in ginfos)}
     b.close()
     for op in ops:
@@ -690,6 +722,8 @@ def run_ours(args):
     f = op.load_vector(WORKLOAD["geometry"], WORKLOAD["forcing"])
     u = torch.empty_like(f)
     rtol = WORKLOAD["rtol"]
+    fd_desc = ("FP64 FD on the BF16 tensor cores by operand splitting (8 x 7-bit slices, exact level sums)"
+               if op.fd64_path == "split" else "FP64 FD on the FP64 pipe")
 
     def step():
         return op.solve(f, u=None, rtol=rtol, maxit=1000)
@@ -800,10 +834,12 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOAD["name"], "p": p, "nel": nel, "N": N, "Nq": Nq, "rtol": rtol,
                    "step": "one FD-preconditioned BiCGStab solve from u=0", "l2": "inputs larger than L2 (C alone 873 MB)",
+                   "fd": fd_desc,
                    "parallelism": "replicas" if ws > 1 else "single"},
         "solve": {"time_s": ms_step / 1e3, "iterations": statistics.mean(iters), "rel_residual": info.rel_residual},
         "apply_only": {"ms": apply_ms, "dof_per_s": N / (apply_ms * 1e-3)},
         "fd_precond_ms": fd_ms,
+        "fd_precond_fp64_equiv_tflops": 4.0 * N * sum(n) / (fd_ms * 1e-3) / 1e12,
         "stages_ms_per_launch": {k: v[0] / v[1] for k, v in stages.items()},
         "stages_share": {k: v[0] / sum(s[0] for s in stages.values()) for k, v in stages.items()},
         "stages_source": "one profiled solve after the warm-up, every launch bracketed by CUDA events (outside the "
@@ -825,7 +861,7 @@ def run_ours(args):
     return 0
 
 
-def kernel_run(which, nel_override=None, fp32_path=None, p_override=None):
+def kernel_run(which, nel_override=None, fp32_path=None, p_override=None, fd64_path=None):
     """Setup + three launches of one operator on the bench workload (the
     p = 6, 192-element ring for the mixed-precision operators), or on the
     same degree with the elements per direction given (a smaller case with
@@ -848,6 +884,8 @@ def kernel_run(which, nel_override=None, fp32_path=None, p_override=None):
     op, _ = make_op(mf, p, nel, mixed=mixed, fd="bf16" if which == "fdbf16" else "tf32", device=dev)
     if fp32_path:
         op.fp32_path = fp32_path
+    if fd64_path:
+        op.fd64_path = fd64_path
     if which == "mixed_solve":  # one warm-up and one measured mixed-precision solve to 1e-8
         f = op.load_vector("ring", "sines")
         for _ in range(2):
@@ -934,7 +972,7 @@ def main():
     if args.table1:
         return table1(args)
     if args.kernel_run:
-        return kernel_run(args.kernel_run, args.kernel_nel, args.fp32_path, args.kernel_p)
+        return kernel_run(args.kernel_run, args.kernel_nel, args.fp32_path, args.kernel_p, args.fd64_path)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -225,15 +225,17 @@ int mfwq_fp32_path(mfwq_handle h);
 
 /* Kernels of the FP64 FD preconditioner (fd_precond and the FP64 solves):
  *  MFWQ_FD64_PIPE: the mode products in FP64 on the FP64 pipe (even/odd
- *    split where the knot vectors are symmetric); the default;
+ *    split where the knot vectors are symmetric); the default where a
+ *    direction has more than 256 DoFs;
  *  MFWQ_FD64_SPLIT: the mode products on the BF16 tensor cores, every FP64
  *    operand split into 8 integer slices of 7 bits under a power-of-two scale
  *    per row (Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012); the
  *    slice products accumulate exactly, and the result keeps 56 bits below
  *    each row's leading power of two, so it agrees with the FP64 products to
- *    about 2^-55 of sum |U_ij| |x_j|.  Needs every n_l <= 256; the first
- *    selection slices the mode matrices and allocates N doubles for the
- *    eigenvalue scaling (synchronous).
+ *    about 2^-55 of sum |U_ij| |x_j|.  Needs every n_l <= 256, and is then
+ *    the default: mfwq_setup slices the mode matrices and allocates N
+ *    doubles for the eigenvalue scaling and about 17 bytes per DoF of slice
+ *    workspace.
  * mfwq_set_fd64_path returns MFWQ_EINVAL for an unknown path or sizes above
  * 256; mfwq_fd64_path returns the path in use. */
 #define MFWQ_FD64_PIPE 0
@@ -365,7 +367,7 @@ int mfwq_fd_precond_noalloc(const int n[3], const double* const U_dev[3], const 
  * four stages, and for the FP32 operator the fused kernel sequence
  * (MFWQ_PATH_FUSED, where available) against the best staged one (cached
  * codes add 10000 when the fused one won) and 1, 2 or 4 columns per thread
- * in its slow stages (cached codes add 100000 times the columns).  *xlines_out (may be NULL) receives the FP64 choice as
+ * in its slow stages (cached codes add 100000 times the columns when above 1).  *xlines_out (may be NULL) receives the FP64 choice as
  * 1000 * carveout + 100 * rows + 10 * mapping + lines.  cache_path (may be
  * NULL) is a file of JSON lines {"key": "...", "xstage": that code}: a hit
  * skips the timing, a miss appends the result (codes below 100 mean one row

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <fstream>
 #include <new>
 #include <sstream>
@@ -387,6 +388,21 @@ int dmalloc(void** p, size_t bytes) {
     return MFWQ_OK;
 }
 
+// Builds the split FP64 FD of the handle (slices of U_l and U_l^T, scaling table) if not built yet.
+int split_fd_enable(mfwq_handle h) {
+    if (h->oz.ok) return MFWQ_OK;
+    for (int l = 0; l < 3; ++l)
+        if (h->n[l] > kOzMaxN) return fail(MFWQ_EINVAL, "the split FP64 FD needs at most 256 DoFs per direction");
+    static std::once_flag once;
+    static int conf = MFWQ_OK;
+    std::call_once(once, [] { conf = configure_fd_oz(); });
+    ST(conf);
+    CU(cudaStreamSynchronize(h->stream));
+    ST(oz_plan_build(h->dir, h->d64, h->stream, h->oz));
+    CU(cudaStreamSynchronize(h->stream));
+    return MFWQ_OK;
+}
+
 int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
     h->stream = static_cast<cudaStream_t>(desc->stream);
     h->mixed = desc->mixed ? 1 : 0;
@@ -553,6 +569,11 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
         ST(configure_xstage_otf_smem(xstage_otf_smem_bytes(h->n[0], h->nq[0])));
         ST(fused_plan_build(h->dir[0], h->dir[1], h->d32[0].SX, h->d32[1].SX, h->nq[2], h->fplan));
         h->fused32 = 0;  // the staged kernels unless mfwq_autotune or mfwq_set_fp32_path picks the fused one
+    }
+    // the FP64 FD on the tensor cores by operand splitting wherever every direction allows it
+    if (h->n[0] <= kOzMaxN && h->n[1] <= kOzMaxN && h->n[2] <= kOzMaxN) {
+        ST(split_fd_enable(h));
+        h->fd64_path = MFWQ_FD64_SPLIT;
     }
     CU(cudaDeviceSynchronize());
     return MFWQ_OK;
@@ -1073,18 +1094,7 @@ int mfwq_fp32_path(mfwq_handle h) {
 int mfwq_set_fd64_path(mfwq_handle h, int path) {
     if (!h) return fail(MFWQ_EINVAL, "NULL handle");
     if (path != MFWQ_FD64_PIPE && path != MFWQ_FD64_SPLIT) return fail(MFWQ_EINVAL, "unknown FP64 FD path");
-    if (path == MFWQ_FD64_SPLIT && !h->oz.ok) {
-        for (int l = 0; l < 3; ++l)
-            if (h->n[l] > kOzMaxN) return fail(MFWQ_EINVAL, "the split FP64 FD needs at most 256 DoFs per direction");
-        static bool configured = false;
-        if (!configured) {
-            ST(configure_fd_oz());
-            configured = true;
-        }
-        CU(cudaStreamSynchronize(h->stream));
-        ST(oz_plan_build(h->dir, h->d64, h->stream, h->oz));
-        CU(cudaStreamSynchronize(h->stream));
-    }
+    if (path == MFWQ_FD64_SPLIT) ST(split_fd_enable(h));
     h->fd64_path = path;
     return MFWQ_OK;
 }
@@ -1258,7 +1268,8 @@ int tune_xstage(mfwq_handle h, bool f32, int* err) {
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (cudaGetLastError() != cudaSuccess) *err = MFWQ_ECUDA;
-    return 100000 * best_V + 10000 * best_fused + 1000 * best_carve + 100 * best_R + 10 * best_mode + best_L;
+    return (best_V > 1 ? 100000 * best_V : 0) + 10000 * best_fused + 1000 * best_carve + 100 * best_R + 10 * best_mode +
+           best_L;
 }
 }  // namespace
 

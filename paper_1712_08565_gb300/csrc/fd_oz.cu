@@ -5,24 +5,28 @@
 // index as the slowest dimension of its output, as the TF32/BF16 passes of
 // fd_tc.cu do:  D[r][o] = sum_t A[r][t] Bm[o][t],  Out[o][r] = D[r][o].
 //
-// A CTA (256 threads, one per SM: its TMEM blocks take the 512 columns) computes 128 rows x kOzNT outputs of one pass per work item.
-//  * Row exponents: the largest biased exponent of each of its 128 rows of A.
-//  * Per K chunk of 32 elements (two pipeline stages): thread 0 starts the
-//    bulk copy of the precomputed Bm slices of the chunk; all threads read A
-//    (two threads per row, 16 elements each), split each element into its 7
-//    slices with integer operations and store them as BF16 in the MMA layout;
-//    then thread 0 issues the 36 slice-pair products (two K steps each) into
-//    the TMEM block of their level and commits to the stage's mbarrier.
-//  * Epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 and half the
-//    columns; per output the 8 level sums (integers in FP32) are converted to
-//    integers, added with their weights 2^(7 (9 - L)) in 128 bits and rounded
-//    to FP64 by constructing the bit pattern with the row and column scales;
-//    the scaling pass multiplies by 1 / (lam1 + lam2 + lam3) from a table.
+// A pass is two kernels.
+//  * k_oz_slice (one warp per row of A, coalesced): the row's largest biased
+//    exponent, then each element split into its 8 slices with integer
+//    operations and stored as BF16 in blocks laid out as the MMA reads them
+//    (one block per 128 rows and K chunk), beside the row exponents.
+//  * k_fd_oz (256 threads, one CTA per SM: its TMEM blocks take the 512
+//    columns) computes 128 rows x kOzNT outputs per work item.  Thread 0
+//    streams the slice blocks of A and Bm for each K chunk of 16 elements by
+//    bulk copies into four shared-memory stages (three chunks ahead) and
+//    issues the 36 slice-pair products of a chunk into the TMEM blocks of
+//    their levels, committing to the stage's mbarrier.  Epilogue: warp w
+//    reads TMEM lanes 32 (w % 4) .. + 31 and half the columns; per output the
+//    8 level sums (integers in FP32) are converted to integers, added with
+//    their weights 2^(7 (9 - L)) in 128 bits and rounded to FP64 by
+//    constructing the bit pattern with the row and column scales; the scaling
+//    pass multiplies by 1 / (lam1 + lam2 + lam3) from a table.
 // Every mbarrier wait is bounded; on timeout the kernel records an error,
 // waits (bounded) for its copies and products in flight, frees TMEM and
 // returns.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -43,14 +47,14 @@ using ptx::smem_u32;
 
 constexpr int kOzThreads = 256;
 constexpr int kOzTileM = 128;
-constexpr int kOzSliceA = kOzTileM * kOzKC * 2;    // bytes of one A slice tile (8 KB)
-constexpr int kOzSliceB = kOzNT * kOzKC * 2;       // bytes of one Bm slice tile (4 KB)
-constexpr int kOzStageA = kOzSlices * kOzSliceA;   // 56 KB
-constexpr int kOzStageB = kOzSlices * kOzSliceB;   // 28 KB
+constexpr int kOzSliceA = kOzTileM * kOzKC * 2;    // bytes of one A slice tile (4 KB)
+constexpr int kOzSliceB = kOzNT * kOzKC * 2;       // bytes of one Bm slice tile (2 KB)
+constexpr int kOzStageA = kOzSlices * kOzSliceA;   // 32 KB
+constexpr int kOzStageB = kOzSlices * kOzSliceB;   // 16 KB
 constexpr int kOzStage = kOzStageA + kOzStageB;
-constexpr int kOzStages = 2;
+constexpr int kOzStages = 4;
 constexpr int kOzTmemCols = 512;                   // kOzLevels * kOzNT
-constexpr int kOzSmem = kOzStages * kOzStage + 1024 /* alignment */ + 64 /* barriers */ + 2 * kOzTileM * 4;
+constexpr int kOzSmem = kOzStages * kOzStage + 1024 /* alignment */ + 128 /* barriers, TMEM address */;
 
 static_assert(kOzLevels * kOzNT <= kOzTmemCols, "level accumulators exceed TMEM");
 static_assert(kOzSlices == 8 && kOzBits == 7, "the slice extraction below is written for 8 x 7 bits");
@@ -80,7 +84,6 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
 }
 
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -159,24 +162,92 @@ __device__ __forceinline__ double oz_combine(const float* v, int scale) {
     return __longlong_as_double((long long)bits);
 }
 
+// ---- slicing pre-pass: one warp per (padded) row of A, lane l holds
+// elements 8 l .. 8 l + 7 (one 16-byte core-matrix row per slice)
+__global__ void __launch_bounds__(256) k_oz_slice(const double* __restrict__ A, int R, int n_in, int kch, int rows_pad,
+                                                  uint16_t* __restrict__ sl, int* __restrict__ aexp, const int* skip) {
+    if (skip && *skip) return;
+    const int lane = threadIdx.x & 31;
+    const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
+    if (row >= rows_pad) return;
+    const int t0 = 8 * lane;
+    const bool active = t0 < kch * kOzKC;  // lanes beyond the padded K write nothing
+    unsigned long long b[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) b[i] = 0ull;
+    if (row < R && t0 < n_in) {
+        const double* p = A + (size_t)row * n_in + t0;
+        if (t0 + 8 <= n_in && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const double2 v = __ldg(reinterpret_cast<const double2*>(p) + i);
+                b[2 * i] = (unsigned long long)__double_as_longlong(v.x);
+                b[2 * i + 1] = (unsigned long long)__double_as_longlong(v.y);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (t0 + i < n_in) b[i] = (unsigned long long)__double_as_longlong(__ldg(p + i));
+        }
+    }
+    int e = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) e = max(e, (int)((b[i] >> 52) & 0x7FF));
+    const int emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+    if (lane == 0) aexp[row] = emax;
+    if (!active) return;
+    uint32_t xh[8], xl[8];
+    float sg[8], sc[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const uint64_t X = oz_fixed(b[i], emax);
+        xh[i] = (uint32_t)(X >> 32);
+        xl[i] = (uint32_t)X;
+        const bool ng = (b[i] >> 63) != 0ull;
+        sg[i] = ng ? -1.f : 1.f;
+        sc[i] = ng ? 8388608.f : -8388608.f;
+    }
+    const int mt = row / kOzTileM, rr = row - mt * kOzTileM, kc = t0 / kOzKC;
+    unsigned char* blk = reinterpret_cast<unsigned char*>(sl) + ((size_t)mt * kch + kc) * kOzStageA + oz_off(rr, t0 % kOzKC);
+    auto put = [&](auto S_tag) {
+        constexpr int S = decltype(S_tag)::value;
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            w[q] = oz_pack2(oz_slice<S>(xh[2 * q], xl[2 * q]), sg[2 * q], sc[2 * q], oz_slice<S>(xh[2 * q + 1], xl[2 * q + 1]),
+                            sg[2 * q + 1], sc[2 * q + 1]);
+        *reinterpret_cast<uint4*>(blk + S * kOzSliceA) = make_uint4(w[0], w[1], w[2], w[3]);
+    };
+    put(std::integral_constant<int, 0>{});
+    put(std::integral_constant<int, 1>{});
+    put(std::integral_constant<int, 2>{});
+    put(std::integral_constant<int, 3>{});
+    put(std::integral_constant<int, 4>{});
+    put(std::integral_constant<int, 5>{});
+    put(std::integral_constant<int, 6>{});
+    put(std::integral_constant<int, 7>{});
+}
+
 struct OzArgs {
-    const double* A;     // [R][n_in]
-    double* Out;         // [n_out][R]
+    const uint16_t* Asl;  // A slices, [mtiles][k_chunks] blocks of kOzStageA bytes (k_oz_slice)
+    const int* aexp;      // [mtiles * 128]: row exponents of A
+    double* Out;          // [n_out][R]
     OzMat B;
-    const double* dinv;  // null, or the [n_out][R] scaling table
+    const double* dinv;   // null, or the [n_out][R] scaling table
     int R;
     int* err;
     const int* skip;
 };
 
+// ---- products: thread 0 streams the slice blocks of A and Bm by bulk copies
+// (one chunk ahead) and issues the MMAs; all warps run the epilogue.
 __global__ void __launch_bounds__(kOzThreads, 1) k_fd_oz(OzArgs a) {
     if (a.skip && *a.skip) return;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOzStages * kOzStage);  // Bm slices arrived
-    uint64_t* done = full + kOzStages;                                          // the stage's products finished
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOzStages * kOzStage);  // a stage's slices arrived
+    uint64_t* done = full + kOzStages;                                          // a stage's products finished
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + kOzStages);
-    int* s_e = reinterpret_cast<int*>(smem + kOzStages * kOzStage + 64);        // [2][128] row exponents
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -195,118 +266,76 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_fd_oz(OzArgs a) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int n_in = a.B.n_in, n_out = a.B.n_out, kch = a.B.k_chunks, ntl = a.B.n_tiles;
+    const int n_out = a.B.n_out, kch = a.B.k_chunks, ntl = a.B.n_tiles;
     const int mtiles = (a.R + kOzTileM - 1) / kOzTileM;
     const int items = mtiles * ntl;
-    const int r = tid & (kOzTileM - 1), half = tid >> 7;  // slicing: row r, elements 16 half .. 16 half + 15
+    const int my_items = (int)blockIdx.x < items ? (items - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int total = my_items * kch;  // chunks of this CTA, in order
     bool ok = true;
-    int g = 0;       // chunks consumed by this CTA (stage g & 1, use g >> 1)
-    int issued = 0;     // Bm copies started (thread 0)
-    int committed = 0;  // chunks whose products were committed (thread 0)
-    for (int item = blockIdx.x; item < items && ok; item += gridDim.x) {
+    int issued = 0, committed = 0;  // thread 0: chunk copies started, chunk products committed
+    // thread 0: start the copies of chunk q (stage q % kOzStages); the stage's products of chunk q - kOzStages
+    // must have finished
+    auto issue = [&](int q) -> bool {
+        const int s = q % kOzStages, use = q / kOzStages;
+        if (use >= 1 && !mbar_wait(smem_u32(&done[s]), (uint32_t)((use - 1) & 1))) return false;
+        const int it = (int)blockIdx.x + (q / kch) * (int)gridDim.x, c = q % kch;
+        const int mt = it / ntl, nt = it - mt * ntl;
+        unsigned char* sa = smem + s * kOzStage;
+        mbar_expect_tx(smem_u32(&full[s]), (uint32_t)kOzStage);
+        ptx::bulk_g2s(smem_u32(sa), reinterpret_cast<const unsigned char*>(a.Asl) + ((size_t)mt * kch + c) * kOzStageA,
+                      (uint32_t)kOzStageA, smem_u32(&full[s]));
+        ptx::bulk_g2s(smem_u32(sa + kOzStageA),
+                      reinterpret_cast<const unsigned char*>(a.B.sl) + ((size_t)nt * kch + c) * kOzStageB,
+                      (uint32_t)kOzStageB, smem_u32(&full[s]));
+        ++issued;
+        return true;
+    };
+    if (tid == 0)
+        for (int q = 0; q < kOzStages - 1 && q < total && ok; ++q) ok = issue(q);
+    int g = 0;
+    for (int ii = 0; ii < my_items; ++ii) {
+        const int item = (int)blockIdx.x + ii * (int)gridDim.x;
         const int mt = item / ntl, nt = item - mt * ntl;
         const int row0 = mt * kOzTileM;
-        const int row = row0 + r;
-        const double* Arow = a.A + (size_t)(row < a.R ? row : 0) * n_in;
-        // largest biased exponent of each row (two threads per row)
-        {
-            int e = 0;
-            if (row < a.R)
-                for (int t = half; t < n_in; t += 2)
-                    e = max(e, (int)((__double_as_longlong(__ldg(Arow + t)) >> 52) & 0x7FF));
-            s_e[half * kOzTileM + r] = e;
-        }
-        __syncthreads();
-        const int emax = max(s_e[r], s_e[kOzTileM + r]);
         const int nvalid = min(kOzNT, n_out - nt * kOzNT);
-        const int nmma = (nvalid + 15) & ~15;
-        const uint32_t idesc = idesc_bf16(nmma);
-        for (int c = 0; c < kch; ++c, ++g) {
-            const int s = g & 1, use = g >> 1;
-            unsigned char* sa = smem + s * kOzStage;
-            unsigned char* sb = sa + kOzStageA;
-            {  // the stage's previous products must have finished (every thread leaves together on a timeout)
-                const bool w = use < 1 || mbar_wait(smem_u32(&done[s]), (uint32_t)((use - 1) & 1));
-                if (!__syncthreads_and(w ? 1 : 0)) {
+        if (tid == 0 && ok) {
+            const uint32_t idesc = idesc_bf16((nvalid + 15) & ~15);
+            for (int c = 0; c < kch; ++c, ++g) {
+                const int s = g % kOzStages, use = g / kOzStages;
+                if (!mbar_wait(smem_u32(&full[s]), (uint32_t)(use & 1))) {
                     ok = false;
                     break;
                 }
-            }
-            if (tid == 0) {
-                mbar_expect_tx(smem_u32(&full[s]), (uint32_t)kOzStageB);
-                ptx::bulk_g2s(smem_u32(sb), a.B.sl + ((size_t)nt * kch + c) * (kOzStageB / 2), (uint32_t)kOzStageB,
-                              smem_u32(&full[s]));
-                ++issued;
-            }
-            // A: 16 elements of row r, split into 7 BF16 slices each
-            uint32_t xh[16], xl[16];
-            float sg[16], sc[16];
-            const int k0 = c * kOzKC + 16 * half;
+                tc_fence_after();
+                const uint32_t abase = smem_u32(smem + s * kOzStage), bbase = abase + kOzStageA;
+                const uint64_t ad0 = make_desc(abase, 128, kOzSBO), bd0 = make_desc(bbase, 128, kOzSBO);
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int k = k0 + i;
-                const unsigned long long b =
-                    (row < a.R && k < n_in) ? (unsigned long long)__double_as_longlong(__ldg(Arow + k)) : 0ull;
-                const uint64_t X = oz_fixed(b, emax);
-                xh[i] = (uint32_t)(X >> 32);
-                xl[i] = (uint32_t)X;
-                const bool ng = (b >> 63) != 0ull;
-                sg[i] = ng ? -1.f : 1.f;
-                sc[i] = ng ? 8388608.f : -8388608.f;
-            }
-            auto store_slice = [&](auto S_tag) {
-                constexpr int S = decltype(S_tag)::value;
-                uint32_t w[8];
+                for (int L = 2; L <= kOzSlices + 1; ++L) {
+                    const uint32_t td = tmem + (uint32_t)((L - 2) * kOzNT);
 #pragma unroll
-                for (int q = 0; q < 8; ++q)
-                    w[q] = oz_pack2(oz_slice<S>(xh[2 * q], xl[2 * q]), sg[2 * q], sc[2 * q],
-                                    oz_slice<S>(xh[2 * q + 1], xl[2 * q + 1]), sg[2 * q + 1], sc[2 * q + 1]);
-                unsigned char* base = sa + S * kOzSliceA;
-                *reinterpret_cast<uint4*>(base + oz_off(r, 16 * half)) = make_uint4(w[0], w[1], w[2], w[3]);
-                *reinterpret_cast<uint4*>(base + oz_off(r, 16 * half + 8)) = make_uint4(w[4], w[5], w[6], w[7]);
-            };
-            store_slice(std::integral_constant<int, 0>{});
-            store_slice(std::integral_constant<int, 1>{});
-            store_slice(std::integral_constant<int, 2>{});
-            store_slice(std::integral_constant<int, 3>{});
-            store_slice(std::integral_constant<int, 4>{});
-            store_slice(std::integral_constant<int, 5>{});
-            store_slice(std::integral_constant<int, 6>{});
-            store_slice(std::integral_constant<int, 7>{});
-            fence_async_smem();
-            __syncthreads();
-            if (tid == 0) {
-                if (!mbar_wait(smem_u32(&full[s]), (uint32_t)(use & 1))) {
-                    ok = false;
-                } else {
-                    tc_fence_after();
-                    const uint32_t abase = smem_u32(sa), bbase = smem_u32(sb);
+                    for (int si = 1; si < L; ++si) {
 #pragma unroll
-                    for (int L = 2; L <= kOzSlices + 1; ++L) {
-                        const uint32_t td = tmem + (uint32_t)((L - 2) * kOzNT);
-#pragma unroll
-                        for (int si = 1; si < L; ++si) {
-                            const int sj = L - si;
-#pragma unroll
-                            for (int kk = 0; kk < kOzKC / 16; ++kk) {
-                                const uint64_t ad = make_desc(abase + (si - 1) * kOzSliceA + kk * 256, 128, 512);
-                                const uint64_t bd = make_desc(bbase + (sj - 1) * kOzSliceB + kk * 256, 128, 512);
-                                mma_bf16(td, ad, bd, idesc, (c > 0 || si > 1 || kk > 0) ? 1u : 0u);
-                            }
+                        for (int kk = 0; kk < kOzKC / 16; ++kk) {
+                            // descriptor start addresses advance in 16-byte units
+                            const uint64_t ad = ad0 + (uint64_t)(((si - 1) * kOzSliceA + kk * 256) >> 4);
+                            const uint64_t bd = bd0 + (uint64_t)(((L - si - 1) * kOzSliceB + kk * 256) >> 4);
+                            mma_bf16(td, ad, bd, idesc, (c > 0 || si > 1 || kk > 0) ? 1u : 0u);
                         }
                     }
                 }
                 mma_commit(smem_u32(&done[s]));
                 ++committed;
+                if (g + kOzStages - 1 < total && !issue(g + kOzStages - 1)) {
+                    ok = false;
+                    ++g;
+                    break;
+                }
             }
-            if (!__syncthreads_and(ok ? 1 : 0)) ok = false;
-            if (!ok) break;
-        }
-        if (!ok) break;
-        // epilogue: the item's last products, then TMEM -> FP64
-        {
-            const int gl = g - 1;
-            if (!mbar_wait(smem_u32(&done[gl & 1]), (uint32_t)((gl >> 1) & 1))) ok = false;
+            // the item's products complete with its last chunk's commit
+            if (ok) {
+                const int gl = g - 1;
+                if (!mbar_wait(smem_u32(&done[gl % kOzStages]), (uint32_t)((gl / kOzStages) & 1))) ok = false;
+            }
         }
         if (!__syncthreads_and(ok ? 1 : 0)) {
             ok = false;
@@ -316,7 +345,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_fd_oz(OzArgs a) {
         const int q = warp & 3, hc = warp >> 2;
         const int er = q * 32 + lane;  // this thread's TMEM lane = tile row
         const int grow = row0 + er;
-        const int erow = max(s_e[er], s_e[kOzTileM + er]);
+        const int erow = __ldg(a.aexp + row0 + er);
         const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hc * 32);
 #pragma unroll 1
         for (int cg = 0; cg < 4; ++cg) {
@@ -343,16 +372,17 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_fd_oz(OzArgs a) {
             }
         }
         tc_fence_before();
-        __syncthreads();
+        __syncthreads();  // TMEM is read: the next item's products may overwrite it
     }
     if (!ok && tid == 0) atomicExch(a.err, 1);
     // drain: products and copies in flight must land before TMEM and shared memory go away
     if (tid == 0) {
         if (committed > 0) {
             const int gl = committed - 1;
-            mbar_wait(smem_u32(&done[gl & 1]), (uint32_t)((gl >> 1) & 1));
+            mbar_wait(smem_u32(&done[gl % kOzStages]), (uint32_t)((gl / kOzStages) & 1));
         }
-        for (int q2 = committed; q2 < issued; ++q2) mbar_wait(smem_u32(&full[q2 & 1]), (uint32_t)((q2 >> 1) & 1));
+        for (int q2 = committed; q2 < issued; ++q2)
+            mbar_wait(smem_u32(&full[q2 % kOzStages]), (uint32_t)((q2 / kOzStages) & 1));
     }
     tc_fence_before();
     __syncthreads();
@@ -448,8 +478,16 @@ int oz_plan_build(const Dir1D dir[3], const DirD<double> d64[3], cudaStream_t s,
         bytes += (fx[m].size() * 4 + 255) / 256 * 256;
     }
     const size_t N = (size_t)dir[0].n * dir[1].n * dir[2].n;
+    size_t asl_bytes = 0, aexp_n = 0;
+    for (int l = 0; l < 3; ++l) {
+        const size_t R = N / dir[l].n, mt = (R + kOzTileM - 1) / kOzTileM;
+        asl_bytes = std::max(asl_bytes, mt * (size_t)kc[l] * kOzStageA);
+        aexp_n = std::max(aexp_n, mt * kOzTileM);
+    }
     if (cudaMalloc(&plan.dmem, bytes) != cudaSuccess) return MFWQ_ENOMEM;
-    if (cudaMalloc((void**)&plan.dinv, sizeof(double) * N) != cudaSuccess) {
+    if (cudaMalloc((void**)&plan.dinv, sizeof(double) * N) != cudaSuccess ||
+        cudaMalloc((void**)&plan.asl, asl_bytes) != cudaSuccess ||
+        cudaMalloc((void**)&plan.aexp, sizeof(int) * aexp_n) != cudaSuccess) {
         oz_plan_free(plan);
         return MFWQ_ENOMEM;
     }
@@ -479,14 +517,17 @@ int oz_plan_build(const Dir1D dir[3], const DirD<double> d64[3], cudaStream_t s,
 void oz_plan_free(OzPlan& plan) {
     if (plan.dmem) cudaFree(plan.dmem);
     if (plan.dinv) cudaFree(plan.dinv);
+    if (plan.asl) cudaFree(plan.asl);
+    if (plan.aexp) cudaFree(plan.aexp);
     plan = OzPlan{};
 }
 
 namespace {
-int oz_pass(const OzMat& B, const double* A, double* Out, int R, const double* dinv, int* err, const int* skip,
-            cudaStream_t s) {
+int oz_pass(const OzPlan& p, const OzMat& B, const double* A, double* Out, int R, const double* dinv, int* err,
+            const int* skip, cudaStream_t s) {
     OzArgs a;
-    a.A = A;
+    a.Asl = p.asl;
+    a.aexp = p.aexp;
     a.Out = Out;
     a.B = B;
     a.dinv = dinv;
@@ -497,10 +538,15 @@ int oz_pass(const OzMat& B, const double* A, double* Out, int R, const double* d
         g_rec->unsupported = true;
         return MFWQ_OK;
     }
-    const int items = (R + kOzTileM - 1) / kOzTileM * B.n_tiles;
+    const int mtiles = (R + kOzTileM - 1) / kOzTileM;
+    const int items = mtiles * B.n_tiles;
     int grid = g_oz_sms > 0 ? g_oz_sms : 148;
     if (grid > items) grid = items;
     if (grid < 1) grid = 1;
+    const int rows_pad = mtiles * kOzTileM;
+    launch_begin(S_FD_OZ, s);
+    k_oz_slice<<<(rows_pad + 7) / 8, 256, 0, s>>>(A, R, B.n_in, B.k_chunks, rows_pad, p.asl, p.aexp, skip);
+    launch_end(S_FD_OZ, s);
     launch_begin(S_FD_OZ, s);
     k_fd_oz<<<grid, kOzThreads, kOzSmem, s>>>(a);
     launch_end(S_FD_OZ, s);
@@ -512,12 +558,12 @@ int run_fd_oz(const OzPlan& p, const double* r, double* z, double* tmp, int* err
     if (!p.ok) return MFWQ_EINVAL;
     const int n1 = p.fwd[0].n_in, n2 = p.fwd[1].n_in, n3 = p.fwd[2].n_in;
     // forward U^T products with the scaling in the third, then the U products (fd_tc.cu's rotation order)
-    if (oz_pass(p.fwd[0], r, tmp, n3 * n2, nullptr, err, skip, s)) return MFWQ_ECUDA;
-    if (oz_pass(p.fwd[1], tmp, z, n1 * n3, nullptr, err, skip, s)) return MFWQ_ECUDA;
-    if (oz_pass(p.fwd[2], z, tmp, n2 * n1, p.dinv, err, skip, s)) return MFWQ_ECUDA;
-    if (oz_pass(p.bwd[0], tmp, z, n3 * n2, nullptr, err, skip, s)) return MFWQ_ECUDA;
-    if (oz_pass(p.bwd[1], z, tmp, n1 * n3, nullptr, err, skip, s)) return MFWQ_ECUDA;
-    if (oz_pass(p.bwd[2], tmp, z, n2 * n1, nullptr, err, skip, s)) return MFWQ_ECUDA;
+    if (oz_pass(p, p.fwd[0], r, tmp, n3 * n2, nullptr, err, skip, s)) return MFWQ_ECUDA;
+    if (oz_pass(p, p.fwd[1], tmp, z, n1 * n3, nullptr, err, skip, s)) return MFWQ_ECUDA;
+    if (oz_pass(p, p.fwd[2], z, tmp, n2 * n1, p.dinv, err, skip, s)) return MFWQ_ECUDA;
+    if (oz_pass(p, p.bwd[0], tmp, z, n3 * n2, nullptr, err, skip, s)) return MFWQ_ECUDA;
+    if (oz_pass(p, p.bwd[1], z, tmp, n1 * n3, nullptr, err, skip, s)) return MFWQ_ECUDA;
+    if (oz_pass(p, p.bwd[2], tmp, z, n2 * n1, nullptr, err, skip, s)) return MFWQ_ECUDA;
     return MFWQ_OK;
 }
 

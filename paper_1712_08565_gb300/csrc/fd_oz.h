@@ -27,14 +27,15 @@ constexpr int kOzBits = 7;     // bits per slice
 constexpr int kOzFix = kOzSlices * kOzBits;  // fixed-point bits per operand (56)
 constexpr int kOzLevels = 8;   // levels L = 2 .. kOzSlices + 1
 constexpr int kOzNT = 64;      // output columns per tile (N of the MMA)
-constexpr int kOzKC = 32;      // K elements per pipeline chunk
+constexpr int kOzKC = 16;      // K elements per pipeline chunk (one MMA K step)
+constexpr int kOzSBO = kOzKC / 8 * 128;  // bytes between 8-row groups of a slice tile
 constexpr int kOzMaxN = 256;   // largest mode-matrix order
 
 // A mode matrix Bm [n_out][n_in] (U_l^T or U_l) in slices, on the device.
 struct OzMat {
     const uint16_t* sl = nullptr;  // [n_tiles][k_chunks] blocks of kOzSlices x (kOzNT rows x kOzKC) BF16 bits, each
                                    // slice in the shared-memory layout the MMA reads (8-row x 16-byte core matrices,
-                                   // 128 B between K-neighbours, 512 B between 8-row groups)
+                                   // 128 B between K-neighbours, kOzSBO bytes between 8-row groups)
     const int* fexp = nullptr;     // [n_tiles * kOzNT]: biased exponent of each row's largest entry (0: zero row)
     int n_out = 0, n_in = 0, n_tiles = 0, k_chunks = 0;
 };
@@ -44,6 +45,8 @@ struct OzPlan {
     OzMat fwd[3], bwd[3];          // U_l^T (forward products) and U_l (backward products)
     double* dinv = nullptr;        // [n3][n2 n1]: 1 / (lam1[i] + lam2[j] + lam3[k]), the scaling pass's layout
     void* dmem = nullptr;          // slices and exponents (one allocation)
+    uint16_t* asl = nullptr;       // slices of one pass's input, in the MMA layout (largest pass)
+    int* aexp = nullptr;           // its row exponents
 };
 
 // 56-bit fixed-point magnitude of the FP64 value with bit pattern `bits`
@@ -60,7 +63,7 @@ MFWQ_HD inline uint64_t oz_fixed(uint64_t bits, int emax) {
 
 // Byte offset of element (r, k) of a slice tile (rows of kOzKC BF16 values)
 // in the MMA's no-swizzle K-major layout.
-MFWQ_HD inline int oz_off(int r, int k) { return (r >> 3) * 512 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+MFWQ_HD inline int oz_off(int r, int k) { return (r >> 3) * kOzSBO + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
 
 // Builds the slices of U_l, U_l^T from the host tables and the scaling table
 // from the device eigenvalues (d64[l].lam, which include any FD shift).

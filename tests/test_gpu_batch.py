@@ -37,6 +37,8 @@ def test_batch_equals_separate_solves(mf):
     (same kernels, same deterministic reductions, independent patches)."""
     specs = inputs.batch_patches(count=6, seed=3, nel_range=(3, 12))
     ops = [_patch(mf, p, nel, i) for i, (p, nel) in enumerate(specs)]
+    for op in ops:
+        op.fd64_path = "pipe"  # the FD kernels with a grouped form
     fs = [op.load_vector("ring", "sines") for op in ops]
     ref = [op.solve(f, rtol=1e-8, force_fp64=True) for op, f in zip(ops, fs)]
     b = mf.Batch(ops)
@@ -62,10 +64,13 @@ def test_batch_equals_separate_solves(mf):
 
 def test_grouped_sweep_equals_per_stream_sweep(mf):
     """The grouped FP64 sweep and the per-patch-stream sweep give the same
-    bits; a patch with a reaction term (no grouped form) makes the batch fall
-    back to per-patch streams, still matching its separate solve."""
+    bits (FP64-pipe FD, whose kernels have grouped forms); a patch with a
+    reaction term (no grouped form) makes the batch fall back to per-patch
+    streams, still matching its separate solve."""
     specs = inputs.batch_patches(count=5, seed=11, nel_range=(3, 10))
     ops = [_patch(mf, p, nel, 40 + i) for i, (p, nel) in enumerate(specs)]
+    for op in ops:
+        op.fd64_path = "pipe"
     fs = [op.load_vector("ring", "sines") for op in ops]
     b = mf.Batch(ops)
     us, i_s = b.solve(fs, rtol=1e-9)  # per-patch streams (the default)

@@ -1,6 +1,7 @@
 """GPU tests of the FP64 FD preconditioner on the BF16 tensor cores by operand
-splitting (mfwq_set_fd64_path(MFWQ_FD64_SPLIT)) against the oracle's FD
-(O.fd_apply, the FD method of Section 4 in float64).
+splitting (MFWQ_FD64_SPLIT, the default wherever every n_l <= 256) and of the
+FP64-pipe kernels (MFWQ_FD64_PIPE) against the oracle's FD (O.fd_apply, the
+FD method of Section 4 in float64).
 
 Tolerance: 1e-12 of the largest oracle entry, the bar of the FP64 FD tests.
 Each of the six mode products keeps 49 bits below the leading power of two of
@@ -49,9 +50,7 @@ def _fd(op, r):
 def test_split_fd_matches_oracle(mf, ps, nel):
     knots = [inputs.open_uniform_knots(ps[l], nel[l]) for l in range(3)]
     op, tabs = _op(mf, ps, knots)
-    assert op.fd64_path == "pipe"
-    op.fd64_path = "split"
-    assert op.fd64_path == "split"
+    assert op.fd64_path == "split"  # the default wherever every n_l <= 256
     r = inputs.uniform_vector(op.shape, sum(nel))
     ref = O.fd_apply(O.fd_setup(tabs), r)
     z = _fd(op, r)
@@ -88,6 +87,7 @@ def test_split_fd_with_shift_and_solve(mf):
     op, tabs = _op(mf, p, knots)
     op.set_coeff(op.eval_coeff("ring"))
     f = op.load_vector("ring", "sines")
+    op.fd64_path = "pipe"
     u0, i0 = op.solve(f, rtol=1e-10)
     op.fd64_path = "split"
     u1, i1 = op.solve(f, rtol=1e-10)
@@ -132,6 +132,7 @@ def test_split_fd_in_a_batch(mf):
 def test_split_fd_refuses_large_directions(mf):
     knots = [inputs.open_uniform_knots(2, 260), inputs.open_uniform_knots(2, 3), inputs.open_uniform_knots(2, 3)]
     op = mf.Operator(2, knots, device=DEV)
+    assert op.fd64_path == "pipe"  # 262 DoFs in direction 1: the FP64-pipe FD
     with pytest.raises(mf.MfwqError):
         op.fd64_path = "split"
     assert op.fd64_path == "pipe"

@@ -76,12 +76,13 @@ def test_apply_sampled_rows_at_128_elements(mf, p):
 def test_fd_full_at_130_cubed(mf):
     op, tabs = _ring(mf, 4, 128)
     r = inputs.uniform_vector(op.shape, 7)
-    z = op.fd_precond(torch.from_numpy(r).to(DEV)).cpu().numpy()
     ref = O.fd_apply(O.fd_setup(tabs), r)
-    assert np.abs(z - ref).max() <= 1e-12 * np.abs(ref).max()
-    op.fd64_path = "split"  # the same products on the BF16 tensor cores by operand splitting
+    assert op.fd64_path == "split"  # the default: the products on the BF16 tensor cores by operand splitting
     zs = op.fd_precond(torch.from_numpy(r).to(DEV)).cpu().numpy()
     assert np.abs(zs - ref).max() <= 1e-12 * np.abs(ref).max()
+    op.fd64_path = "pipe"  # the FP64-pipe kernels (even/odd split)
+    z = op.fd_precond(torch.from_numpy(r).to(DEV)).cpu().numpy()
+    assert np.abs(z - ref).max() <= 1e-12 * np.abs(ref).max()
     op.close()
 
 
@@ -105,13 +106,13 @@ def test_solve_130_cubed_residual_and_load_vector(mf):
 def test_mixed_196_cubed(mf):
     op, tabs = _ring(mf, 6, 192, mixed=True)
     r = inputs.uniform_vector(op.shape, 8)
-    z64 = op.fd_precond(torch.from_numpy(r).to(DEV)).cpu().numpy()
     ref = O.fd_apply(O.fd_setup(tabs), r)
-    assert np.abs(z64 - ref).max() <= 1e-12 * np.abs(ref).max()
-    op.fd64_path = "split"
-    zs = op.fd_precond(torch.from_numpy(r).to(DEV)).cpu().numpy()
+    zs = op.fd_precond(torch.from_numpy(r).to(DEV)).cpu().numpy()  # split FD (default)
     assert np.abs(zs - ref).max() <= 1e-12 * np.abs(ref).max()
     op.fd64_path = "pipe"
+    z64 = op.fd_precond(torch.from_numpy(r).to(DEV)).cpu().numpy()
+    assert np.abs(z64 - ref).max() <= 1e-12 * np.abs(ref).max()
+    op.fd64_path = "split"
     z32 = op.fd_precond_f32(torch.from_numpy(r).float().to(DEV)).double().cpu().numpy()
     assert np.linalg.norm(z32 - ref) <= 1e-2 * np.linalg.norm(ref)
     # the FP32 operator in its autotuned launch shape, sampled rows computed one by one
@@ -184,11 +185,16 @@ def test_batched_64_patches(mf):
     assert all(i.converged and i.rel_residual <= 1e-8 for i in infos)
     um, minfos = b.solve(fs, [torch.empty_like(f) for f in fs], rtol=1e-8)
     assert all(i.converged and i.rel_residual <= 1e-8 for i in minfos)
-    b.set_grouped(4)  # the grouped sweep (4 concurrent groups): the same bits as the per-patch streams
+    # the grouped sweep (4 concurrent groups, FP64-pipe FD): the same bits as the per-patch streams
+    for op in ops:
+        op.fd64_path = "pipe"
+    up, pinfos = b.solve(fs, [torch.empty_like(f) for f in fs], rtol=1e-8, force_fp64=True)
+    assert not b.grouped and all(i.converged and i.rel_residual <= 1e-8 for i in pinfos)
+    b.set_grouped(4)
     ug, ginfos = b.solve(fs, [torch.empty_like(f) for f in fs], rtol=1e-8, force_fp64=True)
     assert b.grouped
-    assert all(a.iterations == c.iterations for a, c in zip(ginfos, infos))
-    assert all(torch.equal(x, y) for x, y in zip(ug, us))
+    assert all(a.iterations == c.iterations for a, c in zip(ginfos, pinfos))
+    assert all(torch.equal(x, y) for x, y in zip(ug, up))
     for i in range(6):  # the oracle checks the residual of a few patches, FP64 and mixed
         box = O.coefficient_box_fn(tabs[i], "ring", inputs.fourier_modes(1000 + i), 0.3)
         rows = _rows(ops[i].shape, 8, i)
