@@ -29,6 +29,8 @@ struct XArgs {
     TileD<T> WX;   // W in two-output tiles (tiled mapping)
     int n1, nq1, nlines;
     int wnb;       // W rows at each end with a band length other than the middle row's
+    const int* qord;  // points by decreasing W^T band length (the transposed and gradient x stages)
+    const int* jord;  // DoFs by decreasing B^T band length
     size_t cs;     // element stride between the coefficient fields of C
     size_t gs;     // element stride between the fields of the gradient output
     const T* C;    // [6][cs], the first Nq of each field used
@@ -49,6 +51,8 @@ XArgs<T> xargs(const DirD<T>& d1, int nlines, size_t cs, const T* C) {
     a.nq1 = d1.nq;
     a.nlines = nlines;
     a.wnb = d1.wnb;
+    a.qord = d1.qord;
+    a.jord = d1.jord;
     a.cs = cs;
     a.gs = 0;
     a.C = C;

@@ -559,6 +559,12 @@ static int aux_threads(int nq1) {
     return std::max(64, std::min(kAuxMaxThreads, (per + 31) / 32 * 32));
 }
 
+// Row stride (elements) of the per-line shared-memory rows of the transposed
+// and gradient x stages: the smallest stride >= n that is 8 mod 16, so that the
+// 4 lines x 8 rows of a warp's lanes (lines innermost) spread over the banks:
+// two wavefronts per 8-byte load, one per 4-byte load.
+MFWQ_HD inline int aux_stride(int n) { return n + (8 - n % 16 + 16) % 16; }
+
 // Transposed x stage: R (9 inputs [line][n1]) -> S^(ab) = W1^T R at q1 ->
 // E_b = sum_a C_ab S^(ab) -> X_b = B1^(b)T E_b (3 outputs [line][n1]).
 template <typename T>
@@ -567,28 +573,27 @@ __global__ void __launch_bounds__(kAuxMaxThreads) k_xstage_applyT(XArgs<T> a, Pt
                                                             const int* skip) {
     if (skip && *skip) return;
     extern __shared__ unsigned char smem_raw[];
-    T* sR = reinterpret_cast<T*>(smem_raw);  // [9][kLines][n1]
-    T* sE = sR + 9 * kLines * a.n1;          // [3][kLines][nq1]
+    const int n1 = a.n1, nq1 = a.nq1, rs = aux_stride(n1), qs = aux_stride(nq1);
+    T* sR = reinterpret_cast<T*>(smem_raw);  // [9][kLines][rs]
+    T* sE = sR + 9 * kLines * rs;            // [3][kLines][qs]
     const int line0 = blockIdx.x * kLines;
     const int nl = min(kLines, a.nlines - line0);
-    const int n1 = a.n1, nq1 = a.nq1;
     for (int e = threadIdx.x; e < nl * n1; e += blockDim.x) {
         const int l = e / n1, j = e - l * n1;
         const size_t gi = (size_t)(line0 + l) * n1 + j;
 #pragma unroll
-        for (int k = 0; k < 9; ++k) sR[(k * kLines + l) * n1 + j] = rin.p[k][gi];
+        for (int k = 0; k < 9; ++k) sR[(k * kLines + l) * rs + j] = rin.p[k][gi];
     }
     __syncthreads();
-    // points in parity order (even q, then odd q): the transposed W rows of
-    // interior points of one parity have one band length, so a warp's lanes
-    // leave the tap loop together
-    const int half = (nq1 + 1) >> 1;
+    // items (point, line), lines innermost, points by decreasing W^T band length
+    // (a.qord): the lanes of a warp walk bands of one length and leave the tap
+    // loop together
     for (int e = threadIdx.x; e < nl * nq1; e += blockDim.x) {
-        const int l = e / nq1, r = e - l * nq1;
-        const int q = r < half ? 2 * r : 2 * (r - half) + 1;
+        const int k = e / nl, l = e - k * nl;
+        const int q = a.qord[k];
         const int s = a.WT.start[q], L = a.WT.len[q];
-        const int fs = kLines * n1;
-        const T* R = sR + l * n1 + s;
+        const int fs = kLines * rs;
+        const T* R = sR + l * rs + s;
         T S[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) S[k] = 0;
@@ -607,18 +612,20 @@ __global__ void __launch_bounds__(kAuxMaxThreads) k_xstage_applyT(XArgs<T> a, Pt
         const size_t pt = (size_t)(line0 + l) * nq1 + q;
         const T c11 = a.C[pt], c22 = a.C[a.cs + pt], c33 = a.C[2 * a.cs + pt];
         const T c12 = a.C[3 * a.cs + pt], c13 = a.C[4 * a.cs + pt], c23 = a.C[5 * a.cs + pt];
-        const int es = kLines * nq1;
-        T* E = sE + l * nq1 + q;
+        const int es = kLines * qs;
+        T* E = sE + l * qs + q;
         E[0 * es] = c11 * S[0] + c12 * S[3] + c13 * S[6];  // beta = 1: C_11 S11 + C_21 S21 + C_31 S31
         E[1 * es] = c12 * S[1] + c22 * S[4] + c23 * S[7];  // beta = 2
         E[2 * es] = c13 * S[2] + c23 * S[5] + c33 * S[8];  // beta = 3
     }
     __syncthreads();
+    // items (DoF, line), lines innermost, DoFs by decreasing B^T band length (a.jord)
     for (int e = threadIdx.x; e < nl * n1; e += blockDim.x) {
-        const int l = e / n1, j = e - l * n1;
+        const int k = e / nl, l = e - k * nl;
+        const int j = a.jord[k];
         const int s = a.BT.start[j], L = a.BT.len[j];
-        const int es = kLines * nq1;
-        const T* E = sE + l * nq1 + s;
+        const int es = kLines * qs;
+        const T* E = sE + l * qs + s;
         T o1 = 0, o2 = 0, o3 = 0;
         for (int t = 0; t < L; ++t) {
             const T b0 = a.BT.lane(0, j, t), b1 = a.BT.lane(1, j, t);
@@ -639,31 +646,30 @@ template <typename T>
 __global__ void __launch_bounds__(kAuxMaxThreads) k_xstage_grad(XArgs<T> a, const T* __restrict__ y0, const T* __restrict__ y1,
                                                           const T* __restrict__ y2, Ptr9<T> rin, T* __restrict__ g6) {
     extern __shared__ unsigned char smem_raw[];
-    T* sY = reinterpret_cast<T*>(smem_raw);  // [3][kLines][n1]
-    T* sR = sY + 3 * kLines * a.n1;          // [9][kLines][n1]
+    const int n1 = a.n1, nq1 = a.nq1, rs = aux_stride(n1);
+    T* sY = reinterpret_cast<T*>(smem_raw);  // [3][kLines][rs]
+    T* sR = sY + 3 * kLines * rs;            // [9][kLines][rs]
     const int line0 = blockIdx.x * kLines;
     const int nl = min(kLines, a.nlines - line0);
-    const int n1 = a.n1, nq1 = a.nq1;
     for (int e = threadIdx.x; e < nl * n1; e += blockDim.x) {
         const int l = e / n1, j = e - l * n1;
         const size_t gi = (size_t)(line0 + l) * n1 + j;
-        sY[(0 * kLines + l) * n1 + j] = y0[gi];
-        sY[(1 * kLines + l) * n1 + j] = y1[gi];
-        sY[(2 * kLines + l) * n1 + j] = y2[gi];
+        sY[(0 * kLines + l) * rs + j] = y0[gi];
+        sY[(1 * kLines + l) * rs + j] = y1[gi];
+        sY[(2 * kLines + l) * rs + j] = y2[gi];
 #pragma unroll
-        for (int k = 0; k < 9; ++k) sR[(k * kLines + l) * n1 + j] = rin.p[k][gi];
+        for (int k = 0; k < 9; ++k) sR[(k * kLines + l) * rs + j] = rin.p[k][gi];
     }
     __syncthreads();
-    // points in parity order, as in the transposed x stage
-    const int half = (nq1 + 1) >> 1;
+    // items (point, line) in the order of the transposed x stage (a.qord)
     for (int e = threadIdx.x; e < nl * nq1; e += blockDim.x) {
-        const int l = e / nq1, r = e - l * nq1;
-        const int q = r < half ? 2 * r : 2 * (r - half) + 1;
-        const int fs = kLines * n1;
+        const int k = e / nl, l = e - k * nl;
+        const int q = a.qord[k];
+        const int fs = kLines * rs;
         T g1 = 0, g2 = 0, g3 = 0;
         {
             const int s = a.B.start[q], L = a.B.len[q];
-            const T* Y = sY + l * n1 + s;
+            const T* Y = sY + l * rs + s;
             for (int t = 0; t < L; ++t) {
                 const T b0 = a.B.lane(0, q, t), b1 = a.B.lane(1, q, t);
                 g1 = fmaT(b1, Y[0 * fs + t], g1);
@@ -676,7 +682,7 @@ __global__ void __launch_bounds__(kAuxMaxThreads) k_xstage_grad(XArgs<T> a, cons
         for (int k = 0; k < 9; ++k) S[k] = 0;
         {
             const int s = a.WT.start[q], L = a.WT.len[q];
-            const T* R = sR + l * n1 + s;
+            const T* R = sR + l * rs + s;
             for (int t = 0; t < L; ++t) {
                 const T f00 = a.WT.lane(0, q, t), f01 = a.WT.lane(1, q, t), f10 = a.WT.lane(2, q, t), f11 = a.WT.lane(3, q, t);
                 S[0] = fmaT(f11, R[0 * fs + t], S[0]);
@@ -1077,7 +1083,7 @@ int run_apply_T(const OpCtx<T>& c, const T* x, T* y, const int* skip) {
     // x stage: R (P[3..12)) -> X1, X2, X3 (P[0..3))
     {
         XArgs<T> a = xargs(d1, q3 * q2, c.cs, c.C);
-        size_t sm = sizeof(T) * ((size_t)9 * kLines * n1 + (size_t)3 * kLines * q1);
+        size_t sm = sizeof(T) * ((size_t)9 * kLines * aux_stride(n1) + (size_t)3 * kLines * aux_stride(q1));
         dim3 grid((q3 * q2 + kLines - 1) / kLines);
         Ptr9<T> rp;
         for (int k = 0; k < 9; ++k) rp.p[k] = P + (3 + k) * SP;
@@ -1120,7 +1126,7 @@ int run_grad(const OpCtx<T>& c, const T* lam, const T* u, T* g6) {
     if (st != MFWQ_OK) return st;
     XArgs<T> a = xargs(d1, q3 * q2, c.cs, c.C);
     a.gs = c.Nq;
-    size_t sm = sizeof(T) * ((size_t)12 * kLines * n1);
+    size_t sm = sizeof(T) * ((size_t)12 * kLines * aux_stride(n1));
     dim3 grid((q3 * q2 + kLines - 1) / kLines);
     Ptr9<T> rp;
     for (int k = 0; k < 9; ++k) rp.p[k] = P + (3 + k) * SP;
@@ -1170,8 +1176,8 @@ size_t rhs_scratch_elems(const int n[3], const int ng[3]) {
 }
 
 int xstage_aux_smem_bytes(int elem_size, int n1, int nq1) {
-    size_t b = (size_t)9 * kLines * n1 + (size_t)3 * kLines * nq1;  // transposed x stage
-    size_t c = (size_t)12 * kLines * n1;                             // gradient x stage
+    size_t b = (size_t)9 * kLines * aux_stride(n1) + (size_t)3 * kLines * aux_stride(nq1);  // transposed x stage
+    size_t c = (size_t)12 * kLines * aux_stride(n1);                                         // gradient x stage
     return (int)((b > c ? b : c) * elem_size);
 }
 

@@ -435,9 +435,23 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
     BandOff bo[3][6];
     TileOff to[3][2];
     size_t U64[3], UT64[3], L64[3], U32[3], UT32[3], L32[3], XQ[3], XG[3], XE[3], WE[3];
-    size_t VE[3] = {}, VET[3] = {}, VO[3] = {}, VOT[3] = {}, LS[3] = {};
+    size_t VE[3] = {}, VET[3] = {}, VO[3] = {}, VOT[3] = {}, LS[3] = {}, QO[3], JO[3];
     for (int l = 0; l < 3; ++l) {
         const Dir1D& d = h->dir[l];
+        {
+            // item orders of the transposed and gradient x stages: rows by decreasing band
+            // length, so that the lanes of a warp walk bands of one length
+            auto by_len = [](const Band1D& b, std::vector<int> ord) {
+                std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return b.len[x] > b.len[y]; });
+                return ord;
+            };
+            std::vector<int> q(d.nq), j(d.n);
+            const int half = (d.nq + 1) / 2;
+            for (int r = 0; r < d.nq; ++r) q[r] = r < half ? 2 * r : 2 * (r - half) + 1;  // parity order
+            for (int r = 0; r < d.n; ++r) j[r] = r;
+            QO[l] = a.add_vec(by_len(d.WT, q));
+            JO[l] = a.add_vec(by_len(d.BT, j));
+        }
         bo[l][0] = stage_band(a, d.B);
         bo[l][1] = stage_band(a, d.BT);
         bo[l][2] = stage_band(a, d.W);
@@ -500,6 +514,8 @@ int setup_impl(const mfwq_setup_desc* desc, mfwq_handle h) {
                 if (W.len[i] != lm) nb = std::max(nb, std::min(i + 1, nr - i));
             x.wnb = y.wnb = 2 * nb < nr ? nb : 0;
         }
+        x.qord = y.qord = reinterpret_cast<const int*>(base + QO[l]);
+        x.jord = y.jord = reinterpret_cast<const int*>(base + JO[l]);
         x.SX = detect_stencil(h->dir[l]);
         y.SX = stencil_as<float>(x.SX);
         y.BX = tiles_at<float>(base, to[l][0]);

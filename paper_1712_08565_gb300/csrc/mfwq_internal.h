@@ -113,6 +113,8 @@ struct DirD {
     TileD<T> BX, WX;  // B and W in two-row tiles (the tiled x stage)
     StencilD<T> SX;   // translation-invariant interior of B and W (the stencil x stage)
     int wnb;          // W rows at each end whose band length differs from the middle row's (0: none split off)
+    const int* qord;  // points q by decreasing length of their W^T band (ties in parity order): [nq]
+    const int* jord;  // DoFs j by decreasing length of their B^T band (ties in index order): [n]
     int ne;           // error points
     const double* xe; // error points and weights (always FP64)
     const double* we;
