@@ -10,13 +10,13 @@
 //    exponent, then each element split into its 8 slices with integer
 //    operations and stored as BF16 in blocks laid out as the MMA reads them
 //    (one block per 128 rows and K chunk), beside the row exponents.
-//  * k_fd_oz (256 threads, one CTA per SM: its TMEM blocks take the 512
+//  * k_fd_oz (512 threads, one CTA per SM: its TMEM blocks take the 512
 //    columns) computes 128 rows x kOzNT outputs per work item.  Thread 0
 //    streams the slice blocks of A and Bm for each K chunk of 16 elements by
 //    bulk copies into four shared-memory stages (three chunks ahead) and
 //    issues the 36 slice-pair products of a chunk into the TMEM blocks of
 //    their levels, committing to the stage's mbarrier.  Epilogue: warp w
-//    reads TMEM lanes 32 (w % 4) .. + 31 and half the columns; per output the
+//    reads TMEM lanes 32 (w % 4) .. + 31 and a quarter of the columns; per output the
 //    8 level sums (integers in FP32) are converted to integers, added with
 //    their weights 2^(7 (9 - L)) in 128 bits and rounded to FP64 by
 //    constructing the bit pattern with the row and column scales; the scaling
@@ -45,7 +45,7 @@ using ptx::mbar_init;
 using ptx::mbar_wait;
 using ptx::smem_u32;
 
-constexpr int kOzThreads = 256;
+constexpr int kOzThreads = 512;  // 16 warps: 4 TMEM lane quarters x 4 column quarters in the epilogue
 constexpr int kOzTileM = 128;
 constexpr int kOzSliceA = kOzTileM * kOzKC * 2;    // bytes of one A slice tile (4 KB)
 constexpr int kOzSliceB = kOzNT * kOzKC * 2;       // bytes of one Bm slice tile (2 KB)
@@ -342,14 +342,15 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_fd_oz(OzArgs a) {
             break;
         }
         tc_fence_after();
+        constexpr int kColsPerWarp = kOzNT / (kOzThreads / 128);  // 16
         const int q = warp & 3, hc = warp >> 2;
         const int er = q * 32 + lane;  // this thread's TMEM lane = tile row
         const int grow = row0 + er;
         const int erow = __ldg(a.aexp + row0 + er);
-        const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hc * 32);
+        const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hc * kColsPerWarp);
 #pragma unroll 1
-        for (int cg = 0; cg < 4; ++cg) {
-            const int col0 = hc * 32 + cg * 8;  // column within the tile
+        for (int cg = 0; cg < kColsPerWarp / 8; ++cg) {
+            const int col0 = hc * kColsPerWarp + cg * 8;  // column within the tile
             if (col0 >= nvalid) break;          // warp-uniform
             uint32_t raw[kOzLevels][8];
 #pragma unroll

@@ -62,6 +62,26 @@ __device__ __forceinline__ void st_pair(const StencilD<T>& st, const T* Y, T& g0
     g1 = b;
 }
 
+// Two pairs at once (windows YA and YB), their four FMA chains interleaved;
+// each value is summed in the order of st_pair.
+template <typename T, int P, int BF>
+__device__ __forceinline__ void st_pair2(const StencilD<T>& st, const T* YA, const T* YB, T& a0, T& a1, T& b0, T& b1) {
+    constexpr int NB = P + 2;
+    T x0 = 0, x1 = 0, z0 = 0, z1 = 0;
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+        const T ya = YA[t], yb = YB[t];
+        x0 = fmaT(st.bf[BF][0][t], ya, x0);
+        x1 = fmaT(st.bf[BF][1][t], ya, x1);
+        z0 = fmaT(st.bf[BF][0][t], yb, z0);
+        z1 = fmaT(st.bf[BF][1][t], yb, z1);
+    }
+    a0 = x0;
+    a1 = x1;
+    b0 = z0;
+    b1 = z1;
+}
+
 template <typename T, int P>
 __device__ __forceinline__ void st_seg(const T* w, const T* H, T* To) {
     constexpr int NW = 2 * P + 1, WIN = 2 * (kSeg - 1) + NW;
@@ -164,18 +184,22 @@ __device__ __forceinline__ void st_trial(const XArgs<T>& a, const StencilD<T>& s
             load6(k0 + 64, cn[0]);
             load6(k0 + 96, cn[1]);
         }
+        // both pairs of this pass together (the second's window clamped to the
+        // first's where it lies beyond the line; its results are not stored)
+        if (k0 + lane >= npairs) break;
+        const bool okB = k0 + 32 + lane < npairs;
+        T g[2][2];
+        st_pair2<T, P, BF>(st, Yl + k0, Yl + k0 + (okB ? 32 : 0), g[0][0], g[0][1], g[1][0], g[1][1]);
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            if (k0 + 32 * h + lane >= npairs) break;
-            T g0, g1;
-            st_pair<T, P, BF>(st, Yl + k0 + 32 * h, g0, g1);
+            if (h == 1 && !okB) break;
             T* H = Hl + 2 * (k0 + 32 * h);
-            H[0] = c[h][0] * g0;
-            H[1] = c[h][1] * g1;
-            H[kStLines * rG] = c[h][2] * g0;
-            H[kStLines * rG + 1] = c[h][3] * g1;
-            H[2 * kStLines * rG] = c[h][4] * g0;
-            H[2 * kStLines * rG + 1] = c[h][5] * g1;
+            H[0] = c[h][0] * g[h][0];
+            H[1] = c[h][1] * g[h][1];
+            H[kStLines * rG] = c[h][2] * g[h][0];
+            H[kStLines * rG + 1] = c[h][3] * g[h][1];
+            H[2 * kStLines * rG] = c[h][4] * g[h][0];
+            H[2 * kStLines * rG + 1] = c[h][5] * g[h][1];
         }
     }
     // boundary points (band tables)
