@@ -335,10 +335,40 @@ __device__ __forceinline__ void st_trial_otf(const XArgs<float>& a, const Stenci
     }
 }
 
+// Boundary outputs of the test side (outside the segments of kSeg): the
+// interior's leading outputs i < i_lo and those from the last full segment on.
+__host__ __device__ inline int st_bnd_count(int i_lo, int i_hi, int n1) {
+    const int nseg = (i_hi - i_lo) / kSeg;
+    return i_lo + (n1 - (i_lo + nseg * kSeg));
+}
+constexpr int kStBndMax = 32;  // boundary outputs with their weights staged in shared memory (more: global tables)
+
+// Stages the W bands of the boundary outputs, all four families, zero-padded
+// to kBndW<P> taps: sW [4][nb][kBndW<P>], then starts and lengths [2][nb] as ints.
+template <typename T, int P>
+__device__ __forceinline__ void st_bnd_load(const XArgs<T>& a, const StencilD<T>& st, T* sW) {
+    constexpr int KB = kBndW<P>;
+    const int n1 = a.n1, nb = st_bnd_count(st.i_lo, st.i_hi, n1);
+    const int i_st = n1 - (nb - st.i_lo);
+    int* sSL = reinterpret_cast<int*>(sW + 4 * nb * KB);
+    for (int e = threadIdx.x; e < 4 * nb * KB; e += blockDim.x) {
+        const int f = e / (nb * KB), r = e - f * nb * KB, b = r / KB, t = r - b * KB;
+        const int i = b < st.i_lo ? b : i_st + (b - st.i_lo);
+        sW[e] = t < a.W.len[i] ? a.W.lane(f, i, t) : T(0);
+    }
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const int i = b < st.i_lo ? b : i_st + (b - st.i_lo);
+        sSL[b] = a.W.start[i];
+        sSL[nb + b] = a.W.len[i];
+    }
+}
+
 // Test side of one beta: the 24 rows (alpha, line) of H against the WQ
-// weights of their family, outputs into sT.
+// weights of their family, outputs into sT.  sW: the boundary weights staged
+// by st_bnd_load (nullptr: read from the band tables).
 template <typename T, int P, int BETA>
-__device__ __forceinline__ void st_test(const XArgs<T>& a, const StencilD<T>& st, const T* sH, T* sT, int rG, int rT) {
+__device__ __forceinline__ void st_test(const XArgs<T>& a, const StencilD<T>& st, const T* sH, T* sT, int rG, int rT,
+                                        const T* sW = nullptr) {
     constexpr int BF = BETA == 0 ? 1 : 0;
     constexpr int NW = 2 * P + 1;
     const int n1 = a.n1;
@@ -396,13 +426,23 @@ __device__ __forceinline__ void st_test(const XArgs<T>& a, const StencilD<T>& st
         const int k = it / (3 * kStLines), row = it - k * (3 * kStLines);
         const int i = k < st.i_lo ? k : i_st + (k - st.i_lo);
         const int fam = row < kStLines ? 2 + BF : BF;  // alpha = 1 tests the derivative
-        const int s0 = a.W.start[i], L = a.W.len[i];
-        const T* Hr = sH + row * rG + s0;
         T acc = 0;
+        if (sW) {
+            const int* sSL = reinterpret_cast<const int*>(sW + 4 * nbi * kBndW<P>);
+            const int s0 = sSL[k], L = sSL[nbi + k];
+            const T* w = sW + (fam * nbi + k) * kBndW<P>;
+            const T* Hr = sH + row * rG + s0;
 #pragma unroll
-        for (int t = 0; t < kBndW<P>; ++t)
-            if (t < L) acc = fmaT(a.W.lane(fam, i, t), Hr[t], acc);
-        for (int t = kBndW<P>; t < L; ++t) acc = fmaT(a.W.lane(fam, i, t), Hr[t], acc);
+            for (int t = 0; t < kBndW<P>; ++t)
+                if (t < L) acc = fmaT(w[t], Hr[t], acc);
+        } else {
+            const int s0 = a.W.start[i], L = a.W.len[i];
+            const T* Hr = sH + row * rG + s0;
+#pragma unroll
+            for (int t = 0; t < kBndW<P>; ++t)
+                if (t < L) acc = fmaT(a.W.lane(fam, i, t), Hr[t], acc);
+            for (int t = kBndW<P>; t < L; ++t) acc = fmaT(a.W.lane(fam, i, t), Hr[t], acc);
+        }
         sT[row * rT + i] = acc;
     }
 }

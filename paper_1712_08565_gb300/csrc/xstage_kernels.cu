@@ -25,6 +25,9 @@ using stx::st_load_y;
 using stx::st_stride;
 using stx::st_test;
 using stx::st_trial;
+using stx::st_bnd_load;
+using stx::st_bnd_count;
+using stx::kStBndMax;
 
 // Forward x stage: Y (3 inputs [line][n1]) -> T (9 outputs [line][n1]).
 // The nine products are formed three at a time, one trial direction beta at a
@@ -472,7 +475,8 @@ __device__ __forceinline__ void st_copy_out(int n1, int line0, int nl, const T* 
 template <typename T, int P>
 __global__ void __launch_bounds__(kThreads) k_xstage_stencil(XArgs<T> a, StencilD<T> st, const T* __restrict__ y0,
                                                              const T* __restrict__ y1, const T* __restrict__ y2,
-                                                             T* __restrict__ tout, size_t tstride, const int* skip) {
+                                                             T* __restrict__ tout, size_t tstride, int bnd,
+                                                             const int* skip) {
     if (skip && *skip) return;
     const int line0 = blockIdx.x * kStLines;
     const int nl = min(kStLines, a.nlines - line0);
@@ -489,6 +493,9 @@ __global__ void __launch_bounds__(kThreads) k_xstage_stencil(XArgs<T> a, Stencil
     T* sT = sY + kStLines * st_stride(n1);              // [3 alpha][8][rT]: staged outputs of one beta
     T* sH = sT + 3 * kStLines * st_stride(n1);          // [3 alpha][8][rG]
     const int rY = st_stride(n1), rT = st_stride(n1), rG = st_stride(a.nq1);
+    // boundary weights of the test side, staged once for the block's three betas
+    T* sW = bnd ? sH + 3 * kStLines * rG : nullptr;
+    if (bnd) st_bnd_load<T, P>(a, st, sW);
     st_load_y(y0, n1, line0, nl, sY, rY);
     ptx::cp_async_commit();
     ptx::cp_async_wait_all();
@@ -497,7 +504,7 @@ __global__ void __launch_bounds__(kThreads) k_xstage_stencil(XArgs<T> a, Stencil
     __syncthreads();
     st_load_y(y1, n1, line0, nl, sY, rY);
     ptx::cp_async_commit();
-    st_test<T, P, 0>(a, st, sH, sT, rG, rT);
+    st_test<T, P, 0>(a, st, sH, sT, rG, rT, sW);
     ptx::cp_async_wait_all();
     __syncthreads();
     st_copy_out<T, 0>(n1, line0, nl, sT, tout, tstride);
@@ -505,15 +512,26 @@ __global__ void __launch_bounds__(kThreads) k_xstage_stencil(XArgs<T> a, Stencil
     __syncthreads();
     st_load_y(y2, n1, line0, nl, sY, rY);
     ptx::cp_async_commit();
-    st_test<T, P, 1>(a, st, sH, sT, rG, rT);
+    st_test<T, P, 1>(a, st, sH, sT, rG, rT, sW);
     ptx::cp_async_wait_all();
     __syncthreads();
     st_copy_out<T, 1>(n1, line0, nl, sT, tout, tstride);
     st_trial<T, P, 2>(a, st, line0, nl, sY, sH, rY, rG);
     __syncthreads();
-    st_test<T, P, 2>(a, st, sH, sT, rG, rT);
+    st_test<T, P, 2>(a, st, sH, sT, rG, rT, sW);
     __syncthreads();
     st_copy_out<T, 2>(n1, line0, nl, sT, tout, tstride);
+}
+
+constexpr size_t kStencilSmemCap = 227 * 1024;  // opt-in shared memory per block
+
+// Shared memory for the staged boundary weights of the stencil test side
+// (st_bnd_load), 0 when there are more than kStBndMax boundary outputs.
+template <typename T>
+size_t stencil_bnd_bytes(const StencilD<T>& S, int n1) {
+    const int nb = st_bnd_count(S.i_lo, S.i_hi, n1);
+    if (nb > kStBndMax) return 0;
+    return (size_t)4 * nb * (3 * S.P + 1) * sizeof(T) + (size_t)2 * nb * sizeof(int);
 }
 
 // The same x stage with the coefficient evaluated in the block (CoeffField):
@@ -608,14 +626,18 @@ template <typename T>
 void launch_stencil(const StencilD<T>& S, int nlines, size_t sm, cudaStream_t st, const XArgs<T>& a, const T* y0,
                     const T* y1, const T* y2, T* tout, size_t tstride, const int* skip) {
     const dim3 grid((nlines + kStLines - 1) / kStLines);
+    size_t bb = stencil_bnd_bytes(S, a.n1);
+    if (sm + bb > kStencilSmemCap) bb = 0;  // the configured limit (configure_forward_xstage_smem)
+    const int bnd = bb > 0 ? 1 : 0;
+    sm += bb;
     switch (S.P) {
-        case 2: k_xstage_stencil<T, 2><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
-        case 3: k_xstage_stencil<T, 3><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
-        case 4: k_xstage_stencil<T, 4><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
-        case 5: k_xstage_stencil<T, 5><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
-        case 6: k_xstage_stencil<T, 6><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
-        case 7: k_xstage_stencil<T, 7><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
-        case 8: k_xstage_stencil<T, 8><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, skip); break;
+        case 2: k_xstage_stencil<T, 2><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, bnd, skip); break;
+        case 3: k_xstage_stencil<T, 3><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, bnd, skip); break;
+        case 4: k_xstage_stencil<T, 4><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, bnd, skip); break;
+        case 5: k_xstage_stencil<T, 5><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, bnd, skip); break;
+        case 6: k_xstage_stencil<T, 6><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, bnd, skip); break;
+        case 7: k_xstage_stencil<T, 7><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, bnd, skip); break;
+        case 8: k_xstage_stencil<T, 8><<<grid, kThreads, sm, st>>>(a, S, y0, y1, y2, tout, tstride, bnd, skip); break;
         default: break;  // unreachable: the stencil tables exist only for P <= kStencilMaxP (checked at dispatch)
     }
 }
@@ -671,7 +693,7 @@ cudaError_t launch_forward_xstage(const OpCtx<T>& c, const XArgs<T>& a, const T*
 }
 
 int xstage_smem_bytes(int elem_size, int n1, int nq1, int lines, int mode) {
-    if (mode == 6)  // stencil: Y rows of 8 lines, staged outputs and H rows of 8 lines x 3 alpha
+    if (mode == 6)  // stencil: Y rows of 8 lines, staged outputs and H rows of 8 lines x 3 alpha (+ boundary weights)
         return (int)((size_t)kStLines * (4 * (size_t)st_stride(n1) + 3 * (size_t)st_stride(nq1)) * elem_size);
     if (mode >= 4) {  // tiled: two lines-innermost slabs of 3 x (rows + 4) padded rows
         const int pr = 128 / (kTileLines * elem_size), pad = 16 / elem_size;
@@ -748,8 +770,13 @@ cudaError_t configure_forward_xstage_smem(int bytes) {
     cudaError_t e = set_xstage_smem_all<0>(bytes);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_xstage_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess) e = set_xstage_smem_all<1>(bytes);
-    if (e == cudaSuccess) e = set_stencil_smem<float>(bytes);
-    if (e == cudaSuccess) e = set_stencil_smem<double>(bytes);
+    // the stencil kernels also stage their boundary weights (at most kStBndMax outputs of 3 P + 1 taps, 4 families)
+    auto with_bnd = [&](int elem) {
+        const size_t b = (size_t)bytes + (size_t)4 * kStBndMax * (3 * kStencilMaxP + 1) * elem + 2 * kStBndMax * 4;
+        return (int)std::min<size_t>(b, kStencilSmemCap);
+    };
+    if (e == cudaSuccess) e = set_stencil_smem<float>(with_bnd(4));
+    if (e == cudaSuccess) e = set_stencil_smem<double>(with_bnd(8));
     return e;
 }
 
