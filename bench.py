@@ -651,8 +651,20 @@ def batched(mf, device):
     torch.cuda.synchronize()
     tm = time.perf_counter() - t0
     merr = max(float(torch.linalg.vector_norm(u - v) / torch.linalg.vector_norm(v)) for u, v in zip(us, u64))
-    # the grouped FP64 sweep: one launch per kernel stage over each of 4 groups of patches; its kernels
-    # are the FP64-pipe FD's, so it is compared with the per-patch streams on that FD
+    # the grouped FP64 sweep: one launch per kernel stage over each of 4 groups of patches, with the
+    # split FD (the default) and then with the FP64-pipe FD beside the per-patch streams on that FD
+    b.set_grouped(4)
+    ugs = [torch.empty_like(f) for f in fs]
+    b.solve(fs, ugs, rtol=BATCH["rtol"], force_fp64=True)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, gsinfos = b.solve(fs, ugs, rtol=BATCH["rtol"], force_fp64=True)
+    torch.cuda.synchronize()
+    tgs = time.perf_counter() - t0
+    gs_ran = b.grouped
+    gs_equal = all(torch.equal(a, c) for a, c in zip(ugs, u64))
+    b.set_grouped(0)
+    del ugs
     for op in ops:
         op.fd64_path = "pipe"
     b.solve(fs, us, rtol=BATCH["rtol"], force_fp64=True)  # warm-up
@@ -693,7 +705,9 @@ def batched(mf, device):
            "all_converged": all(i.converged for i in infos),
            "apply_dof_per_s": sum(2 * i.iterations * op.N for i, op in zip(infos, ops)) / tb,
            "autotuned_xstage": {str(k): v for k, v in sorted(lines.items())},
-           "fd64_path": "split", "batched_s_pipe_fd": tp,
+           "fd64_path": "split", "grouped_4_s": tgs, "grouped_split_ran": gs_ran,
+           "grouped_split_bitwise_equal_to_streams": gs_equal,
+           "grouped_split_all_converged": all(i.converged for i in gsinfos), "batched_s_pipe_fd": tp,
            "grouped_4_s_pipe_fd": tg, "grouped_ran": g_ran, "grouped_bitwise_equal_to_streams": g_equal,
            "grouped_all_converged": all(i.converged for i in ginfos)}
     b.close()

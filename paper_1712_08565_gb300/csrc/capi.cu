@@ -1684,7 +1684,8 @@ int build_grouped_sweep(mfwq_batch b, const std::vector<PatchOps>& ops, const do
             ok = grouped_launch_krylov(kind, tab, stride[k], n, grid[g][k], smem[k], sg) ||
                  grouped_launch_fd(kind, tab, stride[k], n, grid[g][k], smem[k], sg) ||
                  grouped_launch_apply(kind, tab, stride[k], n, grid[g][k], smem[k], sg) ||
-                 grouped_launch_xstage(kind, tab, stride[k], n, grid[g][k], smem[k], sg);
+                 grouped_launch_xstage(kind, tab, stride[k], n, grid[g][k], smem[k], sg) ||
+                 grouped_launch_oz(kind, tab, stride[k], n, grid[g][k], smem[k], sg);
         }
         if (ok) ok = cudaEventRecord(b->join[g], sg) == cudaSuccess && cudaStreamWaitEvent(b->origin, b->join[g], 0) == cudaSuccess;
     }

@@ -164,68 +164,87 @@ __device__ __forceinline__ double oz_combine(const float* v, int scale) {
 
 // ---- slicing pre-pass: one warp per (padded) row of A, lane l holds
 // elements 8 l .. 8 l + 7 (one 16-byte core-matrix row per slice)
-__global__ void __launch_bounds__(256) k_oz_slice(const double* __restrict__ A, int R, int n_in, int kch, int rows_pad,
-                                                  uint16_t* __restrict__ sl, int* __restrict__ aexp, const int* skip) {
-    if (skip && *skip) return;
+struct OzSliceArgs {
+    const double* A;  // [R][n_in]
+    int R, n_in, kch, rows_pad;
+    uint16_t* sl;     // slice blocks (OzPlan::asl)
+    int* aexp;        // row exponents
+};
+
+// Block blk of 256 threads: rows 8 blk .. 8 blk + 7.  No early return: the
+// grouped launch runs it between block-wide barriers.
+__device__ __forceinline__ void oz_slice_body(const OzSliceArgs& a, int blk) {
     const int lane = threadIdx.x & 31;
-    const int row = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5);
-    if (row >= rows_pad) return;
-    const int t0 = 8 * lane;
-    const bool active = t0 < kch * kOzKC;  // lanes beyond the padded K write nothing
-    unsigned long long b[8];
+    const int row = blk * 8 + (int)(threadIdx.x >> 5);
+    if (row < a.rows_pad) {
+        const int t0 = 8 * lane;
+        unsigned long long b[8];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) b[i] = 0ull;
-    if (row < R && t0 < n_in) {
-        const double* p = A + (size_t)row * n_in + t0;
-        if (t0 + 8 <= n_in && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        for (int i = 0; i < 8; ++i) b[i] = 0ull;
+        if (row < a.R && t0 < a.n_in) {
+            const double* p = a.A + (size_t)row * a.n_in + t0;
+            if (t0 + 8 <= a.n_in && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const double2 v = __ldg(reinterpret_cast<const double2*>(p) + i);
-                b[2 * i] = (unsigned long long)__double_as_longlong(v.x);
-                b[2 * i + 1] = (unsigned long long)__double_as_longlong(v.y);
+                for (int i = 0; i < 4; ++i) {
+                    const double2 v = __ldg(reinterpret_cast<const double2*>(p) + i);
+                    b[2 * i] = (unsigned long long)__double_as_longlong(v.x);
+                    b[2 * i + 1] = (unsigned long long)__double_as_longlong(v.y);
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (t0 + i < a.n_in) b[i] = (unsigned long long)__double_as_longlong(__ldg(p + i));
             }
-        } else {
+        }
+        int e = 0;
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-                if (t0 + i < n_in) b[i] = (unsigned long long)__double_as_longlong(__ldg(p + i));
+        for (int i = 0; i < 8; ++i) e = max(e, (int)((b[i] >> 52) & 0x7FF));
+        const int emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+        if (lane == 0) a.aexp[row] = emax;
+        if (t0 < a.kch * kOzKC) {  // lanes beyond the padded K write nothing
+            uint32_t xh[8], xl[8];
+            float sg[8], sc[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const uint64_t X = oz_fixed(b[i], emax);
+                xh[i] = (uint32_t)(X >> 32);
+                xl[i] = (uint32_t)X;
+                const bool ng = (b[i] >> 63) != 0ull;
+                sg[i] = ng ? -1.f : 1.f;
+                sc[i] = ng ? 8388608.f : -8388608.f;
+            }
+            const int mt = row / kOzTileM, rr = row - mt * kOzTileM, kc = t0 / kOzKC;
+            unsigned char* blkp =
+                reinterpret_cast<unsigned char*>(a.sl) + ((size_t)mt * a.kch + kc) * kOzStageA + oz_off(rr, t0 % kOzKC);
+            auto put = [&](auto S_tag) {
+                constexpr int S = decltype(S_tag)::value;
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    w[q] = oz_pack2(oz_slice<S>(xh[2 * q], xl[2 * q]), sg[2 * q], sc[2 * q],
+                                    oz_slice<S>(xh[2 * q + 1], xl[2 * q + 1]), sg[2 * q + 1], sc[2 * q + 1]);
+                *reinterpret_cast<uint4*>(blkp + S * kOzSliceA) = make_uint4(w[0], w[1], w[2], w[3]);
+            };
+            put(std::integral_constant<int, 0>{});
+            put(std::integral_constant<int, 1>{});
+            put(std::integral_constant<int, 2>{});
+            put(std::integral_constant<int, 3>{});
+            put(std::integral_constant<int, 4>{});
+            put(std::integral_constant<int, 5>{});
+            put(std::integral_constant<int, 6>{});
+            put(std::integral_constant<int, 7>{});
         }
     }
-    int e = 0;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) e = max(e, (int)((b[i] >> 52) & 0x7FF));
-    const int emax = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
-    if (lane == 0) aexp[row] = emax;
-    if (!active) return;
-    uint32_t xh[8], xl[8];
-    float sg[8], sc[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const uint64_t X = oz_fixed(b[i], emax);
-        xh[i] = (uint32_t)(X >> 32);
-        xl[i] = (uint32_t)X;
-        const bool ng = (b[i] >> 63) != 0ull;
-        sg[i] = ng ? -1.f : 1.f;
-        sc[i] = ng ? 8388608.f : -8388608.f;
-    }
-    const int mt = row / kOzTileM, rr = row - mt * kOzTileM, kc = t0 / kOzKC;
-    unsigned char* blk = reinterpret_cast<unsigned char*>(sl) + ((size_t)mt * kch + kc) * kOzStageA + oz_off(rr, t0 % kOzKC);
-    auto put = [&](auto S_tag) {
-        constexpr int S = decltype(S_tag)::value;
-        uint32_t w[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            w[q] = oz_pack2(oz_slice<S>(xh[2 * q], xl[2 * q]), sg[2 * q], sc[2 * q], oz_slice<S>(xh[2 * q + 1], xl[2 * q + 1]),
-                            sg[2 * q + 1], sc[2 * q + 1]);
-        *reinterpret_cast<uint4*>(blk + S * kOzSliceA) = make_uint4(w[0], w[1], w[2], w[3]);
-    };
-    put(std::integral_constant<int, 0>{});
-    put(std::integral_constant<int, 1>{});
-    put(std::integral_constant<int, 2>{});
-    put(std::integral_constant<int, 3>{});
-    put(std::integral_constant<int, 4>{});
-    put(std::integral_constant<int, 5>{});
-    put(std::integral_constant<int, 6>{});
-    put(std::integral_constant<int, 7>{});
+}
+
+__global__ void __launch_bounds__(256) k_oz_slice(OzSliceArgs a, const int* skip) {
+    if (skip && *skip) return;
+    oz_slice_body(a, (int)blockIdx.x);
+}
+
+// The slicing passes of a batch's patches in one launch (grouped.h).
+__global__ void __launch_bounds__(256) k_oz_slice_grouped(const unsigned char* __restrict__ tab, int stride, int npatch) {
+    grouped_for<OzSliceArgs, false>(tab, stride, npatch, [](const OzSliceArgs& a, int it) { oz_slice_body(a, it); });
 }
 
 struct OzArgs {
@@ -238,6 +257,63 @@ struct OzArgs {
     int* err;
     const int* skip;
 };
+
+// Epilogue of one work item: warp w reads TMEM lanes 32 (w % 4) .. + 31 and a
+// quarter of the tile's columns, combines the 8 level sums of each output into
+// FP64 and stores it (times the scaling table in the scaling pass).
+__device__ __forceinline__ void oz_epilogue(const OzArgs& a, uint32_t tmem, int row0, int nt, int nvalid) {
+    constexpr int kColsPerWarp = kOzNT / (kOzThreads / 128);  // 16
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = warp & 3, hc = warp >> 2;
+    const int er = q * 32 + lane;  // this thread's TMEM lane = tile row
+    const int grow = row0 + er;
+    const int erow = __ldg(a.aexp + row0 + er);
+    const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hc * kColsPerWarp);
+#pragma unroll 1
+    for (int cg = 0; cg < kColsPerWarp / 8; ++cg) {
+        const int col0 = hc * kColsPerWarp + cg * 8;  // column within the tile
+        if (col0 >= nvalid) break;                     // warp-uniform
+        uint32_t raw[kOzLevels][8];
+#pragma unroll
+        for (int l = 0; l < kOzLevels; ++l) tmem_ld8_nowait(tbase + (uint32_t)(l * kOzNT + cg * 8), raw[l]);
+        tmem_wait_ld();
+        if (grow < a.R) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int col = col0 + j;
+                if (col >= nvalid) continue;
+                const int o = nt * kOzNT + col;
+                float v[kOzLevels];
+#pragma unroll
+                for (int l = 0; l < kOzLevels; ++l) v[l] = __uint_as_float(raw[l][j]);
+                double d = oz_combine(v, erow + __ldg(a.B.fexp + o));
+                const size_t oi = (size_t)o * a.R + grow;
+                if (a.dinv) d *= __ldg(a.dinv + oi);
+                a.Out[oi] = d;
+            }
+        }
+    }
+}
+
+// The slice-pair products of one K chunk (stage at abase / bbase) into the
+// TMEM blocks of their levels (thread 0); the first chunk of an item overwrites.
+__device__ __forceinline__ void oz_mma_chunk(uint32_t tmem, uint32_t abase, uint32_t bbase, uint32_t idesc, bool first) {
+    const uint64_t ad0 = make_desc(abase, 128, kOzSBO), bd0 = make_desc(bbase, 128, kOzSBO);
+#pragma unroll
+    for (int L = 2; L <= kOzSlices + 1; ++L) {
+        const uint32_t td = tmem + (uint32_t)((L - 2) * kOzNT);
+#pragma unroll
+        for (int si = 1; si < L; ++si) {
+#pragma unroll
+            for (int kk = 0; kk < kOzKC / 16; ++kk) {
+                // descriptor start addresses advance in 16-byte units
+                const uint64_t ad = ad0 + (uint64_t)(((si - 1) * kOzSliceA + kk * 256) >> 4);
+                const uint64_t bd = bd0 + (uint64_t)(((L - si - 1) * kOzSliceB + kk * 256) >> 4);
+                mma_bf16(td, ad, bd, idesc, (!first || si > 1 || kk > 0) ? 1u : 0u);
+            }
+        }
+    }
+}
 
 // ---- products: thread 0 streams the slice blocks of A and Bm by bulk copies
 // (one chunk ahead) and issues the MMAs; all warps run the epilogue.
@@ -308,21 +384,7 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_fd_oz(OzArgs a) {
                 }
                 tc_fence_after();
                 const uint32_t abase = smem_u32(smem + s * kOzStage), bbase = abase + kOzStageA;
-                const uint64_t ad0 = make_desc(abase, 128, kOzSBO), bd0 = make_desc(bbase, 128, kOzSBO);
-#pragma unroll
-                for (int L = 2; L <= kOzSlices + 1; ++L) {
-                    const uint32_t td = tmem + (uint32_t)((L - 2) * kOzNT);
-#pragma unroll
-                    for (int si = 1; si < L; ++si) {
-#pragma unroll
-                        for (int kk = 0; kk < kOzKC / 16; ++kk) {
-                            // descriptor start addresses advance in 16-byte units
-                            const uint64_t ad = ad0 + (uint64_t)(((si - 1) * kOzSliceA + kk * 256) >> 4);
-                            const uint64_t bd = bd0 + (uint64_t)(((L - si - 1) * kOzSliceB + kk * 256) >> 4);
-                            mma_bf16(td, ad, bd, idesc, (c > 0 || si > 1 || kk > 0) ? 1u : 0u);
-                        }
-                    }
-                }
+                oz_mma_chunk(tmem, abase, bbase, idesc, c == 0);
                 mma_commit(smem_u32(&done[s]));
                 ++committed;
                 if (g + kOzStages - 1 < total && !issue(g + kOzStages - 1)) {
@@ -342,41 +404,119 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_fd_oz(OzArgs a) {
             break;
         }
         tc_fence_after();
-        constexpr int kColsPerWarp = kOzNT / (kOzThreads / 128);  // 16
-        const int q = warp & 3, hc = warp >> 2;
-        const int er = q * 32 + lane;  // this thread's TMEM lane = tile row
-        const int grow = row0 + er;
-        const int erow = __ldg(a.aexp + row0 + er);
-        const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(hc * kColsPerWarp);
-#pragma unroll 1
-        for (int cg = 0; cg < kColsPerWarp / 8; ++cg) {
-            const int col0 = hc * kColsPerWarp + cg * 8;  // column within the tile
-            if (col0 >= nvalid) break;          // warp-uniform
-            uint32_t raw[kOzLevels][8];
-#pragma unroll
-            for (int l = 0; l < kOzLevels; ++l) tmem_ld8_nowait(tbase + (uint32_t)(l * kOzNT + cg * 8), raw[l]);
-            tmem_wait_ld();
-            if (grow < a.R) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const int col = col0 + j;
-                    if (col >= nvalid) continue;
-                    const int o = nt * kOzNT + col;
-                    float v[kOzLevels];
-#pragma unroll
-                    for (int l = 0; l < kOzLevels; ++l) v[l] = __uint_as_float(raw[l][j]);
-                    double d = oz_combine(v, erow + __ldg(a.B.fexp + o));
-                    const size_t oi = (size_t)o * a.R + grow;
-                    if (a.dinv) d *= __ldg(a.dinv + oi);
-                    a.Out[oi] = d;
-                }
-            }
-        }
+        oz_epilogue(a, tmem, row0, nt, nvalid);
         tc_fence_before();
         __syncthreads();  // TMEM is read: the next item's products may overwrite it
     }
     if (!ok && tid == 0) atomicExch(a.err, 1);
     // drain: products and copies in flight must land before TMEM and shared memory go away
+    if (tid == 0) {
+        if (committed > 0) {
+            const int gl = committed - 1;
+            mbar_wait(smem_u32(&done[gl % kOzStages]), (uint32_t)((gl / kOzStages) & 1));
+        }
+        for (int q2 = committed; q2 < issued; ++q2)
+            mbar_wait(smem_u32(&full[q2 % kOzStages]), (uint32_t)((q2 / kOzStages) & 1));
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kOzTmemCols));
+    }
+}
+
+// The product passes of a batch's patches in one launch (grouped.h): the
+// CTAs walk every live patch's work items (table of OzArgs); per item thread 0
+// starts its first chunks' copies, consumes the chunks in order with the
+// copies of later chunks kept up to three ahead, and all warps run the
+// epilogue.  Chunks are counted over the whole launch for the stage barriers.
+__global__ void __launch_bounds__(kOzThreads, 1) k_fd_oz_grouped(const unsigned char* __restrict__ tab, int stride,
+                                                               int npatch) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kOzStages * kOzStage);
+    uint64_t* done = full + kOzStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + kOzStages);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kOzTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kOzStages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&done[s]), 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    int issued = 0, g = 0, committed = 0;  // thread 0: chunk copies started, consumed, committed
+    bool ok = true;
+    int* err = nullptr;
+    grouped_for<OzArgs, false>(tab, stride, npatch, [&](const OzArgs& a, int item) {
+        if (!ok) return;  // uniform: set from a block-wide vote
+        err = a.err;
+        const int ntl = a.B.n_tiles, kch = a.B.k_chunks;
+        const int mt = item / ntl, nt = item - mt * ntl;
+        const int row0 = mt * kOzTileM;
+        const int nvalid = min(kOzNT, a.B.n_out - nt * kOzNT);
+        if (tid == 0) {
+            // chunk c of this item into stage issued % kOzStages, once that stage's previous products finished
+            auto issue = [&](int c) -> bool {
+                const int q = issued, s = q % kOzStages, use = q / kOzStages;
+                if (use >= 1 && !mbar_wait(smem_u32(&done[s]), (uint32_t)((use - 1) & 1))) return false;
+                unsigned char* sa = smem + s * kOzStage;
+                mbar_expect_tx(smem_u32(&full[s]), (uint32_t)kOzStage);
+                ptx::bulk_g2s(smem_u32(sa),
+                              reinterpret_cast<const unsigned char*>(a.Asl) + ((size_t)mt * kch + c) * kOzStageA,
+                              (uint32_t)kOzStageA, smem_u32(&full[s]));
+                ptx::bulk_g2s(smem_u32(sa + kOzStageA),
+                              reinterpret_cast<const unsigned char*>(a.B.sl) + ((size_t)nt * kch + c) * kOzStageB,
+                              (uint32_t)kOzStageB, smem_u32(&full[s]));
+                ++issued;
+                return true;
+            };
+            bool lok = true;
+            for (int c = 0; c < kOzStages - 1 && c < kch && lok; ++c) lok = issue(c);
+            const uint32_t idesc = idesc_bf16((nvalid + 15) & ~15);
+            for (int c = 0; c < kch && lok; ++c, ++g) {
+                const int s = g % kOzStages, use = g / kOzStages;
+                if (!mbar_wait(smem_u32(&full[s]), (uint32_t)(use & 1))) {
+                    lok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t abase = smem_u32(smem + s * kOzStage), bbase = abase + kOzStageA;
+                oz_mma_chunk(tmem, abase, bbase, idesc, c == 0);
+                mma_commit(smem_u32(&done[s]));
+                ++committed;
+                if (c + kOzStages - 1 < kch && !issue(c + kOzStages - 1)) {
+                    lok = false;
+                    ++g;
+                    break;
+                }
+            }
+            if (lok) {
+                const int gl = g - 1;
+                if (!mbar_wait(smem_u32(&done[gl % kOzStages]), (uint32_t)((gl / kOzStages) & 1))) lok = false;
+            }
+            ok = lok;
+        }
+        if (!__syncthreads_and(ok ? 1 : 0)) {
+            ok = false;
+            return;
+        }
+        tc_fence_after();
+        oz_epilogue(a, tmem, row0, nt, nvalid);
+        tc_fence_before();
+        __syncthreads();  // TMEM is read: the next item's products may overwrite it
+    });
+    if (!ok && tid == 0 && err) atomicExch(err, 1);
     if (tid == 0) {
         if (committed > 0) {
             const int gl = committed - 1;
@@ -447,7 +587,8 @@ int configure_fd_oz() {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return MFWQ_ECUDA;
     if (cudaDeviceGetAttribute(&g_oz_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MFWQ_ECUDA;
-    if (cudaFuncSetAttribute(k_fd_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_fd_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_fd_oz_grouped, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem) != cudaSuccess)
         return MFWQ_ECUDA;
     return MFWQ_OK;
 }
@@ -535,18 +676,20 @@ int oz_pass(const OzPlan& p, const OzMat& B, const double* A, double* Out, int R
     a.R = R;
     a.err = err;
     a.skip = skip;
-    if (g_rec) {  // no grouped form: a batch with this path runs its patches on streams
-        g_rec->unsupported = true;
-        return MFWQ_OK;
-    }
     const int mtiles = (R + kOzTileM - 1) / kOzTileM;
     const int items = mtiles * B.n_tiles;
+    const int rows_pad = mtiles * kOzTileM;
+    const OzSliceArgs sa{A, R, B.n_in, B.k_chunks, rows_pad, p.asl, p.aexp};
+    if (g_rec) {  // the batch's grouped sweep runs both passes over all its patches
+        record_launch(GK_OZ_SLICE, sa, (rows_pad + 7) / 8, 256, 0, skip);
+        record_launch(GK_OZ_PROD, a, items, kOzThreads, kOzSmem, skip);
+        return MFWQ_OK;
+    }
     int grid = g_oz_sms > 0 ? g_oz_sms : 148;
     if (grid > items) grid = items;
     if (grid < 1) grid = 1;
-    const int rows_pad = mtiles * kOzTileM;
     launch_begin(S_FD_OZ, s);
-    k_oz_slice<<<(rows_pad + 7) / 8, 256, 0, s>>>(A, R, B.n_in, B.k_chunks, rows_pad, p.asl, p.aexp, skip);
+    k_oz_slice<<<(rows_pad + 7) / 8, 256, 0, s>>>(sa, skip);
     launch_end(S_FD_OZ, s);
     launch_begin(S_FD_OZ, s);
     k_fd_oz<<<grid, kOzThreads, kOzSmem, s>>>(a);
@@ -554,6 +697,20 @@ int oz_pass(const OzPlan& p, const OzMat& B, const double* A, double* Out, int R
     return cudaGetLastError() == cudaSuccess ? MFWQ_OK : MFWQ_ECUDA;
 }
 }  // namespace
+
+bool grouped_launch_oz(int kind, const unsigned char* tab, int stride, int npatch, int grid, int smem, cudaStream_t s) {
+    (void)smem;
+    if (kind == GK_OZ_SLICE) {
+        k_oz_slice_grouped<<<grid, 256, 0, s>>>(tab, stride, npatch);
+        return true;
+    }
+    if (kind == GK_OZ_PROD) {  // one CTA per SM (shared memory and TMEM)
+        const int sms = g_oz_sms > 0 ? g_oz_sms : 148;
+        k_fd_oz_grouped<<<grid < sms ? grid : sms, kOzThreads, kOzSmem, s>>>(tab, stride, npatch);
+        return true;
+    }
+    return false;
+}
 
 int run_fd_oz(const OzPlan& p, const double* r, double* z, double* tmp, int* err, const int* skip, cudaStream_t s) {
     if (!p.ok) return MFWQ_EINVAL;

@@ -29,6 +29,7 @@ enum GroupKind {
     GK_DENSE_SLOW, GK_DENSE_FAST,                                      // k_dense_slow/fast<double>
     GK_SLOW_TRIAL_Z, GK_SLOW_TRIAL_Y, GK_SLOW_TEST_Y, GK_SLOW_TEST_Z,  // k_slow<Op<double>, 1>
     GK_XSTAGE0,                                                        // k_xstage_apply<double, 4, 0, 0>
+    GK_OZ_SLICE, GK_OZ_PROD,                                           // k_oz_slice, k_fd_oz (split FP64 FD)
     GK_COUNT
 };
 
@@ -79,6 +80,7 @@ bool grouped_launch_fd(int kind, const unsigned char* tab, int stride, int npatc
 bool grouped_launch_apply(int kind, const unsigned char* tab, int stride, int npatch, int grid, int smem, cudaStream_t s);
 bool grouped_launch_xstage(int kind, const unsigned char* tab, int stride, int npatch, int grid, int smem,
                            cudaStream_t s);
+bool grouped_launch_oz(int kind, const unsigned char* tab, int stride, int npatch, int grid, int smem, cudaStream_t s);
 // Raises the dynamic shared-memory limit of the grouped kernels that take it.
 int configure_grouped_smem(int bytes);
 

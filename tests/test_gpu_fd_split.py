@@ -105,8 +105,9 @@ def test_split_fd_with_shift_and_solve(mf):
 
 
 def test_split_fd_in_a_batch(mf):
-    """Patches with the split FD solve on streams (no grouped form) and match
-    their separate solves bitwise."""
+    """Patches with the split FD: the per-patch streams and the grouped sweep
+    (one launch per stage over all patches, the split FD's slicing and product
+    passes included) both match the separate solves bitwise."""
     specs = [(2, (6, 7, 5)), (3, (9, 8, 7)), (4, (10, 6, 6))]
     ops, fs = [], []
     for p, nel in specs:
@@ -118,12 +119,18 @@ def test_split_fd_in_a_batch(mf):
         fs.append(op.load_vector("ring", "sines"))
     sep = [op.solve(f, rtol=1e-10)[0].cpu().numpy() for op, f in zip(ops, fs)]
     batch = mf.Batch(ops)
-    batch.set_grouped(True)
     us, infos = batch.solve(fs, rtol=1e-10)
     assert not batch.grouped
     for u, s_, info in zip(us, sep, infos):
         assert info.converged
         assert np.array_equal(u.cpu().numpy(), s_)
+    for groups in (1, 2):
+        batch.set_grouped(groups)
+        ug, ig = batch.solve(fs, rtol=1e-10)
+        assert batch.grouped
+        for u, s_, info in zip(ug, sep, ig):
+            assert info.converged
+            assert np.array_equal(u.cpu().numpy(), s_)
     batch.close()
     for op in ops:
         op.close()

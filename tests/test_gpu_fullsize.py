@@ -185,7 +185,14 @@ def test_batched_64_patches(mf):
     assert all(i.converged and i.rel_residual <= 1e-8 for i in infos)
     um, minfos = b.solve(fs, [torch.empty_like(f) for f in fs], rtol=1e-8)
     assert all(i.converged and i.rel_residual <= 1e-8 for i in minfos)
-    # the grouped sweep (4 concurrent groups, FP64-pipe FD): the same bits as the per-patch streams
+    # the grouped sweep (4 concurrent groups): the same bits as the per-patch streams, with the split FD
+    # (the default) and with the FP64-pipe FD
+    b.set_grouped(4)
+    us2, sinfos = b.solve(fs, [torch.empty_like(f) for f in fs], rtol=1e-8, force_fp64=True)
+    assert b.grouped
+    assert all(a.iterations == c.iterations for a, c in zip(sinfos, infos))
+    assert all(torch.equal(x, y) for x, y in zip(us2, us))
+    b.set_grouped(0)
     for op in ops:
         op.fd64_path = "pipe"
     up, pinfos = b.solve(fs, [torch.empty_like(f) for f in fs], rtol=1e-8, force_fp64=True)
