@@ -66,15 +66,53 @@ __device__ __forceinline__ void st_pairs(float* __restrict__ p, const float2* v)
     else *reinterpret_cast<float2*>(p) = v[0];
 }
 
+// Per-thread asynchronous copy of VW = 2 or 4 FP32 values (8 or 16 bytes, both
+// addresses aligned to the size) into shared memory; 16-byte copies bypass L1.
+template <int VW>
+__device__ __forceinline__ void cp_async_vec(void* dst, const float* src) {
+    const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst));
+    if constexpr (VW == 4)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(reinterpret_cast<uint64_t>(src)) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(reinterpret_cast<uint64_t>(src)) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Waits until at most N of this thread's committed copy groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait_pending() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Input rows a thread keeps in flight in the FP32 slow stages (its ring of
+// shared-memory slots): deep enough to cover the load latency with the few
+// warps the register use allows, small enough that the ring of the 9-input
+// test y stage leaves room for two blocks per SM.
+template <class Op>
+__host__ __device__ constexpr int slow_ring_stages() { return Op::NIN >= 8 ? 3 : 4; }
+
+// Shared memory of a k_slow_vec block: the band rows ([R][width][NF] (w, w)
+// pairs, padded to 16 bytes), then the ring of ST stages x NIN inputs x
+// kThreads vectors of VW values.
+template <class Op>
+size_t slow_vec_smem(int R, int width, int vw) {
+    const size_t band = sizeof(float2) * (((size_t)R * width * Op::NF + 1) & ~(size_t)1);
+    return band + sizeof(float) * (size_t)slow_ring_stages<Op>() * Op::NIN * kThreads * vw;
+}
+
 // The same stage with a thread owning VW = 2 or 4 consecutive columns (FP32,
-// C a multiple of VW): one vector load per input row and tensor, and the
+// C a multiple of VW): one vector copy per input row and tensor, and the
 // columns taken in pairs by the packed FP32 FMA (Op::fma2, each of its two
 // FMAs rounded as by fmaf).  The band weights sit in shared memory as
-// (w, w) pairs.  Every output is summed in the same order as by the
-// one-column form, so the results are bitwise the same.
+// (w, w) pairs.  The input rows reach the thread through its own ring of ST
+// shared-memory slots filled by cp.async, ST - 1 rows ahead of the row being
+// summed, so several rows' loads are in flight per thread without holding
+// registers (no block barrier: each thread reads only the slots it filled).
+// Every output is summed in the same order as by the one-column form, so the
+// results are bitwise the same.
 template <class Op, int R, int VW>
 __device__ __forceinline__ void slow_body_vec(const Op& op, const SlowGeom& g, int bx, int by, int gx, float2* sb) {
-    constexpr int NF = Op::NF, NIN = Op::NIN, NACC = Op::NACC, VP = VW / 2;
+    constexpr int NF = Op::NF, NIN = Op::NIN, NACC = Op::NACC, VP = VW / 2, ST = slow_ring_stages<Op>();
+    using Vec = std::conditional_t<VW == 4, float4, float2>;
     const int r0 = by * R;
     const int nr = min(R, g.Rout - r0);
     const int W = op.band.width;
@@ -99,6 +137,8 @@ __device__ __forceinline__ void slow_body_vec(const Op& op, const SlowGeom& g, i
         sb[e] = make_float2(v, v);
     }
     __syncthreads();
+    // this thread's ring: input i of slot st at [(st NIN + i) kThreads] (blocks of kThreads threads)
+    Vec* ring = reinterpret_cast<Vec*>(sb + ((R * W * NF + 1) & ~1)) + threadIdx.x;
     const size_t CV = (size_t)g.C / VW, ACV = (size_t)g.A * CV;
     for (size_t e = (size_t)bx * blockDim.x + threadIdx.x; e < ACV; e += (size_t)gx * blockDim.x) {
         const size_t a = e / CV, c = (e - a * CV) * VW;
@@ -110,14 +150,36 @@ __device__ __forceinline__ void slow_body_vec(const Op& op, const SlowGeom& g, i
 #pragma unroll
                 for (int m = 0; m < NACC; ++m) acc[k][v][m] = make_float2(0.f, 0.f);
         const size_t ib = a * g.Rin * (size_t)g.C + c;
-        for (int q = lo; q < hi; ++q) {
+        // row lo + j sits in slot j % ST; copy group j carries it (groups of rows
+        // past hi are empty), so before summing row lo + j at most ST - 1 of the
+        // ST + j groups committed so far may still be pending
+        auto fetch = [&](int q, int slot) {
+            const size_t off = ib + (size_t)q * g.C;
+            Vec* d = ring + slot * (NIN * kThreads);
+#pragma unroll
+            for (int i = 0; i < NIN; ++i) cp_async_vec<VW>(d + i * kThreads, op.in_ptr(i) + off);
+        };
+        const int nq = hi - lo;
+#pragma unroll
+        for (int j = 0; j < ST; ++j) {
+            if (j < nq) fetch(lo + j, j);
+            cp_async_commit_group();
+        }
+        int slot = 0;
+        for (int j = 0; j < nq; ++j) {
+            const int q = lo + j;
+            cp_async_wait_pending<ST - 1>();
             float2 x[VP][NIN];
+            const Vec* r = ring + slot * (NIN * kThreads);
 #pragma unroll
             for (int i = 0; i < NIN; ++i) {
-                float2 t[VP];
-                ld_pairs<VW>(op.in_ptr(i) + ib + (size_t)q * g.C, t);
-#pragma unroll
-                for (int v = 0; v < VP; ++v) x[v][i] = t[v];
+                const Vec t = r[i * kThreads];
+                if constexpr (VW == 4) {
+                    x[0][i] = make_float2(t.x, t.y);
+                    x[1][i] = make_float2(t.z, t.w);
+                } else {
+                    x[0][i] = t;
+                }
             }
 #pragma unroll
             for (int k = 0; k < R; ++k) {
@@ -128,6 +190,10 @@ __device__ __forceinline__ void slow_body_vec(const Op& op, const SlowGeom& g, i
                     for (int v = 0; v < VP; ++v) op.fma2(w, x[v], acc[k][v]);
                 }
             }
+            // the slot just read takes row q + ST (issue is in order: its reads are done)
+            if (j + ST < nq) fetch(q + ST, slot);
+            cp_async_commit_group();
+            slot = slot + 1 == ST ? 0 : slot + 1;
         }
 #pragma unroll
         for (int k = 0; k < R; ++k) {
@@ -489,6 +555,28 @@ struct HasVec : std::false_type {};
 template <class Op>
 struct HasVec<Op, std::void_t<decltype(Op::kVec)>> : std::true_type {};
 
+// Lets every k_slow_vec form of Op use up to 227 KB of dynamic shared memory
+// (the input rings need more than the default 48 KB), once per device.
+template <class Op>
+cudaError_t slow_vec_configure() {
+    static std::mutex mu;
+    static bool configured[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (configured[dev]) return cudaSuccess;
+    const int mx = 227 * 1024;
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_slow_vec<Op, 4, 4>, A, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slow_vec<Op, 2, 4>, A, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slow_vec<Op, 1, 4>, A, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slow_vec<Op, 4, 2>, A, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slow_vec<Op, 2, 2>, A, mx);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_slow_vec<Op, 1, 2>, A, mx);
+    if (e == cudaSuccess) configured[dev] = true;
+    return e;
+}
+
 template <class Op>
 cudaError_t launch_slow(int tag, const Op& op, int A, int Rin, int Rout, int C, const int* skip, cudaStream_t s,
                         int rows = 1, int vw = 1) {
@@ -516,7 +604,8 @@ cudaError_t launch_slow(int tag, const Op& op, int A, int Rin, int Rout, int C, 
             unsigned bx = (unsigned)((ACV + kThreads - 1) / kThreads);
             if (bx > 65535u) bx = 65535u;
             dim3 grid(bx, (Rout + R - 1) / R);
-            const size_t sm = sizeof(float2) * (size_t)R * op.band.width * Op::NF;
+            const size_t sm = slow_vec_smem<Op>(R, op.band.width, vw);
+            if (const cudaError_t ce = slow_vec_configure<Op>(); ce != cudaSuccess) return ce;
             launch_begin(tag, s);
             if (vw == 4) {
                 if (R == 4) k_slow_vec<Op, 4, 4><<<grid, kThreads, sm, s>>>(op, g, skip);
