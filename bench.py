@@ -613,10 +613,13 @@ def coeff_onthefly(mf, device):
     return res
 
 
-def batched(mf, device):
+def batched(mf, device, apply_rate=None):
     """64 independent ring patches of uneven degree and size, each with its own
     K = exp(0.3 g) field: one batched FP64 solve (one CUDA graph launch per
-    BiCGStab sweep) against the same solves run one after the other."""
+    BiCGStab sweep) against the same solves run one after the other.
+    apply_rate: {degree: apply DoF/s of a full-size single patch} (the p sweep);
+    with it the result also holds the time the batch's applies alone would take
+    at those rates, a floor for the batched solve."""
     import torch
     from paper_1712_08565_gb300 import inputs
     specs = inputs.batch_patches(count=BATCH["count"], seed=BATCH["seed"])
@@ -704,6 +707,9 @@ def batched(mf, device):
            "sweeps": max(i.outer_iterations for i in infos), "iterations_min_max": [min(i.iterations for i in infos), max(i.iterations for i in infos)],
            "all_converged": all(i.converged for i in infos),
            "apply_dof_per_s": sum(2 * i.iterations * op.N for i, op in zip(infos, ops)) / tb,
+           "applies_at_full_size_rates_s": (sum(2 * i.iterations * op.N / apply_rate[p]
+                                                for i, op, (p, _) in zip(infos, ops, specs))
+                                            if apply_rate and all(p in apply_rate for p, _ in specs) else None),
            "autotuned_xstage": {str(k): v for k, v in sorted(lines.items())},
            "fd64_path": "split", "grouped_4_s": tgs, "grouped_split_ran": gs_ran,
            "grouped_split_bitwise_equal_to_streams": gs_equal,
@@ -838,7 +844,8 @@ def run_ours(args):
         extras["p_sweep_nel128"] = p_sweep(mf, device)
         extras["mixed_vs_fp64"] = mixed_vs_fp64(mf, device)
         extras["coeff_onthefly"] = coeff_onthefly(mf, device)
-        extras["batched_64"] = batched(mf, device)
+        rates = {int(k[1:]): v["dof_per_s"] for k, v in extras["p_sweep_nel128"].items()}
+        extras["batched_64"] = batched(mf, device, rates)
         extras["reaction"] = reaction(mf, device)
         extras["fp64_solve_low_fd"] = fp64_low_fd(mf, device)
         extras["adjoint"] = adjoint(mf, device)
