@@ -104,7 +104,7 @@ size_t slow_vec_smem(int R, int width, int vw) {
 // columns taken in pairs by the packed FP32 FMA (Op::fma2, each of its two
 // FMAs rounded as by fmaf).  The band weights sit in shared memory as
 // (w, w) pairs.  The input rows reach the thread through its own ring of ST
-// shared-memory slots filled by cp.async, ST - 1 rows ahead of the row being
+// shared-memory slots filled by cp.async, up to ST rows ahead of the row being
 // summed, so several rows' loads are in flight per thread without holding
 // registers (no block barrier: each thread reads only the slots it filled).
 // Every output is summed in the same order as by the one-column form, so the
@@ -190,7 +190,8 @@ __device__ __forceinline__ void slow_body_vec(const Op& op, const SlowGeom& g, i
                     for (int v = 0; v < VP; ++v) op.fma2(w, x[v], acc[k][v]);
                 }
             }
-            // the slot just read takes row q + ST (issue is in order: its reads are done)
+            // the slot just read takes row q + ST: its shared-memory loads were issued
+            // before this copy, which writes the slot only once its global read returns
             if (j + ST < nq) fetch(q + ST, slot);
             cp_async_commit_group();
             slot = slot + 1 == ST ? 0 : slot + 1;
